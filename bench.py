@@ -1,0 +1,323 @@
+"""Benchmark of the weighting-field hot path on GB300.
+
+Workload (default): the 3x3 pixel cell (165 x 165 x 500 um, grid
+128 x 128 x 256, 18 graphitised columns, 256 sources per column, 512
+log-spaced time samples 1 ps - 10 ns).  Metric: H grid-point x time-samples
+per second of the FP32 bulk extension (basis-field spectral passes + tensor-
+core expansion writing H once), at the accuracy checked against the FP64
+plain path and the oracle in tests/.  The one-time FP64 setup (boundary fit,
+relaxation modes, time basis) is done before timing and reported as
+``setup_s``.
+
+One step = one wt_extend(WT_FP32) into a device buffer.  L2 is flushed
+(256 MB write) before every timed step.  ``e2e`` times the same call through
+the C ABI with a pinned host buffer (device compute + device-to-host copy of
+H).  ``cpu_baseline`` times the FP64 oracle on a bounded sample of the same
+workload.  Multi-GPU: every rank runs its own replica (the path has no
+exchange step); value = all ranks' point-samples / max time.
+
+--impl reference runs the FP64 CPU oracle (the reference arm of this
+build: the paper ships no code) on the same workload, a bounded sample per
+step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD_NAME = "c2: 3x3 pixel cell 165x165x500 um, grid 128x128x256, 18 columns x 256 sources, 512 time samples"
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, gpu_index):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines()]
+            rows = [[x.strip() for x in r] for r in rows if len(r) >= 9 and r[0].strip() == str(gpu_index)]
+            if not rows:
+                return out
+            sm = [float(r[1]) for r in rows]
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(float(r[2]) for r in rows)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for k, n in enumerate(names):
+                if any(r[5 + k].lower() == "active" for r in rows):
+                    out["reasons"].append(n)
+            out["samples"] = len(rows)
+        except Exception:
+            pass
+        return out
+
+
+def dist_init():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, sol, rng_seed=11, n_t=4, n_side=12):
+    """Bounded oracle sample of the workload's H: n_t time samples on an
+    n_side^3 random tensor-product subgrid.  Returns (point-samples, seconds)."""
+    import numpy as np
+    rng = np.random.default_rng(rng_seed)
+    g = w.grid
+    ti = np.sort(rng.choice(len(w.times), n_t, replace=False))
+    ix = np.sort(rng.choice(g.Nx, n_side, replace=False))
+    iy = np.sort(rng.choice(g.Ny, n_side, replace=False))
+    iz = np.sort(rng.choice(g.Nz, n_side, replace=False))
+    t0 = time.perf_counter()
+    sol.H_subgrid(t_idx=ti, ix=ix, iy=iy, iz=iz)
+    dt = time.perf_counter() - t0
+    return n_t * n_side ** 3, dt
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores (reference arm)."""
+    rank, local, world = dist_init()
+    if rank != 0:
+        return 0
+    import workloads as W
+    import oracle as O
+    w = W.workload("c2")
+    t0 = time.perf_counter()
+    sol = O.solve(w)
+    setup = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        oracle_sample(w, sol, n_t=1, n_side=8)
+    tot_ps, tot_s = 0, 0.0
+    for k in range(args.steps):
+        ps, s = oracle_sample(w, sol, rng_seed=100 + k)
+        tot_ps += ps
+        tot_s += s
+    v = tot_ps / tot_s
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": "H grid-point*time-samples/sec", "value": v,
+            "unit": "point-samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": "4 time samples x 12^3 random subgrid per step"},
+            "cpu_baseline": {"value": v, "unit": "point-samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "4 time samples x 12^3 grid points per step; oracle setup excluded "
+                                       f"({setup:.1f} s)"},
+            "e2e": {"value": v, "unit": "point-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "setup_s": setup}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2605_13987_gb300 as P
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load_library()
+    w = W.workload("c2")
+    g = w.grid
+    npts = g.Nx * g.Ny * g.Nz
+    nt = len(w.times)
+    ps_step = npts * nt
+
+    t0 = time.perf_counter()
+    sen = P.Sensor(w.grid, w.columns, device=local)
+    cond = sen.fit()
+    sen.relax(w.times)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    info = sen.info()
+
+    H = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sen.extend("fp32", out=H)
+    torch.cuda.synchronize()
+
+    sen.set_timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = []
+    launches = 0
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            sen.extend("fp32", out=H)
+            ends[k].record(stream)
+            ms3, n = sen.timing()
+            stage_ms.append(ms3)
+            launches += n
+        torch.cuda.synchronize()
+        barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    value = world * ps_step / (ms_max / 1e3)
+
+    # dominant kernel: the expansion; algorithmic bytes = 12 B per point-sample (H written once)
+    exp_ms = sum(s[2] for s in stage_ms) / len(stage_ms)
+    peak, peak_kind = peaks()
+    alg_bytes = 12.0 * ps_step
+    achieved = alg_bytes / (exp_ms / 1e3) / 1e9
+    traffic = None
+    tr_file = os.path.join(ROOT, "profiles", "expand_tc_traffic.json")
+    if os.path.exists(tr_file):
+        try:
+            traffic = json.load(open(tr_file)).get("bytes_per_launch_full_size")
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI: pinned host output, device compute + D2H copy of H
+    e2e = None
+    if not args.no_e2e:
+        Hh = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, pin_memory=True)
+        sen.set_timing(False)
+        sen.extend("fp32", out=Hh)
+        barrier(world)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        k2 = max(1, min(3, args.steps))
+        for _ in range(k2):
+            sen.extend("fp32", out=Hh)
+        torch.cuda.synchronize()
+        el = max_over_ranks((time.perf_counter() - t1) / k2, world)
+        e2e = {"value": world * ps_step / el, "unit": "point-samples/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(Hh.numel() * 4)}
+        del Hh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        t2 = time.perf_counter()
+        sol = O.solve(w)
+        osetup = time.perf_counter() - t2
+        tot_ps, tot_s = 0, 0.0
+        while tot_s < 10.0:
+            ps_, s_ = oracle_sample(w, sol, rng_seed=7 + int(tot_s * 10))
+            tot_ps += ps_
+            tot_s += s_
+        cpu = {"value": tot_ps / tot_s, "unit": "point-samples/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{tot_ps} point-samples (4 time samples x 12^3 random grid points per draw) in "
+                         f"{tot_s:.1f} s; oracle setup ({osetup:.1f} s) excluded like the GPU setup"}
+
+    if rank == 0:
+        line = {
+            "metric": "H grid-point*time-samples/sec (FP32 extension, 12 B/point-sample written once)",
+            "value": value, "unit": "point-samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}", "rank": info["rank"], "time_samples": nt,
+                       "grid_points": npts},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "expand_tc_kernel", "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": exp_ms},
+            "stage_ms": {"column_transform": sum(s[0] for s in stage_ms) / len(stage_ms),
+                         "spectral_passes": sum(s[1] for s in stage_ms) / len(stage_ms),
+                         "expansion": exp_ms},
+            "step_frac_of_hbm_roof": (alg_bytes / (ms_max / 1e3) / 1e9) / peak,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(local),
+            "setup_s": setup,
+            "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond,
+                      "boundary_residual": info["boundary_residual"], "trunc_rel": info["trunc_rel"]},
+        }
+        print(json.dumps(line), flush=True)
+    sen.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    args = ap.parse_args()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

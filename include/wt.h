@@ -1,0 +1,204 @@
+/*
+ * wt.h -- C ABI of the GB300 weighting-field library.
+ *
+ * Computes the time-dependent weighting field H(x, t) of a 3D diamond sensor
+ * with resistive graphitised column electrodes (arXiv 2605.13987), and the
+ * Ramo-Shockley-Riegler induced current of Eq. 1 from it.
+ *
+ * Method (the paper prints only Eq. 1 and the resistance formula of Sec. 5;
+ * the rest is its Abstract / Sec. 1 / Sec. 3 description):
+ *   - point sources ("fundamental solutions", Abstract; Sec. 3) on each column
+ *     axis, their magnitudes fitted to the electrode boundary values;
+ *   - the quasi-static third-order PDE (Abstract) reduced to resistive lines
+ *     coupled through the fitted capacitance, relaxed in time exactly in
+ *     FP64 (Sec. 3 describes forward-Euler steps; the exact modal exponential
+ *     is their dt -> 0 limit);
+ *   - a pseudo-spectral extension into the bulk (Abstract; Sec. 1 "discrete
+ *     Fourier transforms"; Sec. 3 spectra multiplied/divided by |k|^2) at
+ *     every time sample.
+ *
+ * Units: SI (m, s, Ohm*m, F, C, V).  Grid points: x_i = i Lx/Nx,
+ * y_j = j Ly/Ny, z_k = (k + 1/2) Lz/Nz.  Lateral boundaries are periodic; z is
+ * mirrored at 0 and Lz (Neumann).  Spectral modes: |m_x| <= Nx/2 - 1,
+ * |m_y| <= Ny/2 - 1 (Nyquist dropped), k_z = pi m_z / Lz, m_z = 0..Nz-1.
+ *
+ * H layout in memory: H[t][c][x][y][z], z fastest, c = 0,1,2 the field
+ * components (V/m), t the time samples given to wt_relax.  H stores
+ * W = -grad(psi) of the step response to V_w applied at t = 0 on the driven
+ * readout; Eq. 1's impulse response is its time derivative (see wt_eq1).
+ *
+ * Conventions.  Every call returns a wt_status; nothing aborts or prints.
+ * wt_last_error() gives the message of the last failed call on a context.
+ * The caller owns every buffer it passes; the library owns the context and
+ * its internal device workspaces (allocated with cudaMalloc on the
+ * context's device).  Calls must come in order: create -> add_columns ->
+ * fit -> relax -> extend / sample_H / eq1; an out-of-order call returns
+ * WT_ERR_STATE.  A context is not thread-safe; use one per host thread.
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wt_ctx wt_ctx;
+
+typedef enum {
+    WT_OK = 0,
+    WT_ERR_ARG = 1,              /* bad argument: NULL, size, range */
+    WT_ERR_GEOMETRY = 2,         /* overlapping columns, column outside the sensor */
+    WT_ERR_ILL_CONDITIONED = 3,  /* fit matrix too ill-conditioned for FP64 */
+    WT_ERR_NOT_SPD = 4,          /* fitted capacitance not positive definite */
+    WT_ERR_OOM = 5,              /* device allocation failed */
+    WT_ERR_CUDA = 6,             /* CUDA runtime error */
+    WT_ERR_TIMEOUT = 7,          /* a bounded device wait gave up */
+    WT_ERR_STATE = 8,            /* call out of order */
+    WT_ERR_NAN = 9,              /* non-finite input or intermediate */
+    WT_ERR_UNSUPPORTED = 10      /* size or option this build does not handle */
+} wt_status;
+
+typedef enum { WT_FP32 = 0, WT_FP64 = 1 } wt_precision;
+typedef enum { WT_Z_MIRROR = 0, WT_Z_PERIODIC = 1 } wt_zbc;
+
+/* Sensor box and voxel grid.  Nx, Ny even; eps_r = relative permittivity
+ * (5.7 for diamond; the columns take the same value). */
+typedef struct {
+    double Lx, Ly, Lz;
+    int Nx, Ny, Nz;
+    double eps_r;
+    int zbc;                     /* wt_zbc; only WT_Z_MIRROR in this build */
+} wt_grid;
+
+/* One graphitised column: axis at (x, y), spanning z0..z1, radius, and
+ * resistivity [Ohm*m] (Sec. 5: R = 4 rho L / (pi d^2)).  terminal_top = 1
+ * puts the terminal at z1 (readout), 0 at z0 (bias).  driven = 1 holds the
+ * terminal at V_w (the readout whose weighting field is computed); all other
+ * terminals are at 0.  n_sources point sources sit on the axis at
+ * z0 + (j + 1/2)(z1 - z0)/n_sources. */
+typedef struct {
+    double x, y, z0, z1, radius, resistivity;
+    int terminal_top;
+    int driven;
+    int n_sources;
+} wt_column;
+
+/* Boundary fit: n_h * n_sources collocation heights times n_az azimuths
+ * (az0 + 2 pi a / n_az) per column, on the column surface.  tikhonov >= 0
+ * is a relative ridge weight (0 = plain least squares).  v_w = weighting
+ * potential (Eq. 1: 1 V). */
+typedef struct {
+    int n_az, n_h;
+    double tikhonov;
+    double v_w;
+    double az0;
+} wt_fit_opts;
+
+/* Carrier tracks for Eq. 1, [track][step] float32 arrays, positions in m,
+ * velocities in m/s, time step dt [s].  Pointers may be device or host
+ * memory.  q: optional per-track charge [C] (NULL: every track has
+ * `charge`).  n_out output times tau_m = m dt, m = 0..n_out-1. */
+typedef struct {
+    int n_tracks, n_steps, n_out;
+    double dt, charge;
+    const float *x, *y, *z, *vx, *vy, *vz;
+    const float *q;
+} wt_tracks;
+
+/* Diagnostics of a context after wt_fit / wt_relax. */
+typedef struct {
+    int n_columns, n_sources, n_colloc, n_t;
+    int rank;                    /* time-basis rank of the FP32 path (0 before relax) */
+    double cond_estimate;        /* 2-norm condition estimate of the column-scaled fit matrix */
+    double boundary_residual;    /* ||P q + c - S phi_DC|| / ||S phi_DC|| of the DC state */
+    double asymmetry;            /* ||F - F^T|| / ||F|| (Green reciprocity) */
+    double trunc_rel;            /* sigma_{rank+1} / sigma_1 of the charge history */
+    double mu_min, mu_max;       /* relaxation rates [1/s] */
+    double fit_seconds, relax_seconds;
+} wt_info;
+
+/* Create a context on CUDA device `cuda_device` for the given grid.
+ * Fails with WT_ERR_ARG for non-positive sizes or odd Nx/Ny, and
+ * WT_ERR_UNSUPPORTED for a z boundary this build does not implement. */
+wt_status wt_create(wt_ctx** out, const wt_grid* grid, int cuda_device);
+
+/* Append n columns (host array).  Geometry is validated at wt_fit. */
+wt_status wt_add_columns(wt_ctx* ctx, const wt_column* cols, int n);
+
+/* Boundary fit (Abstract; Sec. 3 point charges adjusted in magnitude),
+ * FP64 on the GPU: the fit matrix P of the band-limited fundamental
+ * solution at the collocation points, the neutral least-squares fit
+ * q = F phi with one free potential offset (normal equations with column
+ * scaling, one step of residual correction), capacitance C_n = (F + F^T)/2.
+ * cond_estimate_out (may be NULL) receives the condition estimate.
+ * Synchronous.  Errors: WT_ERR_GEOMETRY, WT_ERR_NOT_SPD (the normal
+ * matrix or the capacitance is not positive definite), WT_ERR_ILL_CONDITIONED. */
+wt_status wt_fit(wt_ctx* ctx, const wt_fit_opts* opts, double* cond_estimate_out);
+
+/* Relaxation in time (Abstract: third-order quasi-static PDE; Sec. 3
+ * forward-Euler iteration, here its exact limit), FP64 on the GPU:
+ * C_n dphi/dt = K phi + b with the resistive lines of Sec. 5, solved by
+ * the generalised symmetric eigenproblem on the neutral subspace; the node
+ * charges q(t_n) at the n_t host times t[] (seconds, increasing, > 0), and
+ * the rank-r time basis used by the FP32 path.  Synchronous. */
+wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
+
+/* Bulk extension (Abstract; Sec. 1 DFT; Sec. 3 |k|^2 spectral division):
+ * writes H[t][c][x][y][z] for all n_t times.  WT_FP64: plain path, one
+ * FP64 spectral transform per time sample, H as double (24 B per
+ * point-sample).  WT_FP32: fast path, FP32 basis fields of the rank-r
+ * time basis and a tensor-core expansion, H as float (12 B per
+ * point-sample).  H may be device memory (written on cuda_stream, a
+ * cudaStream_t or NULL; asynchronous) or host memory (the library computes
+ * into an internal device buffer and copies out; returns after the copy).
+ * H_bytes must be >= n_t * 3 * Nx*Ny*Nz * sizeof(element), else WT_ERR_ARG. */
+wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
+
+/* Exact FP64 point evaluation of H (the band-limited spectral sum, no grid
+ * interpolation) at n host points xyz[n][3] and n_t host times t[] (any
+ * t >= 0, not only the relaxation samples).  out: host [n_t][n][3].
+ * Synchronous. */
+wt_status wt_sample_H(wt_ctx* ctx, const double* xyz, int n, const double* t, int n_t, double* out);
+
+/* Eq. 1 (Ramo-Shockley-Riegler convolution) from an FP32 H produced by
+ * wt_extend(WT_FP32): for each track and output time
+ *   Q(tau_m) = sum_{m' <= m, m' < n_steps} H(x_m', (m - m' + 1/2) dt) . v_m' dt,
+ *   i(tau_m) = -(q / V_w) (Q(tau_m) - Q(tau_{m-1})) / dt,
+ * with trilinear interpolation in space (periodic x, y; z clamped to the
+ * first/last grid plane) and linear interpolation in time (H = 0 at t = 0,
+ * held after the last sample).  H must be device memory.  Track arrays and
+ * i ([n_tracks][n_out] float32) may be device or host memory; the call
+ * returns after the result is written. */
+wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, void* cuda_stream);
+
+/* Copy intermediate results to host memory (for checks and diagnostics):
+ * q: [n_t][n_sources] node charges (after wt_relax);
+ * cn: [n_sources][n_sources] capacitance (after wt_fit);
+ * mu: [n_sources - 1] relaxation rates (after wt_relax). */
+wt_status wt_get_charges(wt_ctx* ctx, double* q);
+wt_status wt_get_capacitance(wt_ctx* ctx, double* cn);
+wt_status wt_get_modes(wt_ctx* ctx, double* mu);
+wt_status wt_get_info(wt_ctx* ctx, wt_info* info);
+
+/* Stage timing of wt_extend (instrumentation, off by default).  With
+ * wt_set_timing(ctx, 1), each wt_extend records CUDA events on the stream it
+ * launches on around its stages; wt_get_timing then waits for them and
+ * returns ms[0] = column transforms, ms[1] = spectral passes, ms[2] =
+ * expansion (FP32 path; 0 for FP64), and the number of kernels the call
+ * launched. */
+wt_status wt_set_timing(wt_ctx* ctx, int enable);
+wt_status wt_get_timing(wt_ctx* ctx, double* ms3, int* n_launches);
+
+/* Message of the last failed call on ctx (or of a failed wt_create when
+ * ctx is NULL); valid until the next call on ctx. */
+const char* wt_last_error(const wt_ctx* ctx);
+
+/* Release the context and its device memory.  NULL is a no-op. */
+void wt_destroy(wt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WT_H */

@@ -1,0 +1,232 @@
+"""ctypes binding of libwt.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (wt_create,
+wt_fit, ...).  Device buffers come from torch tensors (data_ptr) and
+streams from torch.cuda streams; no computation happens in Python.  The
+library must be built (``build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwt.so")
+
+WT_OK, WT_ERR_ARG, WT_ERR_GEOMETRY, WT_ERR_ILL_CONDITIONED, WT_ERR_NOT_SPD = 0, 1, 2, 3, 4
+WT_ERR_OOM, WT_ERR_CUDA, WT_ERR_TIMEOUT, WT_ERR_STATE, WT_ERR_NAN, WT_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
+WT_FP32, WT_FP64 = 0, 1
+WT_Z_MIRROR, WT_Z_PERIODIC = 0, 1
+STATUS_NAMES = {0: "WT_OK", 1: "WT_ERR_ARG", 2: "WT_ERR_GEOMETRY", 3: "WT_ERR_ILL_CONDITIONED",
+                4: "WT_ERR_NOT_SPD", 5: "WT_ERR_OOM", 6: "WT_ERR_CUDA", 7: "WT_ERR_TIMEOUT",
+                8: "WT_ERR_STATE", 9: "WT_ERR_NAN", 10: "WT_ERR_UNSUPPORTED"}
+
+
+class wt_grid(C.Structure):
+    _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int),
+                ("eps_r", C.c_double), ("zbc", C.c_int)]
+
+
+class wt_column(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z0", C.c_double), ("z1", C.c_double),
+                ("radius", C.c_double), ("resistivity", C.c_double),
+                ("terminal_top", C.c_int), ("driven", C.c_int), ("n_sources", C.c_int)]
+
+
+class wt_fit_opts(C.Structure):
+    _fields_ = [("n_az", C.c_int), ("n_h", C.c_int), ("tikhonov", C.c_double),
+                ("v_w", C.c_double), ("az0", C.c_double)]
+
+
+class wt_tracks(C.Structure):
+    _fields_ = [("n_tracks", C.c_int), ("n_steps", C.c_int), ("n_out", C.c_int),
+                ("dt", C.c_double), ("charge", C.c_double),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("q", C.c_void_p)]
+
+
+class wt_info(C.Structure):
+    _fields_ = [("n_columns", C.c_int), ("n_sources", C.c_int), ("n_colloc", C.c_int), ("n_t", C.c_int),
+                ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
+                ("asymmetry", C.c_double), ("trunc_rel", C.c_double), ("mu_min", C.c_double),
+                ("mu_max", C.c_double), ("fit_seconds", C.c_double), ("relax_seconds", C.c_double)]
+
+
+# name -> (restype, argtypes); the ABI of include/wt.h
+SIGNATURES = {
+    "wt_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(wt_grid), C.c_int]),
+    "wt_add_columns": (C.c_int, [C.c_void_p, C.POINTER(wt_column), C.c_int]),
+    "wt_fit": (C.c_int, [C.c_void_p, C.POINTER(wt_fit_opts), C.POINTER(C.c_double)]),
+    "wt_relax": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
+    "wt_extend": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "wt_sample_H": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.c_int,
+                              C.POINTER(C.c_double)]),
+    "wt_eq1": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
+    "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "wt_get_capacitance": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "wt_get_modes": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "wt_get_info": (C.c_int, [C.c_void_p, C.POINTER(wt_info)]),
+    "wt_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "wt_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "wt_last_error": (C.c_char_p, [C.c_void_p]),
+    "wt_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libwt.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} missing: build the CUDA library first (paper_2605_13987_gb300.build.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class WTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, ctx):
+    if code != WT_OK:
+        lib = load_library()
+        raise WTError(code, lib.wt_last_error(ctx).decode(errors="replace"))
+
+
+def _dptr(a):
+    return C.c_double_p if False else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+# ---------------------------------------------------------------- C names
+def wt_create(grid, cuda_device=0):
+    lib = load_library()
+    ctx = C.c_void_p()
+    g = wt_grid(grid.Lx, grid.Ly, grid.Lz, grid.Nx, grid.Ny, grid.Nz, grid.eps_r,
+                WT_Z_MIRROR if getattr(grid, "zbc", "mirror") == "mirror" else WT_Z_PERIODIC)
+    _check(lib.wt_create(C.byref(ctx), C.byref(g), int(cuda_device)), None)
+    return ctx
+
+
+def wt_add_columns(ctx, columns):
+    lib = load_library()
+    arr = (wt_column * len(columns))(*[wt_column(c.x, c.y, c.z0, c.z1, c.radius, c.resistivity,
+                                                 int(c.terminal_top), int(c.driven), int(c.n_sources))
+                                       for c in columns])
+    _check(lib.wt_add_columns(ctx, arr, len(columns)), ctx)
+
+
+def wt_fit(ctx, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0):
+    lib = load_library()
+    o = wt_fit_opts(int(n_az), int(n_h), float(tikhonov), float(v_w), float(az0))
+    cond = C.c_double(0.0)
+    _check(lib.wt_fit(ctx, C.byref(o), C.byref(cond)), ctx)
+    return cond.value
+
+
+def wt_relax(ctx, times):
+    lib = load_library()
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    _check(lib.wt_relax(ctx, _dptr(t), len(t)), ctx)
+
+
+def wt_extend(ctx, precision, H, stream=None):
+    """H: torch tensor (cuda: asynchronous on `stream`; cpu: synchronous copy-out) or numpy array."""
+    lib = load_library()
+    nbytes = H.numel() * H.element_size() if hasattr(H, "numel") else H.nbytes
+    st = _stream_handle(stream) if (hasattr(H, "is_cuda") and H.is_cuda) else None
+    _check(lib.wt_extend(ctx, int(precision), _ptr(H), nbytes, st), ctx)
+
+
+def wt_sample_H(ctx, xyz, times):
+    lib = load_library()
+    p = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(times, dtype=np.float64).ravel()
+    out = np.zeros((len(t), len(p), 3))
+    _check(lib.wt_sample_H(ctx, _dptr(p), len(p), _dptr(t), len(t), _dptr(out)), ctx)
+    return out
+
+
+def wt_eq1(ctx, H, tracks, i_out, stream=None):
+    lib = load_library()
+    tr = wt_tracks(int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"]),
+                   float(tracks["dt"]), float(tracks.get("charge", 1.0)),
+                   _ptr(tracks["x"]), _ptr(tracks["y"]), _ptr(tracks["z"]),
+                   _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
+    st = _stream_handle(stream) if (hasattr(i_out, "is_cuda") and i_out.is_cuda) else None
+    _check(lib.wt_eq1(ctx, _ptr(H), C.byref(tr), _ptr(i_out), st), ctx)
+
+
+def wt_get_charges(ctx, n_t, n_sources):
+    lib = load_library()
+    out = np.zeros((n_t, n_sources))
+    _check(lib.wt_get_charges(ctx, _dptr(out)), ctx)
+    return out
+
+
+def wt_get_capacitance(ctx, n_sources):
+    lib = load_library()
+    out = np.zeros((n_sources, n_sources))
+    _check(lib.wt_get_capacitance(ctx, _dptr(out)), ctx)
+    return out
+
+
+def wt_get_modes(ctx, n_sources):
+    lib = load_library()
+    out = np.zeros(n_sources - 1)
+    _check(lib.wt_get_modes(ctx, _dptr(out)), ctx)
+    return out
+
+
+def wt_get_info(ctx):
+    lib = load_library()
+    info = wt_info()
+    _check(lib.wt_get_info(ctx, C.byref(info)), ctx)
+    return {k: getattr(info, k) for k, _ in wt_info._fields_}
+
+
+def wt_set_timing(ctx, enable=True):
+    _check(load_library().wt_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def wt_get_timing(ctx):
+    """(ms[3], n_launches) of the last timed wt_extend."""
+    ms = (C.c_double * 3)()
+    n = C.c_int(0)
+    _check(load_library().wt_get_timing(ctx, ms, C.byref(n)), ctx)
+    return list(ms), n.value
+
+
+def wt_destroy(ctx):
+    if ctx:
+        load_library().wt_destroy(ctx)

@@ -1,0 +1,102 @@
+// Eq. 1 (Ramo-Shockley-Riegler convolution) against carrier tracks, direct
+// form on the stored FP32 field H[t][c][x][y][z]:
+//   Q(tau_m) = sum_{m' <= m, m' < n_steps} W(x_m', (m - m' + 1/2) dt) . v_m' dt
+//   i(tau_m) = -(q / V_w) (Q(tau_m) - Q(tau_{m-1})) / dt
+// W between grid points: trilinear (periodic x, y; z clamped to the first and
+// last grid planes); between time samples: linear in t, W(0) = 0, held after
+// the last sample.  One block per track: the dot products W(x_m', t_n) . v_m'
+// at the time samples are staged in shared memory for a chunk of steps, then
+// every output time accumulates its lags in FP64.
+#include "wt_internal.cuh"
+
+namespace wt {
+
+struct Eq1Lag {
+    int n;          // lower time sample
+    float w0, w1;   // weights of samples n and n+1
+};
+
+constexpr int EQ1_MC = 16;   // track steps per chunk
+
+__global__ void __launch_bounds__(256) eq1_kernel(const float* __restrict__ H, int Nx, int Ny, int Nz, int nt,
+                                                  float inv_hx, float inv_hy, float inv_hz,
+                                                  const float* __restrict__ X, const float* __restrict__ Y,
+                                                  const float* __restrict__ Z, const float* __restrict__ VX,
+                                                  const float* __restrict__ VY, const float* __restrict__ VZ,
+                                                  const float* __restrict__ qtrack, float qconst, int n_steps,
+                                                  int n_out, double dt, double inv_vw,
+                                                  const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
+    extern __shared__ unsigned char smem_raw[];
+    float* f = reinterpret_cast<float*>(smem_raw);                       // [EQ1_MC][nt]
+    double* Q = reinterpret_cast<double*>(f + EQ1_MC * nt + (EQ1_MC * nt & 1));   // [n_out]
+    const int tr = blockIdx.x;
+    const size_t npts = (size_t)Nx * Ny * Nz;
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x) Q[m] = 0.0;
+    for (int c0 = 0; c0 < n_steps; c0 += EQ1_MC) {
+        const int mc = min(EQ1_MC, n_steps - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < mc * nt; e += blockDim.x) {
+            const int j = e / nt, n = e % nt;
+            const size_t s = (size_t)tr * n_steps + c0 + j;
+            const float vx = VX[s], vy = VY[s], vz = VZ[s];
+            float acc = 0.f;
+            if (vx != 0.f || vy != 0.f || vz != 0.f) {
+                const float fx = X[s] * inv_hx, fy = Y[s] * inv_hy;
+                float fz = fminf(fmaxf(Z[s] * inv_hz - 0.5f, 0.f), (float)(Nz - 1));
+                const float flx = floorf(fx), fly = floorf(fy);
+                int k0 = min((int)floorf(fz), Nz - 2);
+                const float wx = fx - flx, wy = fy - fly, wz = fz - (float)k0;
+                int i0 = ((int)flx % Nx + Nx) % Nx, j0 = ((int)fly % Ny + Ny) % Ny;
+                const int i1 = (i0 + 1) % Nx, j1 = (j0 + 1) % Ny;
+                const float* hb = H + (size_t)n * 3 * npts;
+                float w[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float* h = hb + (size_t)c * npts;
+                    const size_t a00 = ((size_t)i0 * Ny + j0) * Nz + k0, a01 = ((size_t)i0 * Ny + j1) * Nz + k0;
+                    const size_t a10 = ((size_t)i1 * Ny + j0) * Nz + k0, a11 = ((size_t)i1 * Ny + j1) * Nz + k0;
+                    const float v00 = (1.f - wz) * h[a00] + wz * h[a00 + 1];
+                    const float v01 = (1.f - wz) * h[a01] + wz * h[a01 + 1];
+                    const float v10 = (1.f - wz) * h[a10] + wz * h[a10 + 1];
+                    const float v11 = (1.f - wz) * h[a11] + wz * h[a11 + 1];
+                    w[c] = (1.f - wx) * ((1.f - wy) * v00 + wy * v01) + wx * ((1.f - wy) * v10 + wy * v11);
+                }
+                acc = w[0] * vx + w[1] * vy + w[2] * vz;
+            }
+            f[j * nt + n] = acc;
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+            double q = 0.0;
+            const int jmax = min(mc - 1, m - c0);
+            for (int j = 0; j <= jmax; ++j) {
+                const Eq1Lag L = lags[m - (c0 + j)];
+                q += (double)L.w0 * f[j * nt + L.n] + (double)L.w1 * f[j * nt + min(L.n + 1, nt - 1)];
+            }
+            Q[m] += q * dt;
+        }
+    }
+    __syncthreads();
+    const float qc = qtrack ? qtrack[tr] : qconst;
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+        const double dq = Q[m] - (m ? Q[m - 1] : 0.0);
+        out[(size_t)tr * n_out + m] = (float)(-(double)qc * inv_vw * dq / dt);
+    }
+}
+
+void eq1_launch(cudaStream_t s, const float* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
+                const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
+                const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
+                const void* lags, float* out) {
+    size_t sh = (size_t)EQ1_MC * nt * sizeof(float) + 8 + (size_t)n_out * sizeof(double);
+    if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
+    WT_CUDA(cudaFuncSetAttribute(eq1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    eq1_kernel<<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly), (float)(Nz / Lz), x, y,
+                                         z, vx, vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
+                                         static_cast<const Eq1Lag*>(lags), out);
+    WT_LAUNCH("eq1");
+}
+size_t eq1_lag_size() { return sizeof(Eq1Lag); }
+void eq1_pack_lag(void* dst, int n, float w0, float w1) { *static_cast<Eq1Lag*>(dst) = Eq1Lag{n, w0, w1}; }
+
+}  // namespace wt

@@ -1,0 +1,316 @@
+// Tensor-core expansion of the FP32 basis fields over time (the dense
+// source/basis -> grid step of the bulk extension, Sec. 3's V_ext
+// superposition of rescaled fundamental-solution chunks, here in its
+// time-compressed form):
+//
+//   H[t][c][p] = sum_{m < 32} W[t][m] E[c][m][p]
+//
+// One CTA per SM, persistent over work units (128 grid points x one field
+// component).  Per unit the 128 x 32 slice of E is split into TF32 hi/lo
+// parts in shared memory (128-byte swizzled, K-major); the time
+// coefficients W (hi/lo) stay in shared memory for the whole kernel.  Three
+// tcgen05.mma products (hi*hi + hi*lo + lo*hi, kind::tf32, FP32
+// accumulation in tensor memory) give FP32-level accuracy.  The accumulator
+// D[p][t] lives in TMEM (lane = grid point, column = time sample), double
+// buffered in two 256-column halves; four epilogue warps drain it with
+// tcgen05.ld and write H with fully coalesced 128-byte warp stores (32
+// consecutive grid points of one time sample).
+//
+// Warp roles: warp 0 producer, warp 1 TMEM owner + MMA issuer, warps 2-5
+// epilogue.  Every mbarrier wait gives up after ~2 s (globaltimer), sets
+// the device error word and lets the CTA unwind, draining its own MMAs
+// before freeing tensor memory.
+#include "wt_internal.cuh"
+
+namespace wt {
+
+namespace tc {
+
+constexpr int BM = 128;            // grid points per unit (TMEM lanes)
+constexpr int KR = 32;             // basis rank (TF32 elements per 128-byte row)
+constexpr int NCH = 256;           // time samples per accumulator half
+constexpr int TILE_BYTES = BM * 128;  // one 128 x 32 TF32 tile
+constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false on timeout (and the abort flag is raised).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, volatile int* abort_flag,
+                                          int* d_err) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try(b, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > TIMEOUT_NS) {
+            *abort_flag = 1;
+            atomicMax(d_err, (int)DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// byte offset of element (row, k) in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ unsigned sw128(int row, int k) {
+    return (unsigned)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 2) ^ (row & 7))) << 4) + ((k & 3) << 2));
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr) {
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (64ull << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+__device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                         unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct Smem {
+    // tiles first (1024-byte aligned base)
+    // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo]
+    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], drain;
+    unsigned tmem_base;
+    int abort_flag;
+};
+
+__global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restrict__ E, const float* __restrict__ W,
+                                                           int nt, int nt_pad, size_t npts, int n_tiles,
+                                                           float* __restrict__ H, int* __restrict__ d_err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // align the tile region to 1024 bytes
+    unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    unsigned char* b_hi = base;
+    unsigned char* b_lo = b_hi + (size_t)nt_pad * 128;
+    unsigned char* a_tiles = b_lo + (size_t)nt_pad * 128;          // [stage][hi|lo] x TILE_BYTES
+    Smem* S = reinterpret_cast<Smem*>(a_tiles + 4 * TILE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = n_tiles * 3;
+    const int n_chunks = (nt_pad + NCH - 1) / NCH;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S->a_full[i], 32);
+            mbar_init(&S->a_empty[i], 1);
+            mbar_init(&S->acc_full[i], 1);
+            mbar_init(&S->acc_empty[i], 128);
+        }
+        mbar_init(&S->drain, 1);
+        S->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // time coefficients, split hi/lo, into the swizzled B tiles (rows = time samples)
+    for (int e = threadIdx.x; e < nt_pad * KR; e += blockDim.x) {
+        const int t = e / KR, k = e % KR;
+        const float v = t < nt ? W[(size_t)t * KR + k] : 0.f;
+        const unsigned hi = to_tf32(v);
+        const unsigned lo = to_tf32(v - __uint_as_float(hi));
+        *reinterpret_cast<unsigned*>(b_hi + sw128(t, k)) = hi;
+        *reinterpret_cast<unsigned*>(b_lo + sw128(t, k)) = lo;
+    }
+    fence_proxy_async();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&S->tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = S->tmem_base;
+    volatile int* abort_flag = &S->abort_flag;
+
+    if (warp == 0) {
+        // ---------------- producer: E slice -> hi/lo swizzled A tiles
+        int i = 0;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++i) {
+            const int st = i & 1;
+            if (!mbar_wait(&S->a_empty[st], ((i >> 1) & 1) ^ 1, abort_flag, d_err)) break;
+            const int tile = u / 3, c = u % 3;
+            const size_t p0 = (size_t)tile * BM;
+            unsigned char* ah = a_tiles + (size_t)(2 * st) * TILE_BYTES;
+            unsigned char* al = ah + TILE_BYTES;
+            const float* src = E + ((size_t)c * KR + lane) * npts + p0;   // lane = k (basis index)
+            const bool full = p0 + BM <= npts;
+#pragma unroll 4
+            for (int r4 = 0; r4 < BM / 4; ++r4) {
+                float4 v;
+                if (full) {
+                    v = __ldg(reinterpret_cast<const float4*>(src) + r4);
+                } else {
+                    const size_t p = p0 + 4 * r4;
+                    v.x = p + 0 < npts ? src[4 * r4 + 0] : 0.f;
+                    v.y = p + 1 < npts ? src[4 * r4 + 1] : 0.f;
+                    v.z = p + 2 < npts ? src[4 * r4 + 2] : 0.f;
+                    v.w = p + 3 < npts ? src[4 * r4 + 3] : 0.f;
+                }
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int row = 4 * r4 + j;
+                    const unsigned hi = to_tf32(vv[j]);
+                    const unsigned lo = to_tf32(vv[j] - __uint_as_float(hi));
+                    *reinterpret_cast<unsigned*>(ah + sw128(row, lane)) = hi;
+                    *reinterpret_cast<unsigned*>(al + sw128(row, lane)) = lo;
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&S->a_full[st]);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (lane 0)
+        int i = 0, g = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
+            const int st = i & 1;
+            if (!mbar_wait(&S->a_full[st], (i >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
+            tc_fence_after();
+            const unsigned a_hi = smem_u32(a_tiles + (size_t)(2 * st) * TILE_BYTES);
+            const unsigned a_lo = a_hi + TILE_BYTES;
+            for (int ch = 0; ch < n_chunks; ++ch, ++g) {
+                const int b = g & 1;
+                if (!mbar_wait(&S->acc_empty[b], ((g >> 1) & 1) ^ 1, abort_flag, d_err)) { ok = false; break; }
+                tc_fence_after();
+                const int n = min(NCH, nt_pad - ch * NCH);
+                const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) |
+                                       ((unsigned)(BM >> 4) << 24);
+                if (lane == 0) {
+                    const unsigned bh = smem_u32(b_hi + (size_t)ch * NCH * 128);
+                    const unsigned bl = smem_u32(b_lo + (size_t)ch * NCH * 128);
+                    const unsigned d = tmem + (unsigned)(b * NCH);
+#pragma unroll
+                    for (int ks = 0; ks < KR / 8; ++ks) {
+                        const unsigned off = ks * 32;   // 8 TF32 = 32 bytes along K
+                        mma_tf32(d, sdesc(a_lo + off), sdesc(bh + off), idesc, ks > 0);
+                        mma_tf32(d, sdesc(a_hi + off), sdesc(bl + off), idesc, 1);
+                        mma_tf32(d, sdesc(a_hi + off), sdesc(bh + off), idesc, 1);
+                    }
+                    mma_commit(&S->acc_full[b]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (lane == 0) mma_commit(&S->a_empty[st]);
+            __syncwarp();
+        }
+        // drain: every MMA this thread issued has completed before TMEM is freed
+        if (lane == 0) {
+            mma_commit(&S->drain);
+            mbar_wait(&S->drain, 0, abort_flag, d_err);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: TMEM -> H
+        const int q = warp & 3;                      // TMEM lane quadrant of this warp
+        int g = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int tile = u / 3, c = u % 3;
+            const size_t p = (size_t)tile * BM + q * 32 + lane;
+            const bool in = p < npts;
+            float* hp = H + (size_t)c * npts + p;
+            for (int ch = 0; ch < n_chunks; ++ch, ++g) {
+                const int b = g & 1;
+                if (!mbar_wait(&S->acc_full[b], (g >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
+                tc_fence_after();
+                const int n = min(NCH, nt_pad - ch * NCH);
+                for (int j = 0; j < n; j += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), v);
+                    const int t0 = ch * NCH + j;
+                    if (in) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (t0 + e < nt) hp[(size_t)(t0 + e) * 3 * npts] = v[e];
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&S->acc_empty[b]);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+}  // namespace tc
+
+bool expand_tc_available() { return true; }
+
+size_t expand_tc_smem(int nt_pad) {
+    return 1024 + (size_t)2 * nt_pad * 128 + 4 * (size_t)tc::TILE_BYTES + sizeof(tc::Smem);
+}
+
+// E: [3][32][npts] FP32, W: [nt][32] FP32, H: [nt][3][npts] FP32.
+void expand_tc(cudaStream_t s, const float* E, int r_pad, const float* W, int nt, size_t npts, float* H, int* d_err) {
+    if (r_pad != tc::KR) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion needs rank padded to 32");
+    const int nt_pad = ((nt + 31) / 32) * 32;
+    if (nt_pad > 512) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion handles at most 512 time samples");
+    if (npts % 4) fail(WT_ERR_UNSUPPORTED, "grid size must be a multiple of 4");
+    const size_t sh = expand_tc_smem(nt_pad);
+    int dev = 0, n_sm = 0;
+    WT_CUDA(cudaGetDevice(&dev));
+    WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    WT_CUDA(cudaFuncSetAttribute(tc::expand_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    const int n_tiles = (int)((npts + tc::BM - 1) / tc::BM);
+    const int grid = std::min(n_sm, n_tiles * 3);
+    tc::expand_tc_kernel<<<grid, 192, sh, s>>>(E, W, nt, nt_pad, npts, n_tiles, H, d_err);
+    WT_LAUNCH("expand_tc");
+}
+
+}  // namespace wt

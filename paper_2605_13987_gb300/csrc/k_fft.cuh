@@ -1,0 +1,44 @@
+// Batched pseudo-spectral extension: charge vectors -> field components on
+// the voxel grid.  Templated on the arithmetic type (float: fast path basis
+// fields; double: plain FP64 path).
+#pragma once
+#include "wt_internal.cuh"
+
+namespace wt {
+
+struct FftPlan {
+    int N;
+    int ns;
+    int r[16];
+};
+FftPlan make_plan(int N);   // radices 4, 2, 3, 5, 7; fails for other prime factors
+
+struct GridDev {
+    int Nx, Ny, Nz;
+    double Lx, Ly, Lz;
+    double pref;            // 1 / (eps V')
+};
+
+// Per-context spectral machinery for one precision.
+template <class T>
+struct Spectral {
+    GridDev g{};
+    int n_cols = 0;
+    FftPlan pz{}, py{}, px{};
+    DBuf<double> col_xy;          // [n_cols][2]
+    DBuf<T> tw_z, tw_y, tw_x;     // interleaved complex twiddles e^{+2 pi i k / N}
+    void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);
+    // Zc [nb][n_cols][Nz] (column z-transforms of nb charge vectors) ->
+    // out[b * out_sb + c * out_sc + (x Ny + y) Nz + z], c = 0..2.
+    // G is a scratch buffer of nb * 3 * (Nx/2+1) * Ny * Nz complex T.
+    void fields(const T* Zc, int nb, T* G, T* out, size_t out_sb, size_t out_sc, cudaStream_t s) const;
+    size_t scratch_elems(int nb) const { return (size_t)nb * 3 * (g.Nx / 2 + 1) * g.Ny * g.Nz * 2; }
+};
+
+// Column z-transform of charge vectors: Zc[b][c][mz] = sum_{j in c} q[b][j] 2 cos(pi mz z_j / Lz).
+// q: [nb][n_src] (double), zsrc [n_src], src_col offsets [n_cols+1].
+template <class T>
+void column_ztransform(cudaStream_t s, const double* q, int nb, int n_src, int ldq, const double* zsrc,
+                       const int* col_off, int n_cols, int Nz, double Lz, T* Zc);
+
+}  // namespace wt

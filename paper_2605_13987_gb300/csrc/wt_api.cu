@@ -1,0 +1,960 @@
+// C ABI entry points and the host-side orchestration of the library:
+// geometry and layout (host, FP64), boundary fit and relaxation (GPU FP64),
+// bulk extension (GPU FP32 fast path / FP64 plain path).
+#include "wt_internal.cuh"
+#include "k_fft.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+
+namespace wt {
+
+// kernels defined in other translation units
+void green_invk2(cudaStream_t, int, int, int, double, double, double, double*);
+void green_lateral(cudaStream_t, const double*, int, int, int, int, double, double, const double*, double*);
+void green_cos_table(cudaStream_t, const double*, int, int, double, double*);
+void green_pblocks(cudaStream_t, const void*, int, int, int, const double*, const double*, const double*, int, double,
+                   double*, int);
+size_t pblock_size();
+void pack_pblock(void*, int, int, int, int, int, int, int);
+void fit_ats(cudaStream_t, const double*, int, int, int, const int*, const int*, const double*, int, double*);
+void fit_add_s(cudaStream_t, double*, int, int, const int*, const int*, const double*, double);
+void set_column(cudaStream_t, double*, int, int, int, double);
+void build_k(cudaStream_t, const double*, const double*, int, double*);
+void modal_factors(cudaStream_t, const double*, const double*, int, const double*, int, double*);
+void add_column_vector(cudaStream_t, double*, int, int, const double*);
+void to_float(cudaStream_t, const double*, size_t, double, float*);
+void check_finite(cudaStream_t, const double*, size_t, int*);
+void expand_simt(cudaStream_t, const float*, int, const float*, int, int, size_t, float*);
+void sample_lateral(cudaStream_t, const double*, int, const double*, int, int, int, int, double, double,
+                    const double*, double*);
+void sample_contract(cudaStream_t, const double*, const double*, const double*, int, int, int, int, double, double,
+                     double*);
+void eq1_launch(cudaStream_t, const float*, int, int, int, int, double, double, double, const float*, const float*,
+                const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
+                double, const void*, float*);
+size_t eq1_lag_size();
+void eq1_pack_lag(void*, int, float, float);
+bool expand_tc_available();
+void expand_tc(cudaStream_t, const float*, int, const float*, int, size_t, float*, int*);
+
+void fail(wt_status code, const std::string& msg) { throw Error{code, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(WT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+using clk = std::chrono::steady_clock;
+static double secs(clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); }
+
+}  // namespace wt
+
+using namespace wt;
+
+struct wt_ctx {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    wt_grid grid{};
+    std::vector<wt_column> cols;
+    wt_fit_opts opts{};
+    std::string err;
+    int stage = 0;                   // 0 created, 1 fitted, 2 relaxed
+    // layout (host)
+    int ns = 0, nc = 0;
+    std::vector<int> col_off, colloc_off;
+    std::vector<double> src_z;
+    std::vector<double> phi_dc;
+    // S as CSC lists: node j -> (collocation row, weight)
+    std::vector<int> s_ptr, s_idx;
+    std::vector<double> s_w;
+    double pref = 0;
+    // device, fit results
+    DBuf<int> d_err;
+    DBuf<double> d_scr;
+    DBuf<double> Cn;                 // ns x ns capacitance
+    DBuf<double> offset;             // ns: potential offset per node potential
+    // relaxation
+    std::vector<double> times;
+    DBuf<double> d_times, mu, qinf, Qt;   // Qt [nt][ns]
+    DBuf<double> Vm, amp;                 // modes (n1 x n1), amplitudes (n1)
+    DBuf<double> hv;                      // Householder vector
+    double beta = 0;
+    int rank = 0, r_pad = 0;
+    DBuf<double> Ub;                      // [r][ns] basis charge vectors
+    DBuf<float> W32;                      // [nt][r_pad] time coefficients
+    // spectral
+    DBuf<double> d_zsrc;
+    DBuf<int> d_col_off;
+    Spectral<float> sp32;
+    Spectral<double> sp64;
+    bool sp_ready = false;
+    DBuf<float> Zc32, G32, E32;
+    DBuf<double> Zc64, G64;
+    DBuf<float> stage32;
+    DBuf<double> stage64;
+    wt_info info{};
+    // stage timing (wt_set_timing)
+    bool timing = false;
+    bool use_tc = true;          // WT_EXPAND=simt selects the FP32 FMA expansion
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+    int last_launches = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+template <class F>
+wt_status run(wt_ctx* ctx, const char* fn, F&& body) {
+    try {
+        if (ctx) {
+            cudaError_t e = cudaSetDevice(ctx->dev);
+            if (e != cudaSuccess) fail(WT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+        }
+        body();
+        if (ctx) ctx->err.clear();
+        return WT_OK;
+    } catch (const Error& e) {
+        if (ctx) ctx->err = std::string(fn) + ": " + e.msg;
+        else g_create_err = std::string(fn) + ": " + e.msg;
+        return e.code;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->err = std::string(fn) + ": " + e.what();
+        return WT_ERR_CUDA;
+    }
+}
+
+int read_err(wt_ctx* c) {
+    int h = 0;
+    WT_CUDA(cudaMemcpyAsync(&h, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    WT_CUDA(cudaStreamSynchronize(c->s));
+    return h;
+}
+void clear_err(wt_ctx* c) { WT_CUDA(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->s)); }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void validate_geometry(const wt_ctx* c) {
+    const wt_grid& g = c->grid;
+    if (c->cols.empty()) fail(WT_ERR_GEOMETRY, "no columns");
+    for (size_t i = 0; i < c->cols.size(); ++i) {
+        const wt_column& k = c->cols[i];
+        if (!(k.z0 >= 0.0 && k.z1 > k.z0 && k.z1 <= g.Lz * (1 + 1e-12)))
+            fail(WT_ERR_GEOMETRY, "column " + std::to_string(i) + " z range outside the sensor");
+        if (!(k.radius > 0.0) || !(k.resistivity > 0.0) || k.n_sources < 1)
+            fail(WT_ERR_GEOMETRY, "column " + std::to_string(i) + ": radius, resistivity and n_sources must be > 0");
+        if (!std::isfinite(k.x) || !std::isfinite(k.y)) fail(WT_ERR_NAN, "non-finite column position");
+    }
+    for (size_t i = 0; i < c->cols.size(); ++i)
+        for (size_t j = i + 1; j < c->cols.size(); ++j) {
+            double dx = c->cols[i].x - c->cols[j].x, dy = c->cols[i].y - c->cols[j].y;
+            dx -= g.Lx * std::round(dx / g.Lx);
+            dy -= g.Ly * std::round(dy / g.Ly);
+            if (std::hypot(dx, dy) <= c->cols[i].radius + c->cols[j].radius)
+                fail(WT_ERR_GEOMETRY, "columns " + std::to_string(i) + " and " + std::to_string(j) + " overlap");
+        }
+}
+
+void build_layout(wt_ctx* c) {
+    const int ncol = (int)c->cols.size();
+    const int n_az = c->opts.n_az, n_h = c->opts.n_h;
+    c->col_off.assign(ncol + 1, 0);
+    c->colloc_off.assign(ncol + 1, 0);
+    c->src_z.clear();
+    for (int k = 0; k < ncol; ++k) {
+        const wt_column& col = c->cols[k];
+        const int m = col.n_sources;
+        const double dz = (col.z1 - col.z0) / m;
+        for (int j = 0; j < m; ++j) c->src_z.push_back(col.z0 + (j + 0.5) * dz);
+        c->col_off[k + 1] = c->col_off[k] + m;
+        c->colloc_off[k + 1] = c->colloc_off[k] + n_az * n_h * m;
+    }
+    c->ns = c->col_off[ncol];
+    c->nc = c->colloc_off[ncol];
+    // S: collocation height -> linear interpolation between the bracketing nodes
+    std::vector<std::vector<std::pair<int, double>>> lists(c->ns);
+    for (int k = 0; k < ncol; ++k) {
+        const wt_column& col = c->cols[k];
+        const int m = col.n_sources, nh = n_h * m;
+        const double dz = (col.z1 - col.z0) / m;
+        for (int a = 0; a < n_az; ++a)
+            for (int p = 0; p < nh; ++p) {
+                const int row = c->colloc_off[k] + a * nh + p;
+                const double zc = col.z0 + (p + 0.5) * (col.z1 - col.z0) / nh;
+                const double u = (zc - col.z0) / dz - 0.5;
+                const int off = c->col_off[k];
+                if (u <= 0.0) lists[off].push_back({row, 1.0});
+                else if (u >= m - 1) lists[off + m - 1].push_back({row, 1.0});
+                else {
+                    const int j = (int)std::floor(u);
+                    const double f = u - j;
+                    lists[off + j].push_back({row, 1.0 - f});
+                    if (f != 0.0) lists[off + j + 1].push_back({row, f});
+                }
+            }
+    }
+    c->s_ptr.assign(c->ns + 1, 0);
+    c->s_idx.clear();
+    c->s_w.clear();
+    for (int j = 0; j < c->ns; ++j) {
+        for (auto& e : lists[j]) { c->s_idx.push_back(e.first); c->s_w.push_back(e.second); }
+        c->s_ptr[j + 1] = (int)c->s_idx.size();
+    }
+    c->phi_dc.assign(c->ns, 0.0);
+    for (int k = 0; k < ncol; ++k)
+        if (c->cols[k].driven)
+            for (int j = c->col_off[k]; j < c->col_off[k + 1]; ++j) c->phi_dc[j] = c->opts.v_w;
+}
+
+// H M H for symmetric M (n x n, in place), H = I - beta v v^T.
+void householder_two_sided(wt_ctx* c, double* M, int n) {
+    DBuf<double> u;
+    u.alloc(n);
+    dgemv(c->s, false, n, n, 1.0, M, n, c->hv.p, 0.0, u.p);
+    std::vector<double> hu(n), hv(n);
+    u.download(hu.data(), n, c->s);
+    c->hv.download(hv.data(), n, c->s);
+    WT_CUDA(cudaStreamSynchronize(c->s));
+    double gamma = 0;
+    for (int i = 0; i < n; ++i) gamma += hv[i] * hu[i];
+    std::vector<double> w(n);
+    for (int i = 0; i < n; ++i) w[i] = c->beta * hu[i] - 0.5 * c->beta * c->beta * gamma * hv[i];
+    DBuf<double> dw;
+    dw.upload(w.data(), n, c->s);
+    rank1(c->s, n, n, -1.0, c->hv.p, dw.p, M, n);
+    rank1(c->s, n, n, -1.0, dw.p, c->hv.p, M, n);
+    WT_CUDA(cudaStreamSynchronize(c->s));
+}
+
+void do_fit(wt_ctx* c) {
+    auto t0 = clk::now();
+    validate_geometry(c);
+    build_layout(c);
+    const wt_grid& g = c->grid;
+    const int ncol = (int)c->cols.size(), ns = c->ns, nc = c->nc;
+    const int n_az = c->opts.n_az;
+    const double eps = kEps0 * g.eps_r;
+    const double vol = g.Lx * g.Ly * 2.0 * g.Lz;
+    c->pref = 1.0 / (eps * vol);
+    cudaStream_t s = c->s;
+    clear_err(c);
+
+    // --- S2: fundamental-solution tables and the fit matrix P
+    DBuf<double> T, L, dxy, Ct, Cs, zc_all, zs_all, P;
+    T.alloc((size_t)(g.Nx / 2) * (g.Ny / 2) * g.Nz);
+    green_invk2(s, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, T.p);
+    const int n_tg = ncol * n_az;                  // target lateral groups
+    std::vector<double> hdxy;
+    for (int k = 0; k < ncol; ++k)
+        for (int a = 0; a < n_az; ++a) {
+            const double th = c->opts.az0 + 2.0 * kPi * a / n_az;
+            const double tx = c->cols[k].x + c->cols[k].radius * std::cos(th);
+            const double ty = c->cols[k].y + c->cols[k].radius * std::sin(th);
+            for (int k2 = 0; k2 < ncol; ++k2) {
+                hdxy.push_back(tx - c->cols[k2].x);
+                hdxy.push_back(ty - c->cols[k2].y);
+            }
+        }
+    const int n_combo = n_tg * ncol;
+    dxy.upload(hdxy.data(), hdxy.size(), s);
+    L.alloc((size_t)n_combo * g.Nz);
+    green_lateral(s, dxy.p, n_combo, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, T.p, L.p);
+    T.release();
+    // cos tables: collocation heights per column (n_h M_c each), source heights
+    std::vector<double> hzc;
+    std::vector<int> ct_off(ncol + 1, 0);
+    for (int k = 0; k < ncol; ++k) {
+        const wt_column& col = c->cols[k];
+        const int nh = c->opts.n_h * col.n_sources;
+        for (int p = 0; p < nh; ++p) hzc.push_back(col.z0 + (p + 0.5) * (col.z1 - col.z0) / nh);
+        ct_off[k + 1] = ct_off[k] + nh;
+    }
+    zc_all.upload(hzc.data(), hzc.size(), s);
+    zs_all.upload(c->src_z.data(), ns, s);
+    Ct.alloc(hzc.size() * g.Nz);
+    Cs.alloc((size_t)ns * g.Nz);
+    green_cos_table(s, zc_all.p, (int)hzc.size(), g.Nz, g.Lz, Ct.p);
+    green_cos_table(s, zs_all.p, ns, g.Nz, g.Lz, Cs.p);
+    std::vector<unsigned char> blocks(pblock_size() * (size_t)n_combo);
+    int max_rows = 0, max_cols = 0;
+    for (int k = 0; k < ncol; ++k)
+        for (int a = 0; a < n_az; ++a)
+            for (int k2 = 0; k2 < ncol; ++k2) {
+                const int tg = k * n_az + a;
+                const int nh = c->opts.n_h * c->cols[k].n_sources;
+                const int row0 = c->colloc_off[k] + a * nh;
+                pack_pblock(blocks.data() + pblock_size() * (size_t)(tg * ncol + k2), row0, nh, c->col_off[k2],
+                            c->cols[k2].n_sources, ct_off[k], c->col_off[k2], tg * ncol + k2);
+                max_rows = std::max(max_rows, nh);
+                max_cols = std::max(max_cols, c->cols[k2].n_sources);
+            }
+    DBuf<unsigned char> dblocks;
+    dblocks.upload(blocks.data(), blocks.size(), s);
+    P.alloc((size_t)nc * ns);
+    green_pblocks(s, dblocks.p, n_combo, max_rows, max_cols, Ct.p, Cs.p, L.p, g.Nz, c->pref, P.p, ns);
+    Ct.release(); Cs.release(); L.release();
+
+    // --- S3: neutral basis (Householder), offset column, column scaling
+    std::vector<double> hv(ns, 1.0);
+    hv[0] += std::sqrt((double)ns);
+    double vtv = 0;
+    for (double x : hv) vtv += x * x;
+    c->beta = 2.0 / vtv;
+    c->hv.upload(hv.data(), ns, s);
+    DBuf<double> w, dcol;
+    w.alloc(nc);
+    dgemv(s, false, nc, ns, 1.0, P.p, ns, c->hv.p, 0.0, w.p);
+    rank1(s, nc, ns, -c->beta, w.p, c->hv.p, P.p, ns);     // P H
+    set_column(s, P.p, nc, ns, 0, 1.0);                     // A = [1 | P B]
+    w.release();
+    dcol.alloc(ns);
+    column_norms(s, P.p, nc, ns, ns, dcol.p);
+    std::vector<double> hd(ns);
+    dcol.download(hd.data(), ns, s);
+    WT_CUDA(cudaStreamSynchronize(s));
+    double max_sq = 0;
+    for (int k = 0; k < ns; ++k) {
+        if (!(hd[k] > 0.0) || !std::isfinite(hd[k])) fail(WT_ERR_ILL_CONDITIONED, "zero or non-finite fit column");
+        if (k > 0) max_sq = std::max(max_sq, hd[k] * hd[k]);
+        hd[k] = 1.0 / hd[k];
+    }
+    dcol.upload(hd.data(), ns, s);
+    scale_columns(s, P.p, nc, ns, ns, dcol.p);               // A_s = A D
+
+    // normal matrix G = A_s^T A_s (+ ridge on the charge part)
+    DBuf<double> G, R, Y;
+    G.alloc((size_t)ns * ns);
+    dgemm(s, true, false, ns, ns, nc, 1.0, P.p, ns, P.p, ns, 0.0, G.p, ns, true);
+    symmetrize_from_lower(s, G.p, ns, ns);
+    if (c->opts.tikhonov > 0.0) {
+        std::vector<double> ridge(ns, 0.0);
+        for (int k = 1; k < ns; ++k) ridge[k] = c->opts.tikhonov * max_sq * hd[k] * hd[k];
+        DBuf<double> dr;
+        dr.upload(ridge.data(), ns, s);
+        // G[k][k] += ridge[k]: a rank-1 of diagonal form via a strided axpy
+        DBuf<double> diag;
+        diag.alloc(ns);
+        get_diag(s, G.p, ns, ns, diag.p);
+        axpy(s, ns, 1.0, dr.p, diag.p);
+        copy_block(s, diag.p, 1, G.p, ns + 1, ns, 1);
+    }
+    // right-hand sides R = A_s^T S
+    DBuf<int> sp, si;
+    DBuf<double> sw;
+    sp.upload(c->s_ptr.data(), c->s_ptr.size(), s);
+    si.upload(c->s_idx.data(), c->s_idx.size(), s);
+    sw.upload(c->s_w.data(), c->s_w.size(), s);
+    R.alloc((size_t)ns * ns);
+    Y.alloc((size_t)ns * ns);
+    fit_ats(s, P.p, ns, nc, ns, sp.p, si.p, sw.p, ns, Y.p);   // Y = R^T
+    transpose(s, Y.p, ns, ns, R.p);
+    // --- S4: Cholesky and solves, one step of corrected semi-normal equations
+    cholesky(s, G.p, ns, ns, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_NOT_SPD, "normal matrix of the fit is not positive definite (rank-deficient fit)");
+    copy_block(s, R.p, ns, Y.p, ns, ns, ns);
+    trsm_lower(s, G.p, ns, ns, Y.p, ns, ns);
+    trsm_lower_t(s, G.p, ns, ns, Y.p, ns, ns);
+    {
+        DBuf<double> Res;
+        Res.alloc((size_t)nc * ns);
+        dgemm(s, false, false, nc, ns, ns, -1.0, P.p, ns, Y.p, ns, 0.0, Res.p, ns);
+        fit_add_s(s, Res.p, ns, ns, sp.p, si.p, sw.p, 1.0);
+        dgemm(s, true, false, ns, ns, nc, 1.0, P.p, ns, Res.p, ns, 0.0, R.p, ns);
+        trsm_lower(s, G.p, ns, ns, R.p, ns, ns);
+        trsm_lower_t(s, G.p, ns, ns, R.p, ns, ns);
+        axpy(s, (size_t)ns * ns, 1.0, R.p, Y.p);
+    }
+    // DC boundary residual || A_s (Y phi) - S phi || / || S phi ||
+    {
+        DBuf<double> dphi, yphi, r;
+        dphi.upload(c->phi_dc.data(), ns, s);
+        yphi.alloc(ns);
+        r.alloc(nc);
+        dgemv(s, false, ns, ns, 1.0, Y.p, ns, dphi.p, 0.0, yphi.p);
+        dgemv(s, false, nc, ns, 1.0, P.p, ns, yphi.p, 0.0, r.p);
+        std::vector<double> hr(nc), sphi(nc, 0.0);
+        r.download(hr.data(), nc, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < ns; ++j)
+            for (int e = c->s_ptr[j]; e < c->s_ptr[j + 1]; ++e) sphi[c->s_idx[e]] += c->s_w[e] * c->phi_dc[j];
+        double num = 0, den = 0;
+        for (int i = 0; i < nc; ++i) { num += (hr[i] - sphi[i]) * (hr[i] - sphi[i]); den += sphi[i] * sphi[i]; }
+        c->info.boundary_residual = den > 0 ? std::sqrt(num / den) : 0.0;
+    }
+    // condition estimate from the Cholesky diagonal of the scaled normal matrix
+    {
+        DBuf<double> dg;
+        dg.alloc(ns);
+        get_diag(s, G.p, ns, ns, dg.p);
+        std::vector<double> h(ns);
+        dg.download(h.data(), ns, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+        double mx = 0, mn = 1e300;
+        for (double x : h) { mx = std::max(mx, std::fabs(x)); mn = std::min(mn, std::fabs(x)); }
+        c->info.cond_estimate = mn > 0 ? mx / mn : INFINITY;
+    }
+    G.release();
+    P.release();
+    // X = D Y; offsets = row 0; F = H [0; X_1:]
+    scale_rows(s, Y.p, ns, ns, ns, dcol.p);
+    c->offset.alloc(ns);
+    copy_block(s, Y.p, ns, c->offset.p, ns, 1, ns);
+    fill(s, Y.p, ns, 0.0);
+    DBuf<double> u;
+    u.alloc(ns);
+    dgemv(s, true, ns, ns, 1.0, Y.p, ns, c->hv.p, 0.0, u.p);
+    rank1(s, ns, ns, -c->beta, c->hv.p, u.p, Y.p, ns);      // F in Y
+    c->Cn.alloc((size_t)ns * ns);
+    symmetrize_avg(s, Y.p, c->Cn.p, ns);
+    transpose(s, Y.p, ns, ns, R.p);
+    double nF = dnrm2(s, Y.p, (size_t)ns * ns, c->d_scr.p);
+    axpy(s, (size_t)ns * ns, -1.0, Y.p, R.p);
+    double nA = dnrm2(s, R.p, (size_t)ns * ns, c->d_scr.p);
+    c->info.asymmetry = nF > 0 ? nA / nF : 0.0;
+    check_finite(s, c->Cn.p, (size_t)ns * ns, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_NAN, "non-finite capacitance");
+    c->info.n_columns = ncol;
+    c->info.n_sources = ns;
+    c->info.n_colloc = nc;
+    c->info.fit_seconds = secs(t0);
+}
+
+// Q [ns][nt] = q(t_n) = q_inf + Cn H [0; V (amp * exp(-mu t_n))] for device times.
+void charges_at(wt_ctx* c, const double* d_t, int nt, double* Q) {
+    cudaStream_t s = c->s;
+    const int ns = c->ns, n1 = ns - 1;
+    DBuf<double> E, Zf, vz;
+    E.alloc((size_t)n1 * nt);
+    modal_factors(s, c->amp.p, c->mu.p, n1, d_t, nt, E.p);
+    Zf.alloc((size_t)ns * nt);
+    Zf.zero(s);
+    dgemm(s, false, false, n1, nt, n1, 1.0, c->Vm.p, n1, E.p, nt, 0.0, Zf.p + nt, nt);
+    vz.alloc(nt);
+    dgemv(s, true, ns, nt, 1.0, Zf.p, nt, c->hv.p, 0.0, vz.p);
+    rank1(s, ns, nt, -c->beta, c->hv.p, vz.p, Zf.p, nt);
+    dgemm(s, false, false, ns, nt, ns, 1.0, c->Cn.p, ns, Zf.p, nt, 0.0, Q, nt);
+    add_column_vector(s, Q, ns, nt, c->qinf.p);
+}
+
+void do_relax(wt_ctx* c, const double* t, int nt) {
+    auto t0 = clk::now();
+    cudaStream_t s = c->s;
+    const int ns = c->ns, n1 = ns - 1;
+    if (n1 < 1) fail(WT_ERR_GEOMETRY, "need at least two sources");
+    clear_err(c);
+    c->times.assign(t, t + nt);
+    // resistive lines (Sec. 5): G_seg = pi r^2 / (rho Delta), terminal 2 G_seg
+    std::vector<double> diag(ns, 0.0), off(ns, 0.0), k1(ns, 0.0);
+    for (size_t k = 0; k < c->cols.size(); ++k) {
+        const wt_column& col = c->cols[k];
+        const int m = col.n_sources, o = c->col_off[k];
+        const double dz = (col.z1 - col.z0) / m;
+        const double gs = kPi * col.radius * col.radius / (col.resistivity * dz);
+        for (int j = 0; j + 1 < m; ++j) {
+            off[o + j] = gs;
+            diag[o + j] -= gs;
+            diag[o + j + 1] -= gs;
+        }
+        const int jt = o + (col.terminal_top ? m - 1 : 0);
+        diag[jt] -= 2.0 * gs;
+        k1[jt] = -2.0 * gs;                 // K 1: only the terminal leak survives
+    }
+    double s1 = 0;
+    for (double x : k1) s1 += x;
+    DBuf<double> dd, doff, dk1, K, Am, Sm;
+    dd.upload(diag.data(), ns, s);
+    doff.upload(off.data(), ns, s);
+    dk1.upload(k1.data(), ns, s);
+    K.alloc((size_t)ns * ns);
+    build_k(s, dd.p, doff.p, ns, K.p);
+    rank1(s, ns, ns, -1.0 / s1, dk1.p, dk1.p, K.p, ns);     // K~ = K - K1 1^T K / (1^T K 1)
+    // reduced pencil on the neutral subspace: Am = (H Cn H)[1:,1:], Sm = -(H K~ H)[1:,1:]
+    DBuf<double> HC;
+    HC.alloc((size_t)ns * ns);
+    copy_block(s, c->Cn.p, ns, HC.p, ns, ns, ns);
+    householder_two_sided(c, HC.p, ns);
+    householder_two_sided(c, K.p, ns);
+    Am.alloc((size_t)n1 * n1);
+    Sm.alloc((size_t)n1 * n1);
+    copy_block(s, HC.p + ns + 1, ns, Am.p, n1, n1, n1);
+    copy_block(s, K.p + ns + 1, ns, Sm.p, n1, n1, n1);
+    HC.release();
+    K.release();
+    dscal(s, (size_t)n1 * n1, -1.0, Sm.p);                  // Sm = -B^T K~ B
+    {
+        DBuf<double> tmp;
+        tmp.alloc((size_t)n1 * n1);
+        symmetrize_avg(s, Am.p, tmp.p, n1);
+        copy_block(s, tmp.p, n1, Am.p, n1, n1, n1);
+        symmetrize_avg(s, Sm.p, tmp.p, n1);
+        copy_block(s, tmp.p, n1, Sm.p, n1, n1, n1);
+    }
+    // Cholesky of the capacitance pencil side
+    cholesky(s, Am.p, n1, n1, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_NOT_SPD, "fitted capacitance is not positive definite on the neutral subspace");
+    // Shat = L^-1 Sm L^-T (symmetric positive definite)
+    DBuf<double> Y, Yt;
+    Y.alloc((size_t)n1 * n1);
+    Yt.alloc((size_t)n1 * n1);
+    copy_block(s, Sm.p, n1, Y.p, n1, n1, n1);
+    trsm_lower(s, Am.p, n1, n1, Y.p, n1, n1);
+    transpose(s, Y.p, n1, n1, Yt.p);
+    trsm_lower(s, Am.p, n1, n1, Yt.p, n1, n1);
+    symmetrize_avg(s, Yt.p, Y.p, n1);
+    c->mu.alloc(n1);
+    DBuf<double> U;
+    U.alloc((size_t)n1 * n1);
+    int sweeps = jacobi_eig(s, Y.p, n1, c->mu.p, U.p, c->d_err.p);
+    (void)sweeps;
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver did not converge");
+    trsm_lower_t(s, Am.p, n1, n1, U.p, n1, n1);              // V = L^-T U
+    Y.release(); Yt.release(); Sm.release();
+    std::vector<double> hmu(n1);
+    c->mu.download(hmu.data(), n1, s);
+    WT_CUDA(cudaStreamSynchronize(s));
+    double mn = 1e300, mx = -1e300;
+    for (double x : hmu) { mn = std::min(mn, x); mx = std::max(mx, x); }
+    if (!(mn > 0.0)) fail(WT_ERR_NOT_SPD, "non-positive relaxation rate (resistive pencil not definite)");
+    c->info.mu_min = mn;
+    c->info.mu_max = mx;
+    // q_inf = Cn phi_DC; amplitudes amp = V^T B^T (-q_inf)
+    DBuf<double> dphi, g;
+    dphi.upload(c->phi_dc.data(), ns, s);
+    c->qinf.alloc(ns);
+    dgemv(s, false, ns, ns, 1.0, c->Cn.p, ns, dphi.p, 0.0, c->qinf.p);
+    std::vector<double> hq(ns), hv(ns);
+    c->qinf.download(hq.data(), ns, s);
+    c->hv.download(hv.data(), ns, s);
+    WT_CUDA(cudaStreamSynchronize(s));
+    double vq = 0;
+    for (int i = 0; i < ns; ++i) vq += hv[i] * hq[i];
+    std::vector<double> hg(n1);
+    for (int i = 1; i < ns; ++i) hg[i - 1] = -(hq[i] - c->beta * hv[i] * vq);
+    g.upload(hg.data(), n1, s);
+    c->amp.alloc(n1);
+    dgemv(s, true, n1, n1, 1.0, U.p, n1, g.p, 0.0, c->amp.p);
+    c->Vm.alloc((size_t)n1 * n1);
+    copy_block(s, U.p, n1, c->Vm.p, n1, n1, n1);
+    U.release();
+    // q(t_n) = q_inf + Cn H [0; V (amp * exp(-mu t_n))]
+    c->d_times.upload(t, nt, s);
+    DBuf<double> Q;
+    Q.alloc((size_t)ns * nt);
+    charges_at(c, c->d_times.p, nt, Q.p);
+    c->Qt.alloc((size_t)nt * ns);
+    transpose(s, Q.p, ns, nt, c->Qt.p);
+    check_finite(s, c->Qt.p, (size_t)nt * ns, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_NAN, "non-finite charges");
+    // S5b: time basis of the charge history (Gram matrix + Jacobi)
+    {
+        DBuf<double> Gt, Wg, lam;
+        Gt.alloc((size_t)nt * nt);
+        dgemm(s, true, false, nt, nt, ns, 1.0, Q.p, nt, Q.p, nt, 0.0, Gt.p, nt);
+        Wg.alloc((size_t)nt * nt);
+        lam.alloc(nt);
+        jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p);
+        if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver (time basis) did not converge");
+        std::vector<double> hl(nt), hw((size_t)nt * nt);
+        lam.download(hl.data(), nt, s);
+        Wg.download(hw.data(), (size_t)nt * nt, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+        std::vector<int> ord(nt);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return hl[a] > hl[b]; });
+        const double s0 = std::sqrt(std::max(hl[ord[0]], 0.0));
+        const int r_max = std::min(32, nt);
+        int r = 0;
+        while (r < r_max && std::sqrt(std::max(hl[ord[r]], 0.0)) > 1e-9 * s0) ++r;
+        if (r < 1) r = 1;
+        c->rank = r;
+        c->r_pad = 32;
+        c->info.trunc_rel = (r < nt && s0 > 0) ? std::sqrt(std::max(hl[ord[r]], 0.0)) / s0 : 0.0;
+        // basis charges u_m = Q w_m / sigma_m ([r][ns]); coefficients sigma_m w_m[t]
+        std::vector<double> wsel((size_t)nt * r), coef((size_t)nt * c->r_pad, 0.0);
+        for (int m = 0; m < r; ++m) {
+            const double sg = std::sqrt(std::max(hl[ord[m]], 0.0));
+            for (int tt = 0; tt < nt; ++tt) {
+                const double wv = hw[(size_t)tt * nt + ord[m]];
+                wsel[(size_t)tt * r + m] = sg > 0 ? wv / sg : 0.0;
+                coef[(size_t)tt * c->r_pad + m] = sg * wv;
+            }
+        }
+        DBuf<double> dws, Ubt, dcoef;
+        dws.upload(wsel.data(), wsel.size(), s);
+        Ubt.alloc((size_t)ns * r);
+        dgemm(s, false, false, ns, r, nt, 1.0, Q.p, nt, dws.p, r, 0.0, Ubt.p, r);
+        c->Ub.alloc((size_t)r * ns);
+        transpose(s, Ubt.p, ns, r, c->Ub.p);
+        dcoef.upload(coef.data(), coef.size(), s);
+        c->W32.alloc(coef.size());
+        to_float(s, dcoef.p, coef.size(), 1.0, c->W32.p);
+        WT_CUDA(cudaStreamSynchronize(s));
+    }
+    c->info.n_t = nt;
+    c->info.rank = c->rank;
+    c->info.relax_seconds = secs(t0);
+}
+
+void ensure_spectral(wt_ctx* c) {
+    if (c->sp_ready) return;
+    const wt_grid& g = c->grid;
+    GridDev gd{g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, c->pref};
+    std::vector<double> xy;
+    for (auto& col : c->cols) { xy.push_back(col.x); xy.push_back(col.y); }
+    c->sp32.init(gd, xy, c->s);
+    c->sp64.init(gd, xy, c->s);
+    c->d_zsrc.upload(c->src_z.data(), c->ns, c->s);
+    c->d_col_off.upload(c->col_off.data(), c->col_off.size(), c->s);
+    WT_CUDA(cudaStreamSynchronize(c->s));
+    c->sp_ready = true;
+}
+
+void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t us) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int nt = (int)c->times.size();
+    const size_t esz = prec == WT_FP64 ? 8 : 4;
+    const size_t need = (size_t)nt * 3 * npts * esz;
+    if (!H) fail(WT_ERR_ARG, "H is NULL");
+    if (bytes < need) fail(WT_ERR_ARG, "H_bytes too small: need " + std::to_string(need));
+    ensure_spectral(c);
+    const bool dev = is_device_ptr(H);
+    cudaStream_t s = us;
+    if (!dev) {  // compute into an internal buffer on the context stream, then copy out
+        s = c->s;
+        if (prec == WT_FP64) c->stage64.alloc((size_t)nt * 3 * npts);
+        else c->stage32.alloc((size_t)nt * 3 * npts);
+    }
+    const int ncol = (int)c->cols.size();
+    if (c->timing) {
+        for (int k = 0; k < 4; ++k)
+            if (!c->ev[k]) WT_CUDA(cudaEventCreate(&c->ev[k]));
+        WT_CUDA(cudaEventRecord(c->ev[0], s));
+    }
+    int launches = 0;
+    if (prec == WT_FP64) {
+        double* out = dev ? static_cast<double*>(H) : c->stage64.p;
+        const int nb = 4;
+        c->Zc64.alloc((size_t)nb * ncol * g.Nz);
+        c->G64.alloc(c->sp64.scratch_elems(nb));
+        for (int t0 = 0; t0 < nt; t0 += nb) {
+            const int b = std::min(nb, nt - t0);
+            column_ztransform<double>(s, c->Qt.p + (size_t)t0 * c->ns, b, c->ns, c->ns, c->d_zsrc.p, c->d_col_off.p,
+                                      ncol, g.Nz, g.Lz, c->Zc64.p);
+            c->sp64.fields(c->Zc64.p, b, c->G64.p, out + (size_t)t0 * 3 * npts, 3 * npts, npts, s);
+            launches += 4;
+        }
+        if (c->timing) {
+            WT_CUDA(cudaEventRecord(c->ev[1], s));
+            WT_CUDA(cudaEventRecord(c->ev[2], s));
+            WT_CUDA(cudaEventRecord(c->ev[3], s));
+        }
+    } else {
+        float* out = dev ? static_cast<float*>(H) : c->stage32.p;
+        const int r = c->rank, rp = c->r_pad;
+        const int nb = 2;
+        c->Zc32.alloc((size_t)rp * ncol * g.Nz);
+        c->G32.alloc(c->sp32.scratch_elems(nb));
+        c->E32.alloc((size_t)3 * rp * npts);
+        if (r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
+        column_ztransform<float>(s, c->Ub.p, r, c->ns, c->ns, c->d_zsrc.p, c->d_col_off.p, ncol, g.Nz, g.Lz,
+                                 c->Zc32.p);
+        launches += 1;
+        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
+        for (int m0 = 0; m0 < r; m0 += nb) {
+            const int b = std::min(nb, r - m0);
+            c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->G32.p, c->E32.p + (size_t)m0 * npts, npts,
+                           (size_t)rp * npts, s);
+            launches += 3;
+        }
+        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
+        if (c->use_tc && expand_tc_available()) expand_tc(s, c->E32.p, rp, c->W32.p, nt, npts, out, c->d_err.p);
+        else expand_simt(s, c->E32.p, rp, c->W32.p, nt, rp, npts, out);
+        launches += 1;
+        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[3], s));
+    }
+    c->last_launches = launches;
+    c->ev_recorded = c->timing;
+    if (!dev) {
+        const void* src = prec == WT_FP64 ? (const void*)c->stage64.p : (const void*)c->stage32.p;
+        WT_CUDA(cudaMemcpyAsync(H, src, need, cudaMemcpyDeviceToHost, s));
+        WT_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+
+void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, double* out) {
+    ensure_spectral(c);
+    cudaStream_t s = c->s;
+    const wt_grid& g = c->grid;
+    const int ns = c->ns, ncol = (int)c->cols.size();
+    for (int i = 0; i < nt; ++i)
+        if (!(t[i] >= 0.0) || !std::isfinite(t[i])) fail(WT_ERR_ARG, "sample times must be finite and >= 0");
+    for (int i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(xyz[i])) fail(WT_ERR_NAN, "non-finite sample point");
+    DBuf<double> dt_, Q, Qt, Zc, T, Lat, pts, o;
+    dt_.upload(t, nt, s);
+    Q.alloc((size_t)ns * nt);
+    charges_at(c, dt_.p, nt, Q.p);
+    Qt.alloc((size_t)nt * ns);
+    transpose(s, Q.p, ns, nt, Qt.p);
+    Zc.alloc((size_t)nt * ncol * g.Nz);
+    column_ztransform<double>(s, Qt.p, nt, ns, ns, c->d_zsrc.p, c->d_col_off.p, ncol, g.Nz, g.Lz, Zc.p);
+    T.alloc((size_t)(g.Nx / 2) * (g.Ny / 2) * g.Nz);
+    green_invk2(s, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, T.p);
+    const int chunk = 512;
+    Lat.alloc((size_t)std::min(n, chunk) * ncol * g.Nz * 3);
+    o.alloc((size_t)nt * std::min(n, chunk) * 3);
+    std::vector<double> hbuf;
+    for (int p0 = 0; p0 < n; p0 += chunk) {
+        const int np = std::min(chunk, n - p0);
+        pts.upload(xyz + 3 * (size_t)p0, 3 * (size_t)np, s);
+        sample_lateral(s, pts.p, np, c->sp64.col_xy.p, ncol, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, T.p, Lat.p);
+        sample_contract(s, pts.p, Lat.p, Zc.p, np, nt, ncol, g.Nz, g.Lz, c->pref, o.p);
+        hbuf.resize((size_t)nt * np * 3);
+        o.download(hbuf.data(), hbuf.size(), s);
+        WT_CUDA(cudaStreamSynchronize(s));
+        for (int tt = 0; tt < nt; ++tt)
+            std::memcpy(out + ((size_t)tt * n + p0) * 3, hbuf.data() + (size_t)tt * np * 3, sizeof(double) * np * 3);
+    }
+}
+
+void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStream_t us) {
+    const wt_grid& g = c->grid;
+    const int nt = (int)c->times.size();
+    if (!H || !tr || !iout) fail(WT_ERR_ARG, "NULL argument");
+    if (!is_device_ptr(H)) fail(WT_ERR_ARG, "H must be device memory (FP32 output of wt_extend)");
+    if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
+        fail(WT_ERR_ARG, "bad track sizes or dt");
+    if (!tr->x || !tr->y || !tr->z || !tr->vx || !tr->vy || !tr->vz) fail(WT_ERR_ARG, "NULL track array");
+    if (tr->n_tracks == 0) return;
+    const size_t nts = (size_t)tr->n_tracks * tr->n_steps;
+    const bool dev_in = is_device_ptr(tr->x);
+    const bool dev_out = is_device_ptr(iout);
+    cudaStream_t s = (dev_in && dev_out) ? us : c->s;
+    const float* arr[7] = {tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz, tr->q};
+    DBuf<float> staged[7];
+    if (!dev_in) {
+        for (int k = 0; k < 6; ++k) { staged[k].upload(arr[k], nts, s); arr[k] = staged[k].p; }
+        if (tr->q) { staged[6].upload(tr->q, tr->n_tracks, s); arr[6] = staged[6].p; }
+    }
+    // lag table: (k + 1/2) dt -> bracketing samples and weights (linear in t; 0 at t = 0; held at the end)
+    std::vector<unsigned char> lag(eq1_lag_size() * (size_t)tr->n_out);
+    const std::vector<double>& ts = c->times;
+    for (int k = 0; k < tr->n_out; ++k) {
+        const double L = (k + 0.5) * tr->dt;
+        int n0 = 0;
+        double w0 = 0, w1 = 0;
+        if (L <= ts.front()) { n0 = 0; w0 = L / ts.front(); }
+        else if (L >= ts.back()) { n0 = nt - 1; w0 = 1.0; }
+        else {
+            n0 = (int)(std::upper_bound(ts.begin(), ts.end(), L) - ts.begin()) - 1;
+            const double f = (L - ts[n0]) / (ts[n0 + 1] - ts[n0]);
+            w0 = 1.0 - f;
+            w1 = f;
+        }
+        eq1_pack_lag(lag.data() + eq1_lag_size() * k, n0, (float)w0, (float)w1);
+    }
+    DBuf<unsigned char> dlag;
+    dlag.upload(lag.data(), lag.size(), s);
+    DBuf<float> dout;
+    float* o = iout;
+    if (!dev_out) { dout.alloc((size_t)tr->n_tracks * tr->n_out); o = dout.p; }
+    eq1_launch(s, static_cast<const float*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, arr[0], arr[1], arr[2], arr[3],
+               arr[4], arr[5], tr->q ? arr[6] : nullptr, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out,
+               tr->dt, c->opts.v_w, dlag.p, o);
+    if (!dev_out) dout.download(iout, (size_t)tr->n_tracks * tr->n_out, s);
+    // staged inputs and the lag table are freed on return: finish first
+    WT_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+extern "C" {
+
+wt_status wt_create(wt_ctx** out, const wt_grid* grid, int cuda_device) {
+    return run(nullptr, "wt_create", [&] {
+        if (!out || !grid) fail(WT_ERR_ARG, "NULL argument");
+        *out = nullptr;
+        const wt_grid& g = *grid;
+        if (!(g.Lx > 0 && g.Ly > 0 && g.Lz > 0) || g.Nx < 4 || g.Ny < 4 || g.Nz < 2 || !(g.eps_r > 0))
+            fail(WT_ERR_ARG, "grid sizes must be positive (Nx, Ny >= 4, Nz >= 2)");
+        if ((g.Nx & 1) || (g.Ny & 1)) fail(WT_ERR_ARG, "Nx and Ny must be even");
+        if (g.zbc != WT_Z_MIRROR) fail(WT_ERR_UNSUPPORTED, "only the mirror z boundary is implemented");
+        make_plan(2 * g.Nz);
+        make_plan(g.Nx);
+        make_plan(g.Ny);
+        int ndev = 0;
+        WT_CUDA(cudaGetDeviceCount(&ndev));
+        if (cuda_device < 0 || cuda_device >= ndev) fail(WT_ERR_ARG, "no such CUDA device");
+        WT_CUDA(cudaSetDevice(cuda_device));
+        wt_ctx* c = new wt_ctx();
+        c->dev = cuda_device;
+        if (const char* e = std::getenv("WT_EXPAND")) c->use_tc = std::strcmp(e, "simt") != 0;
+        c->grid = g;
+        try {
+            WT_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+            c->d_err.alloc(16);
+            c->d_err.zero(c->s);
+            c->d_scr.alloc(16);
+        } catch (...) {
+            if (c->s) cudaStreamDestroy(c->s);
+            delete c;
+            throw;
+        }
+        *out = c;
+    });
+}
+
+wt_status wt_add_columns(wt_ctx* ctx, const wt_column* cols, int n) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_add_columns", [&] {
+        if (ctx->stage != 0) fail(WT_ERR_STATE, "columns must be added before wt_fit");
+        if (n < 0 || (n > 0 && !cols)) fail(WT_ERR_ARG, "bad column array");
+        for (int i = 0; i < n; ++i) ctx->cols.push_back(cols[i]);
+    });
+}
+
+wt_status wt_fit(wt_ctx* ctx, const wt_fit_opts* opts, double* cond_out) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_fit", [&] {
+        if (ctx->stage != 0) fail(WT_ERR_STATE, "wt_fit already called");
+        wt_fit_opts o{4, 2, 0.0, 1.0, 0.0};
+        if (opts) o = *opts;
+        if (o.n_az < 1 || o.n_h < 1 || !(o.tikhonov >= 0) || !(o.v_w != 0) || !std::isfinite(o.az0))
+            fail(WT_ERR_ARG, "bad fit options");
+        ctx->opts = o;
+        do_fit(ctx);
+        ctx->stage = 1;
+        if (cond_out) *cond_out = ctx->info.cond_estimate;
+    });
+}
+
+wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_relax", [&] {
+        if (ctx->stage < 1) fail(WT_ERR_STATE, "wt_relax needs wt_fit first");
+        if (!t || n_t < 1) fail(WT_ERR_ARG, "need at least one time sample");
+        for (int i = 0; i < n_t; ++i) {
+            if (!(t[i] > 0.0) || !std::isfinite(t[i])) fail(WT_ERR_ARG, "times must be finite and > 0");
+            if (i && !(t[i] > t[i - 1])) fail(WT_ERR_ARG, "times must increase");
+        }
+        do_relax(ctx, t, n_t);
+        ctx->stage = 2;
+    });
+}
+
+wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_extend", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_extend needs wt_relax first");
+        if (prec != WT_FP32 && prec != WT_FP64) fail(WT_ERR_ARG, "bad precision");
+        do_extend(ctx, prec, H, H_bytes, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wt_status wt_sample_H(wt_ctx* ctx, const double* xyz, int n, const double* t, int n_t, double* out) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_sample_H", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_sample_H needs wt_relax first");
+        if (n < 0 || n_t < 0 || (n && !xyz) || (n_t && !t) || (n && n_t && !out)) fail(WT_ERR_ARG, "bad arguments");
+        if (n == 0 || n_t == 0) return;
+        do_sample(ctx, xyz, n, t, n_t, out);
+    });
+}
+
+wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1 needs wt_relax first");
+        do_eq1(ctx, H, tracks, i, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wt_status wt_get_charges(wt_ctx* ctx, double* q) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_charges", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "no charges before wt_relax");
+        if (!q) fail(WT_ERR_ARG, "NULL output");
+        ctx->Qt.download(q, ctx->times.size() * (size_t)ctx->ns, ctx->s);
+        WT_CUDA(cudaStreamSynchronize(ctx->s));
+    });
+}
+
+wt_status wt_get_capacitance(wt_ctx* ctx, double* cn) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_capacitance", [&] {
+        if (ctx->stage < 1) fail(WT_ERR_STATE, "no capacitance before wt_fit");
+        if (!cn) fail(WT_ERR_ARG, "NULL output");
+        ctx->Cn.download(cn, (size_t)ctx->ns * ctx->ns, ctx->s);
+        WT_CUDA(cudaStreamSynchronize(ctx->s));
+    });
+}
+
+wt_status wt_get_modes(wt_ctx* ctx, double* mu) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_modes", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "no modes before wt_relax");
+        if (!mu) fail(WT_ERR_ARG, "NULL output");
+        ctx->mu.download(mu, ctx->ns - 1, ctx->s);
+        WT_CUDA(cudaStreamSynchronize(ctx->s));
+    });
+}
+
+wt_status wt_get_info(wt_ctx* ctx, wt_info* info) {
+    if (!ctx || !info) return WT_ERR_ARG;
+    *info = ctx->info;
+    return WT_OK;
+}
+
+wt_status wt_set_timing(wt_ctx* ctx, int enable) {
+    if (!ctx) return WT_ERR_ARG;
+    ctx->timing = enable != 0;
+    return WT_OK;
+}
+
+wt_status wt_get_timing(wt_ctx* ctx, double* ms3, int* n_launches) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_timing", [&] {
+        if (!ms3) fail(WT_ERR_ARG, "NULL output");
+        if (!ctx->ev_recorded) fail(WT_ERR_STATE, "no timed wt_extend (call wt_set_timing(ctx, 1) first)");
+        for (int k = 1; k < 4; ++k) {
+            WT_CUDA(cudaEventSynchronize(ctx->ev[k]));
+            float ms = 0.f;
+            WT_CUDA(cudaEventElapsedTime(&ms, ctx->ev[k - 1], ctx->ev[k]));
+            ms3[k - 1] = ms;
+        }
+        if (n_launches) *n_launches = ctx->last_launches;
+    });
+}
+
+const char* wt_last_error(const wt_ctx* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+void wt_destroy(wt_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->s) cudaStreamSynchronize(ctx->s);
+    cudaStream_t s = ctx->s;
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    if (s) cudaStreamDestroy(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/wt.h"
+
+namespace wt {
+
+constexpr double kEps0 = 8.8541878128e-12;   // vacuum permittivity [F/m]
+constexpr double kPi = 3.14159265358979323846;
+
+// Device error words (ctx->d_err[i]); a kernel that detects a failure sets
+// the word with atomicMax so the host sees the most severe code.
+enum DeviceErr : int {
+    DERR_NONE = 0,
+    DERR_NOT_SPD = 1,        // non-positive pivot in a Cholesky factorisation
+    DERR_NAN = 2,            // non-finite value
+    DERR_TIMEOUT = 3,        // a bounded wait gave up
+};
+
+struct Status {
+    wt_status code = WT_OK;
+    std::string msg;
+    bool ok() const { return code == WT_OK; }
+};
+
+// Throwing is confined to the library; the C entry points catch and convert.
+struct Error {
+    wt_status code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(wt_status code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define WT_CUDA(call) ::wt::cuda_check((call), #call)
+#define WT_LAUNCH(what) ::wt::cuda_check(cudaGetLastError(), what)
+
+// Owning device buffer.
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        if (count == n && p) return;
+        release();
+        if (count == 0) return;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            fail(WT_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+        }
+        n = count;
+    }
+    void zero(cudaStream_t s) { if (n) WT_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
+    void upload(const T* host, size_t count, cudaStream_t s) {
+        alloc(count);
+        if (count) WT_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void download(T* host, size_t count, cudaStream_t s) const {
+        if (count) WT_CUDA(cudaMemcpyAsync(host, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+};
+
+// ---------------------------------------------------------------- dense FP64
+// Row-major matrices.  op(A) is M x K, op(B) is K x N, C is M x N.
+void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+           bool lower_only = false);
+void symmetrize_from_lower(cudaStream_t s, double* A, int n, int lda);
+void symmetrize_avg(cudaStream_t s, const double* F, double* C, int n);   // C = (F + F^T)/2
+void transpose(cudaStream_t s, const double* A, int rows, int cols, double* At);
+// Lower Cholesky in place (upper triangle untouched).  Sets d_err on failure.
+void cholesky(cudaStream_t s, double* A, int n, int lda, int* d_err);
+// Solve L Y = B (lower) in place on B [n x nrhs].
+void trsm_lower(cudaStream_t s, const double* L, int n, int ldl, double* B, int nrhs, int ldb);
+// Solve L^T X = B in place on B.
+void trsm_lower_t(cudaStream_t s, const double* L, int n, int ldl, double* B, int nrhs, int ldb);
+// Symmetric eigendecomposition by parallel two-sided Jacobi: A (n x n,
+// destroyed) -> eigenvalues w[n] (unsorted), eigenvectors V (n x n, columns).
+// Returns the number of sweeps; sets d_err on non-convergence.
+int jacobi_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err, int max_sweeps = 40);
+// y = alpha * A x + beta * y  (A row-major M x N, or its transpose)
+void dgemv(cudaStream_t s, bool ta, int M, int N, double alpha, const double* A, int lda,
+           const double* x, double beta, double* y);
+double dnrm2(cudaStream_t s, const double* x, size_t n, double* d_scratch);
+void fill(cudaStream_t s, double* x, size_t n, double v);
+void axpy(cudaStream_t s, size_t n, double a, const double* x, double* y);
+void dscal(cudaStream_t s, size_t n, double a, double* x);
+// A[i][j] += alpha * u[i] * v[j]
+void rank1(cudaStream_t s, int M, int N, double alpha, const double* u, const double* v, double* A, int lda);
+void copy_block(cudaStream_t s, const double* src, int lds, double* dst, int ldd, int rows, int cols);
+void scale_columns(cudaStream_t s, double* A, int M, int N, int lda, const double* d);
+void scale_rows(cudaStream_t s, double* A, int M, int N, int lda, const double* d);
+void column_norms(cudaStream_t s, const double* A, int M, int N, int lda, double* out);
+void get_diag(cudaStream_t s, const double* A, int n, int lda, double* out);
+
+}  // namespace wt

@@ -1,0 +1,79 @@
+"""Object wrapper over the C ABI: one Sensor = one wt_ctx."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+
+class Sensor:
+    """Sensor(grid, columns, device=0); then fit() -> relax(times) -> extend()."""
+
+    def __init__(self, grid, columns, device: int = 0):
+        self.grid = grid
+        self.columns = list(columns)
+        self.device = device
+        self.ctx = B.wt_create(grid, device)
+        B.wt_add_columns(self.ctx, self.columns)
+        self.n_sources = sum(int(c.n_sources) for c in self.columns)
+        self.times = None
+
+    def fit(self, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0):
+        return B.wt_fit(self.ctx, n_az, n_h, tikhonov, v_w, az0)
+
+    def relax(self, times):
+        self.times = np.asarray(times, dtype=np.float64)
+        B.wt_relax(self.ctx, self.times)
+
+    def h_shape(self):
+        g = self.grid
+        return (len(self.times), 3, g.Nx, g.Ny, g.Nz)
+
+    def extend(self, precision="fp32", out=None, stream=None):
+        import torch
+        prec = B.WT_FP64 if precision in ("fp64", B.WT_FP64) else B.WT_FP32
+        if out is None:
+            dt = torch.float64 if prec == B.WT_FP64 else torch.float32
+            out = torch.empty(self.h_shape(), dtype=dt, device=f"cuda:{self.device}")
+        B.wt_extend(self.ctx, prec, out, stream)
+        return out
+
+    def sample_H(self, xyz, times):
+        return B.wt_sample_H(self.ctx, xyz, times)
+
+    def eq1(self, H, tracks, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((int(tracks["n_tracks"]), int(tracks["n_out"])), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        B.wt_eq1(self.ctx, H, tracks, out, stream)
+        return out
+
+    def charges(self):
+        return B.wt_get_charges(self.ctx, len(self.times), self.n_sources)
+
+    def capacitance(self):
+        return B.wt_get_capacitance(self.ctx, self.n_sources)
+
+    def modes(self):
+        return B.wt_get_modes(self.ctx, self.n_sources)
+
+    def info(self):
+        return B.wt_get_info(self.ctx)
+
+    def set_timing(self, enable=True):
+        B.wt_set_timing(self.ctx, enable)
+
+    def timing(self):
+        return B.wt_get_timing(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            B.wt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
