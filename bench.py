@@ -35,7 +35,19 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-WORKLOAD_NAME = "c2: 3x3 pixel cell 165x165x500 um, grid 128x128x256, 18 columns x 256 sources, 512 time samples"
+WORKLOADS = {
+    "c2": "c2: 3x3 pixel cell 165x165x500 um, grid 128x128x256, 18 columns x 256 sources, 512 time samples",
+    "c1": "c1: single cell 55x55x100 um, grid 32x32x64, 2 columns x 64 sources, 64 time samples",
+    "small": "small: single cell 55x55x100 um, grid 64x64x64, 2 columns x 64 sources, 512 time samples "
+             "(profiling case: H = 1.6 GB > L2)",
+}
+
+
+def make_workload(name):
+    import workloads as W
+    if name == "small":
+        return W.tiny_cell(nx=64, nz=64, n_t=512, radius=6e-6)
+    return W.workload(name)
 
 
 def peaks():
@@ -144,9 +156,8 @@ def run_reference(args):
     rank, local, world = dist_init()
     if rank != 0:
         return 0
-    import workloads as W
     import oracle as O
-    w = W.workload("c2")
+    w = make_workload(args.workload)
     t0 = time.perf_counter()
     sol = O.solve(w)
     setup = time.perf_counter() - t0
@@ -163,7 +174,7 @@ def run_reference(args):
             "unit": "point-samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": "4 time samples x 12^3 random subgrid per step"},
+            "config": {"workload": WORKLOADS[args.workload], "sample": "4 time samples x 12^3 random subgrid per step"},
             "cpu_baseline": {"value": v, "unit": "point-samples/s", "cores": cores, "kind": "oracle",
                              "sample": "4 time samples x 12^3 grid points per step; oracle setup excluded "
                                        f"({setup:.1f} s)"},
@@ -176,14 +187,13 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
-    import workloads as W
     import paper_2605_13987_gb300 as P
 
     rank, local, world = dist_init()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     P.load_library()
-    w = W.workload("c2")
+    w = make_workload(args.workload)
     g = w.grid
     npts = g.Nx * g.Ny * g.Nz
     nt = len(w.times)
@@ -209,6 +219,8 @@ def run_ours(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage_ms = []
     launches = 0
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStart()
     with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
         barrier(world)
         torch.cuda.synchronize()
@@ -222,6 +234,8 @@ def run_ours(args):
             launches += n
         torch.cuda.synchronize()
         barrier(world)
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, world)
@@ -234,15 +248,20 @@ def run_ours(args):
     achieved = alg_bytes / (exp_ms / 1e3) / 1e9
     traffic = None
     tr_file = os.path.join(ROOT, "profiles", "expand_tc_traffic.json")
-    if os.path.exists(tr_file):
+    if os.path.exists(tr_file) and args.workload == "c2":
+        # valid only while the kernel source is the one the counters were taken on
         try:
-            traffic = json.load(open(tr_file)).get("bytes_per_launch_full_size")
+            import hashlib
+            rec = json.load(open(tr_file))
+            src = open(os.path.join(ROOT, "paper_2605_13987_gb300", "csrc", "k_expand_tc.cu"), "rb").read()
+            if rec.get("kernel_source_sha256") == hashlib.sha256(src).hexdigest():
+                traffic = rec.get("bytes_per_launch_full_size")
         except Exception:
             traffic = None
 
     # end to end through the C ABI: pinned host output, device compute + D2H copy of H
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.profile:
         Hh = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, pin_memory=True)
         sen.set_timing(False)
         sen.extend("fp32", out=Hh)
@@ -259,7 +278,7 @@ def run_ours(args):
         del Hh
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         import oracle as O
         t2 = time.perf_counter()
         sol = O.solve(w)
@@ -279,7 +298,7 @@ def run_ours(args):
             "value": value, "unit": "point-samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "l2": "flushed (256 MB write) before every timed step",
+            "config": {"workload": WORKLOADS[args.workload], "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}", "rank": info["rank"], "time_samples": nt,
                        "grid_points": npts},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -312,6 +331,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--profile", action="store_true",
+                    help="wrap only the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off); "
+                         "skips the CPU baseline and e2e")
     args = ap.parse_args()
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     if args.impl == "reference":

@@ -12,23 +12,11 @@
 //   X: half-spectrum -> real inverse FFT along x, written to the output layout.
 // FFTs are Stockham autosort, mixed radix (4, 2, 3, 5, 7), in shared memory.
 #include "k_fft.cuh"
+#include "fft_core.cuh"
 
 #include <cmath>
 
 namespace wt {
-
-template <class T>
-struct C2 {
-    T x, y;
-};
-template <class T>
-__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-template <class T>
-__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
-template <class T>
-__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
 
 FftPlan make_plan(int N) {
     FftPlan p{};
@@ -44,74 +32,6 @@ FftPlan make_plan(int N) {
     }
     if (n != 1) fail(WT_ERR_UNSUPPORTED, "FFT length " + std::to_string(N) + " has a prime factor above 7");
     return p;
-}
-
-// One Stockham stage for element j of a line (N/R butterflies per line).
-template <class T>
-__device__ __forceinline__ void stage(const C2<T>* __restrict__ a, C2<T>* __restrict__ b, int N, int Ns, int R,
-                                      int j, const C2<T>* __restrict__ tw) {
-    const int stride = N / R;
-    const int jm = j % Ns;
-    const int idxD = (j / Ns) * Ns * R + jm;
-    if (R == 4) {
-        C2<T> v0 = a[j], v1 = a[j + stride], v2 = a[j + 2 * stride], v3 = a[j + 3 * stride];
-        if (jm) {
-            const int base = jm * (N / (Ns * 4));
-            v1 = cmul(v1, tw[base]);
-            v2 = cmul(v2, tw[2 * base]);
-            v3 = cmul(v3, tw[3 * base]);
-        }
-        C2<T> s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
-        C2<T> id13 = {-d13.y, d13.x};   // i * (v1 - v3)
-        b[idxD] = cadd(s02, s13);
-        b[idxD + Ns] = cadd(d02, id13);
-        b[idxD + 2 * Ns] = csub(s02, s13);
-        b[idxD + 3 * Ns] = csub(d02, id13);
-    } else if (R == 2) {
-        C2<T> v0 = a[j], v1 = a[j + stride];
-        if (jm) v1 = cmul(v1, tw[jm * (N / (Ns * 2))]);
-        b[idxD] = cadd(v0, v1);
-        b[idxD + Ns] = csub(v0, v1);
-    } else {
-        C2<T> v[7];
-        for (int r = 0; r < R; ++r) v[r] = a[j + r * stride];
-        if (jm) {
-            const int base = jm * (N / (Ns * R));
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * base) % N]);
-        }
-        const int step = N / R;
-        for (int k = 0; k < R; ++k) {
-            C2<T> acc = v[0];
-            for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw[((r * k) % R) * step]));
-            b[idxD + k * Ns] = acc;
-        }
-    }
-}
-
-// Inverse (exp(+i)) unnormalised DFT of nl lines (line l at buf + l * ld) in
-// shared memory.  Returns the buffer holding the result.
-template <class T>
-__device__ C2<T>* fft_lines(C2<T>* buf, C2<T>* scr, int ld, int nl, const FftPlan& pl,
-                            const C2<T>* __restrict__ tw) {
-    C2<T>* in = buf;
-    C2<T>* out = scr;
-    int Ns = 1;
-    const int N = pl.N;
-    for (int s = 0; s < pl.ns; ++s) {
-        const int R = pl.r[s];
-        const int nb = N / R;
-        const int tot = nl * nb;
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int l = e / nb, j = e - l * nb;
-            stage<T>(in + l * ld, out + l * ld, N, Ns, R, j, tw);
-        }
-        __syncthreads();
-        C2<T>* t = in;
-        in = out;
-        out = t;
-        Ns *= R;
-    }
-    return in;
 }
 
 template <class T>
@@ -259,24 +179,37 @@ __global__ void pass_x_kernel(GridDev g, const C2<T>* __restrict__ G, FftPlan pl
 }
 
 // --------------------------------------------------- column z-transforms
+__global__ void column_cos_kernel(const double* __restrict__ zsrc, int n_src, int Nz, double Lz,
+                                  double* __restrict__ zcos) {
+    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n_src * Nz) return;
+    const int j = idx / Nz, m = idx % Nz;
+    zcos[idx] = 2.0 * cospi((double)m * zsrc[j] / Lz);
+}
+void column_cos_table(cudaStream_t s, const double* zsrc, int n_src, int Nz, double Lz, double* zcos) {
+    const size_t tot = (size_t)n_src * Nz;
+    column_cos_kernel<<<(tot + 255) / 256, 256, 0, s>>>(zsrc, n_src, Nz, Lz, zcos);
+    WT_LAUNCH("column_cos_table");
+}
+
 template <class T>
-__global__ void column_z_kernel(const double* __restrict__ q, int nb, int ldq, const double* __restrict__ zsrc,
-                                const int* __restrict__ col_off, int n_cols, int Nz, double Lz, T* __restrict__ Zc) {
+__global__ void column_z_kernel(const double* __restrict__ q, int ldq, const double* __restrict__ zcos,
+                                const int* __restrict__ col_off, int n_cols, int Nz, T* __restrict__ Zc) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y, b = blockIdx.z;
     if (m >= Nz) return;
     double acc = 0.0;
     const double* qb = q + (size_t)b * ldq;
-    for (int j = col_off[c]; j < col_off[c + 1]; ++j) acc += qb[j] * 2.0 * cospi((double)m * zsrc[j] / Lz);
+    for (int j = col_off[c]; j < col_off[c + 1]; ++j) acc = fma(qb[j], zcos[(size_t)j * Nz + m], acc);
     Zc[((size_t)b * n_cols + c) * Nz + m] = (T)acc;
 }
 
 template <class T>
-void column_ztransform(cudaStream_t s, const double* q, int nb, int n_src, int ldq, const double* zsrc,
-                       const int* col_off, int n_cols, int Nz, double Lz, T* Zc) {
+void column_ztransform(cudaStream_t s, const double* q, int nb, int n_src, int ldq, const double* zcos,
+                       const int* col_off, int n_cols, int Nz, T* Zc) {
     (void)n_src;
     dim3 grid((Nz + 127) / 128, n_cols, nb);
-    column_z_kernel<T><<<grid, 128, 0, s>>>(q, nb, ldq, zsrc, col_off, n_cols, Nz, Lz, Zc);
+    column_z_kernel<T><<<grid, 128, 0, s>>>(q, ldq, zcos, col_off, n_cols, Nz, Zc);
     WT_LAUNCH("column_ztransform");
 }
 
@@ -324,8 +257,8 @@ void Spectral<T>::fields(const T* Zc, int nb, T* G, T* out, size_t out_sb, size_
 template struct Spectral<float>;
 template struct Spectral<double>;
 template void column_ztransform<float>(cudaStream_t, const double*, int, int, int, const double*, const int*, int,
-                                       int, double, float*);
+                                       int, float*);
 template void column_ztransform<double>(cudaStream_t, const double*, int, int, int, const double*, const int*, int,
-                                        int, double, double*);
+                                        int, double*);
 
 }  // namespace wt

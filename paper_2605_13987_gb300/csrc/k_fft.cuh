@@ -36,9 +36,30 @@ struct Spectral {
 };
 
 // Column z-transform of charge vectors: Zc[b][c][mz] = sum_{j in c} q[b][j] 2 cos(pi mz z_j / Lz).
-// q: [nb][n_src] (double), zsrc [n_src], src_col offsets [n_cols+1].
+// q: [nb][n_src] (double), zcos [n_src][Nz] = 2 cos(pi mz z_j / Lz), col_off [n_cols+1].
 template <class T>
-void column_ztransform(cudaStream_t s, const double* q, int nb, int n_src, int ldq, const double* zsrc,
-                       const int* col_off, int n_cols, int Nz, double Lz, T* Zc);
+void column_ztransform(cudaStream_t s, const double* q, int nb, int n_src, int ldq, const double* zcos,
+                       const int* col_off, int n_cols, int Nz, T* Zc);
+void column_cos_table(cudaStream_t s, const double* zsrc, int n_src, int Nz, double Lz, double* zcos);
+
+}  // namespace wt
+
+namespace wt {
+
+// FP32 basis-field path: deposit -> per-k_z-plane lateral inverse FFT ->
+// z cosine/sine series, written z-contiguous in the H point order.
+struct Fast32 {
+    GridDev g{};
+    int n_cols = 0;
+    FftPlan py{}, px{}, pz{};
+    DBuf<float> tw_y, tw_x, tw_z;
+    DBuf<float> phx, phy, zsh;     // complex tables
+    void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);
+    // rho scratch: nb * Nz * (Nx/2+1) * Ny complex; R scratch: nb * 3 * Nz * Nx * Ny real.
+    size_t rho_elems(int nb) const { return (size_t)nb * g.Nz * (g.Nx / 2 + 1) * g.Ny * 2; }
+    size_t r_elems(int nb) const { return (size_t)nb * 3 * g.Nz * g.Nx * g.Ny; }
+    void fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
+                cudaStream_t s) const;
+};
 
 }  // namespace wt

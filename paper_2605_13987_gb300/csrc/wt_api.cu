@@ -91,11 +91,12 @@ struct wt_ctx {
     DBuf<float> W32;                      // [nt][r_pad] time coefficients
     // spectral
     DBuf<double> d_zsrc;
+    DBuf<double> zcos;                   // [ns][Nz] 2 cos(pi m z_j / Lz)
     DBuf<int> d_col_off;
-    Spectral<float> sp32;
+    Fast32 sp32;
     Spectral<double> sp64;
     bool sp_ready = false;
-    DBuf<float> Zc32, G32, E32;
+    DBuf<float> Zc32, rho32, R32, E32;
     DBuf<double> Zc64, G64;
     DBuf<float> stage32;
     DBuf<double> stage64;
@@ -618,6 +619,8 @@ void ensure_spectral(wt_ctx* c) {
     c->sp64.init(gd, xy, c->s);
     c->d_zsrc.upload(c->src_z.data(), c->ns, c->s);
     c->d_col_off.upload(c->col_off.data(), c->col_off.size(), c->s);
+    c->zcos.alloc((size_t)c->ns * g.Nz);
+    column_cos_table(c->s, c->d_zsrc.p, c->ns, g.Nz, g.Lz, c->zcos.p);
     WT_CUDA(cudaStreamSynchronize(c->s));
     c->sp_ready = true;
 }
@@ -652,8 +655,8 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
         c->G64.alloc(c->sp64.scratch_elems(nb));
         for (int t0 = 0; t0 < nt; t0 += nb) {
             const int b = std::min(nb, nt - t0);
-            column_ztransform<double>(s, c->Qt.p + (size_t)t0 * c->ns, b, c->ns, c->ns, c->d_zsrc.p, c->d_col_off.p,
-                                      ncol, g.Nz, g.Lz, c->Zc64.p);
+            column_ztransform<double>(s, c->Qt.p + (size_t)t0 * c->ns, b, c->ns, c->ns, c->zcos.p, c->d_col_off.p,
+                                      ncol, g.Nz, c->Zc64.p);
             c->sp64.fields(c->Zc64.p, b, c->G64.p, out + (size_t)t0 * 3 * npts, 3 * npts, npts, s);
             launches += 4;
         }
@@ -665,19 +668,19 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
     } else {
         float* out = dev ? static_cast<float*>(H) : c->stage32.p;
         const int r = c->rank, rp = c->r_pad;
-        const int nb = 2;
+        const int nb = 1;     // one charge vector per batch keeps the intermediates in L2
         c->Zc32.alloc((size_t)rp * ncol * g.Nz);
-        c->G32.alloc(c->sp32.scratch_elems(nb));
+        c->rho32.alloc(c->sp32.rho_elems(nb));
+        c->R32.alloc(c->sp32.r_elems(nb));
         c->E32.alloc((size_t)3 * rp * npts);
         if (r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
-        column_ztransform<float>(s, c->Ub.p, r, c->ns, c->ns, c->d_zsrc.p, c->d_col_off.p, ncol, g.Nz, g.Lz,
-                                 c->Zc32.p);
+        column_ztransform<float>(s, c->Ub.p, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
         launches += 1;
         if (c->timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
         for (int m0 = 0; m0 < r; m0 += nb) {
             const int b = std::min(nb, r - m0);
-            c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->G32.p, c->E32.p + (size_t)m0 * npts, npts,
-                           (size_t)rp * npts, s);
+            c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p,
+                           c->E32.p + (size_t)m0 * npts, npts, (size_t)rp * npts, s);
             launches += 3;
         }
         if (c->timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
@@ -712,7 +715,7 @@ void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, dou
     Qt.alloc((size_t)nt * ns);
     transpose(s, Q.p, ns, nt, Qt.p);
     Zc.alloc((size_t)nt * ncol * g.Nz);
-    column_ztransform<double>(s, Qt.p, nt, ns, ns, c->d_zsrc.p, c->d_col_off.p, ncol, g.Nz, g.Lz, Zc.p);
+    column_ztransform<double>(s, Qt.p, nt, ns, ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, Zc.p);
     T.alloc((size_t)(g.Nx / 2) * (g.Ny / 2) * g.Nz);
     green_invk2(s, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, T.p);
     const int chunk = 512;
@@ -735,12 +738,13 @@ void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, dou
 void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStream_t us) {
     const wt_grid& g = c->grid;
     const int nt = (int)c->times.size();
-    if (!H || !tr || !iout) fail(WT_ERR_ARG, "NULL argument");
-    if (!is_device_ptr(H)) fail(WT_ERR_ARG, "H must be device memory (FP32 output of wt_extend)");
+    if (!tr) fail(WT_ERR_ARG, "NULL tracks");
     if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
         fail(WT_ERR_ARG, "bad track sizes or dt");
+    if (tr->n_tracks == 0) return;     // nothing to convolve; no pointer is read
+    if (!H || !iout) fail(WT_ERR_ARG, "NULL argument");
+    if (!is_device_ptr(H)) fail(WT_ERR_ARG, "H must be device memory (FP32 output of wt_extend)");
     if (!tr->x || !tr->y || !tr->z || !tr->vx || !tr->vy || !tr->vz) fail(WT_ERR_ARG, "NULL track array");
-    if (tr->n_tracks == 0) return;
     const size_t nts = (size_t)tr->n_tracks * tr->n_steps;
     const bool dev_in = is_device_ptr(tr->x);
     const bool dev_out = is_device_ptr(iout);
