@@ -173,6 +173,29 @@ wt_status wt_sample_H(wt_ctx* ctx, const double* xyz, int n, const double* t, in
  * returns after the result is written. */
 wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, void* cuda_stream);
 
+/* Eq. 1 without any allocation.  Same result as wt_eq1, for callers that
+ * cannot call cudaMalloc: code running where device allocation is not
+ * allowed or not safe, for instance inside a memory-pool or arena manager
+ * that owns all device memory, in a real-time loop that must not hit the
+ * allocator's locks and synchronisation, or in a plugin host that hands out
+ * only its own buffers.  The paper has no counterpart; this is a property of
+ * the library only.
+ *
+ * The per-call scratch (the lag table, 12 bytes per output time) lives in a
+ * fixed device array of WT_EQ1_NOALLOC_MAX_OUT entries, which every GPU that
+ * loads the library holds (192 KB) until the process exits.  n_out above the
+ * limit returns WT_ERR_ARG.  H, the track arrays and i must be device
+ * memory (WT_ERR_ARG otherwise: host buffers would need staging).  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites the
+ * entries it uses, so calls that overlap on the GPU (for example on two
+ * streams at once) race on it: order them on one stream.  Asynchronous on
+ * cuda_stream. */
+#define WT_EQ1_NOALLOC_MAX_OUT 16384
+wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tracks, float* i, void* cuda_stream);
+
 /* Copy intermediate results to host memory (for checks and diagnostics):
  * q: [n_t][n_sources] node charges (after wt_relax);
  * cn: [n_sources][n_sources] capacitance (after wt_fit);

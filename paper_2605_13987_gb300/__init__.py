@@ -8,7 +8,7 @@ load the library; the first call does, and fails if it was not built.
 from ._binding import (  # noqa: F401
     WTError, load_library, LIB_PATH,
     WT_FP32, WT_FP64,
-    wt_create, wt_add_columns, wt_fit, wt_relax, wt_extend, wt_sample_H, wt_eq1,
+    wt_create, wt_add_columns, wt_fit, wt_relax, wt_extend, wt_sample_H, wt_eq1, wt_eq1_noalloc,
     wt_get_charges, wt_get_capacitance, wt_get_modes, wt_get_info, wt_set_timing, wt_get_timing,
     wt_destroy,
 )

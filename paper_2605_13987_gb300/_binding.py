@@ -65,6 +65,7 @@ SIGNATURES = {
     "wt_sample_H": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.c_int,
                               C.POINTER(C.c_double)]),
     "wt_eq1": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
+    "wt_eq1_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_capacitance": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_modes": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -185,6 +186,16 @@ def wt_eq1(ctx, H, tracks, i_out, stream=None):
                    _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
     st = _stream_handle(stream) if (hasattr(i_out, "is_cuda") and i_out.is_cuda) else None
     _check(lib.wt_eq1(ctx, _ptr(H), C.byref(tr), _ptr(i_out), st), ctx)
+
+
+def wt_eq1_noalloc(ctx, H, tracks, i_out, stream=None):
+    """Eq. 1 with no device allocation: every buffer must be device memory."""
+    lib = load_library()
+    tr = wt_tracks(int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"]),
+                   float(tracks["dt"]), float(tracks.get("charge", 1.0)),
+                   _ptr(tracks["x"]), _ptr(tracks["y"]), _ptr(tracks["z"]),
+                   _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
+    _check(lib.wt_eq1_noalloc(ctx, _ptr(H), C.byref(tr), _ptr(i_out), _stream_handle(stream)), ctx)
 
 
 def wt_get_charges(ctx, n_t, n_sources):

@@ -9,6 +9,8 @@
 // every output time accumulates its lags in FP64.
 #include "wt_internal.cuh"
 
+#include <mutex>
+
 namespace wt {
 
 struct Eq1Lag {
@@ -98,5 +100,76 @@ void eq1_launch(cudaStream_t s, const float* H, int Nx, int Ny, int Nz, int nt, 
 }
 size_t eq1_lag_size() { return sizeof(Eq1Lag); }
 void eq1_pack_lag(void* dst, int n, float w0, float w1) { *static_cast<Eq1Lag*>(dst) = Eq1Lag{n, w0, w1}; }
+
+// ------------------------------------------------------------------------
+// Allocation-free variant (wt_eq1_noalloc).  The per-call lag table lives in
+// this fixed device array instead of a cudaMalloc'd buffer; every GPU that
+// loads the library holds it (192 KB) until the process exits.
+constexpr int kEq1NoAllocMaxOut = 16384;
+static __device__ __align__(256) Eq1Lag g_eq1_lag_scratch[kEq1NoAllocMaxOut];
+
+// Lag table on the device from the relaxation's time samples: same rule as
+// the host-built table of eq1_launch's callers (linear in t, 0 at t = 0,
+// held after the last sample).  Every entry is overwritten on each call.
+__global__ void eq1_lag_table_kernel(const double* __restrict__ t, int nt, double dt, int n_out,
+                                     Eq1Lag* __restrict__ lags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_out) return;
+    const double L = (k + 0.5) * dt;
+    int n0 = 0;
+    double w0 = 0.0, w1 = 0.0;
+    if (L <= t[0]) { n0 = 0; w0 = L / t[0]; }
+    else if (L >= t[nt - 1]) { n0 = nt - 1; w0 = 1.0; }
+    else {
+        int lo = 0, hi = nt - 1;           // t[lo] <= L < t[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (t[mid] <= L) lo = mid; else hi = mid;
+        }
+        n0 = lo;
+        const double f = (L - t[lo]) / (t[lo + 1] - t[lo]);
+        w0 = 1.0 - f;
+        w1 = f;
+    }
+    lags[k] = Eq1Lag{n0, (float)w0, (float)w1};
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+Eq1Lag* g_noalloc_ptr[kMaxDevices] = {};   // device address of the scratch, per device
+}
+
+int eq1_noalloc_max_out() { return kEq1NoAllocMaxOut; }
+
+// The caller's device is current.  Resolves the scratch address on first use
+// on this device (the symbol's host-side name is not a device address).
+void eq1_noalloc_launch(cudaStream_t s, int device, const float* H, int Nx, int Ny, int Nz, const double* d_times,
+                        int nt, double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
+                        const float* vx, const float* vy, const float* vz, const float* q, float qconst,
+                        int n_tracks, int n_steps, int n_out, double dt, double v_w, float* out) {
+    if (n_out > kEq1NoAllocMaxOut)
+        fail(WT_ERR_ARG, "n_out " + std::to_string(n_out) + " exceeds the allocation-free limit of " +
+                             std::to_string(kEq1NoAllocMaxOut));
+    if (device < 0 || device >= kMaxDevices) fail(WT_ERR_UNSUPPORTED, "device index beyond the scratch table");
+    Eq1Lag* lags = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[device]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_eq1_lag_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                fail(WT_ERR_CUDA, std::string("cudaGetSymbolAddress(eq1 scratch): ") + cudaGetErrorString(e));
+            }
+            g_noalloc_ptr[device] = static_cast<Eq1Lag*>(p);
+        }
+        lags = g_noalloc_ptr[device];
+    }
+    eq1_lag_table_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(d_times, nt, dt, n_out, lags);
+    WT_LAUNCH("eq1_lag_table");
+    eq1_launch(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out, dt, v_w,
+               lags, out);
+}
 
 }  // namespace wt

@@ -38,6 +38,9 @@ void eq1_launch(cudaStream_t, const float*, int, int, int, int, double, double, 
                 const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
                 double, const void*, float*);
 size_t eq1_lag_size();
+void eq1_noalloc_launch(cudaStream_t, int, const float*, int, int, int, const double*, int, double, double, double,
+                        const float*, const float*, const float*, const float*, const float*, const float*,
+                        const float*, float, int, int, int, double, double, float*);
 void eq1_pack_lag(void*, int, float, float);
 bool expand_tc_available();
 void expand_tc(cudaStream_t, const float*, int, const float*, int, size_t, float*, int*);
@@ -885,6 +888,27 @@ wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, 
     return run(ctx, "wt_eq1", [&] {
         if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1 needs wt_relax first");
         do_eq1(ctx, H, tracks, i, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tr, float* i, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_noalloc", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_noalloc needs wt_relax first");
+        if (!tr) fail(WT_ERR_ARG, "NULL tracks");
+        if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
+            fail(WT_ERR_ARG, "bad track sizes or dt");
+        if (tr->n_tracks == 0) return;
+        const void* ptrs[9] = {H, i, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz, tr->q};
+        for (int k = 0; k < 9; ++k) {
+            if (k == 8 && !tr->q) continue;
+            if (!ptrs[k] || !is_device_ptr(ptrs[k]))
+                fail(WT_ERR_ARG, "every buffer must be device memory (no staging without allocation)");
+        }
+        const wt_grid& g = ctx->grid;
+        eq1_noalloc_launch(static_cast<cudaStream_t>(stream), ctx->dev, H, g.Nx, g.Ny, g.Nz, ctx->d_times.p,
+                           (int)ctx->times.size(), g.Lx, g.Ly, g.Lz, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz,
+                           tr->q, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out, tr->dt, ctx->opts.v_w, i);
     });
 }
 
