@@ -51,7 +51,7 @@ namespace wt {
 struct Fast32 {
     GridDev g{};
     int n_cols = 0;
-    FftPlan py{}, px{}, pz{};
+    int rxy = 0, rz = 0;           // register-FFT elements per lane (lateral, z)
     DBuf<float> tw_y, tw_x, tw_z;
     DBuf<float> phx, phy, zsh;     // complex tables
     void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);

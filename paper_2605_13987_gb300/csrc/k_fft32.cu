@@ -9,6 +9,7 @@
 //            packed in one length-2Nz complex FFT; out[b][c][x][y][z].
 #include "k_fft.cuh"
 #include "fft_core.cuh"
+#include "warp_fft.cuh"
 
 namespace wt {
 
@@ -37,47 +38,58 @@ __global__ void f32_tables_kernel(const double* __restrict__ xy, int n_cols, int
     }
 }
 
-// rho^ planes; grid (Nz, nb), threads over (mx, my)
+// rho^ planes; grid (Nz, nb), threads over (mx, my).  Shared tables:
+// px[c][mx] = e^{-i kx x_c}, qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
 __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __restrict__ phx,
                                    const C2<float>* __restrict__ phy, const float* __restrict__ Zc,
                                    C2<float>* __restrict__ rho) {
-    extern __shared__ float zc_s[];
+    extern __shared__ unsigned char smem_raw[];
     const int mz = blockIdx.x, b = blockIdx.y;
-    const int nxh = g.Nx / 2 + 1;
-    for (int c = threadIdx.x; c < n_cols; c += blockDim.x) zc_s[c] = Zc[((size_t)b * n_cols + c) * g.Nz + mz];
+    const int nxh = g.Nx / 2 + 1, ny = g.Ny;
+    C2<float>* px = reinterpret_cast<C2<float>*>(smem_raw);
+    C2<float>* qy = px + (size_t)n_cols * nxh;
+    for (int e = threadIdx.x; e < n_cols * nxh; e += blockDim.x) px[e] = phx[e];
+    for (int e = threadIdx.x; e < n_cols * ny; e += blockDim.x) {
+        const float z = Zc[((size_t)b * n_cols + e / ny) * g.Nz + mz];
+        const C2<float> p = phy[e];
+        qy[e] = {p.x * z, p.y * z};
+    }
     __syncthreads();
-    C2<float>* out = rho + ((size_t)b * g.Nz + mz) * nxh * g.Ny;
-    for (int e = threadIdx.x; e < nxh * g.Ny; e += blockDim.x) {
-        const int mx = e / g.Ny, my = e % g.Ny;
+    C2<float>* out = rho + ((size_t)b * g.Nz + mz) * nxh * ny;
+    for (int e = threadIdx.x; e < nxh * ny; e += blockDim.x) {
+        const int mx = e / ny, my = e % ny;
         C2<float> acc = {0.f, 0.f};
         for (int c = 0; c < n_cols; ++c) {
-            const C2<float> p = cmul(phx[c * nxh + mx], phy[c * g.Ny + my]);
-            acc.x = fmaf(p.x, zc_s[c], acc.x);
-            acc.y = fmaf(p.y, zc_s[c], acc.y);
+            const C2<float> a = px[c * nxh + mx], q = qy[c * ny + my];
+            acc.x = fmaf(a.x, q.x, fmaf(-a.y, q.y, acc.x));
+            acc.y = fmaf(a.x, q.y, fmaf(a.y, q.x, acc.y));
         }
         out[e] = acc;
     }
 }
 
-constexpr int F32_NL = 16;   // lines per FFT batch in the plane kernel
-
-// grid (Nz, 3, nb)
-__global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho, FftPlan py,
-                                                        FftPlan px, const C2<float>* __restrict__ twy,
+// One (k_z plane, component, charge vector) per block: component factor,
+// inverse FFT along y for every m_x row, then half spectrum -> real along x.
+// Warp FFTs in registers; the plane stays in shared memory.
+// Output R[b][c][mz][y][x].  grid (Nz, 3, nb).
+template <int RY, int RX>
+__global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
+                                                        const C2<float>* __restrict__ twy,
                                                         const C2<float>* __restrict__ twx, float* __restrict__ R) {
     extern __shared__ unsigned char smem_raw[];
     const int nx = g.Nx, ny = g.Ny, nz = g.Nz, nxh = nx / 2 + 1;
     const int mz = blockIdx.x, comp = blockIdx.y, b = blockIdx.z;
     const int ldp = ny + 1;
-    const int nmax = nx > ny ? nx : ny;
-    C2<float>* P = reinterpret_cast<C2<float>*>(smem_raw);            // [nxh][ldp]
-    C2<float>* A = P + (size_t)nxh * ldp;                             // [F32_NL][nmax]
-    C2<float>* B = A + (size_t)F32_NL * nmax;
+    C2<float>* P = reinterpret_cast<C2<float>*>(smem_raw);     // [nxh][ldp]
+    C2<float>* ty = P + (size_t)nxh * ldp;                     // [ny]
+    C2<float>* tx = ty + ny;                                   // [nx]
     float* Rout = R + (((size_t)b * 3 + comp) * nz + mz) * nx * ny;
     if (comp == 2 && mz == 0) {       // the sine series has no k_z = 0 term
         for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) Rout[e] = 0.f;
         return;
     }
+    for (int e = threadIdx.x; e < ny; e += blockDim.x) ty[e] = twy[e];
+    for (int e = threadIdx.x; e < nx; e += blockDim.x) tx[e] = twx[e];
     const float kz = (float)(kPi * mz / g.Lz);
     const float ckx = (float)(2.0 * kPi / g.Lx), cky = (float)(2.0 * kPi / g.Ly);
     const float pref = (float)g.pref;
@@ -102,80 +114,106 @@ __global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<floa
         P[mx * ldp + my] = v;
     }
     __syncthreads();
-    // inverse FFT along y for every mx row
-    for (int r0 = 0; r0 < nxh; r0 += F32_NL) {
-        const int nl = min(F32_NL, nxh - r0);
-        for (int e = threadIdx.x; e < nl * ny; e += blockDim.x) A[(e / ny) * nmax + e % ny] = P[(r0 + e / ny) * ldp + e % ny];
-        __syncthreads();
-        C2<float>* res = fft_lines<float>(A, B, nmax, nl, py, twy);
-        for (int e = threadIdx.x; e < nl * ny; e += blockDim.x) P[(r0 + e / ny) * ldp + e % ny] = res[(e / ny) * nmax + e % ny];
-        __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {   // y: nxh lines of length ny
+        const int W = ny / RY, G = 32 / W, grp = lane / W, gl = lane % W;
+        const int k2 = warp_fft_k2(gl, W);
+        for (int base = warp * G; base < nxh; base += 8 * G) {
+            const int mx = base + grp;
+            const bool act = mx < nxh;
+            C2<float> v[RY];
+#pragma unroll
+            for (int j = 0; j < RY; ++j) v[j] = act ? P[mx * ldp + j + RY * gl] : C2<float>{0.f, 0.f};
+            warp_fft<RY>(v, gl, W, ty, ny);
+            if (act)
+#pragma unroll
+                for (int k = 0; k < RY; ++k) P[mx * ldp + k2 + W * k] = v[k];
+        }
     }
-    // half spectrum along x -> real, F32_NL consecutive y at a time
-    for (int y0 = 0; y0 < ny; y0 += F32_NL) {
-        const int nl = min(F32_NL, ny - y0);
-        for (int e = threadIdx.x; e < nl * nx; e += blockDim.x) {
-            const int l = e / nx, mx = e % nx;
-            A[l * nmax + mx] = mx < nx / 2 ? P[mx * ldp + y0 + l] : C2<float>{0.f, 0.f};
+    __syncthreads();
+    {   // x: ny lines of length nx from the half spectrum (m_x >= nx/2 are zero)
+        const int W = nx / RX, G = 32 / W, grp = lane / W, gl = lane % W;
+        const int k2 = warp_fft_k2(gl, W);
+        for (int base = warp * G; base < ny; base += 8 * G) {
+            const int y = base + grp;
+            const bool act = y < ny;
+            C2<float> v[RX];
+#pragma unroll
+            for (int j = 0; j < RX; ++j) {
+                const int mx = j + RX * gl;
+                v[j] = (act && mx < nx / 2) ? P[mx * ldp + y] : C2<float>{0.f, 0.f};
+            }
+            warp_fft<RX>(v, gl, W, tx, nx);
+            if (act)
+#pragma unroll
+                for (int k = 0; k < RX; ++k) Rout[(size_t)y * nx + k2 + W * k] = v[k].x;
         }
-        __syncthreads();
-        C2<float>* res = fft_lines<float>(A, B, nmax, nl, px, twx);
-        for (int e = threadIdx.x; e < nl * nx; e += blockDim.x) {
-            const int x = e / nl, l = e % nl;
-            Rout[(size_t)x * ny + y0 + l] = res[l * nmax + x].x;
-        }
-        __syncthreads();
     }
 }
 
-constexpr int F32_LB = 16;   // (x, y) lines per z-pass block
+constexpr int F32_LB = 32;   // (x, y) lines per z-pass block
 
-// grid (Nx*Ny / F32_LB, 3, nb)
-__global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* __restrict__ R, FftPlan pz,
+// Cosine (W_x, W_y) or sine (W_z) series along z for F32_LB lines; two real
+// lines share one length-2Nz complex warp FFT.  Lines L = y Nx + x of the
+// plane kernel's layout; output in H's point order (x Ny + y) Nz + z.
+// grid (ceil(Nx Ny / F32_LB), 3, nb).
+template <int RZ>
+__global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
                                                         const C2<float>* __restrict__ twz,
                                                         const C2<float>* __restrict__ zsh, float* __restrict__ out,
                                                         size_t out_sb, size_t out_sc) {
     extern __shared__ unsigned char smem_raw[];
-    const int nz = g.Nz, n2 = 2 * nz;
-    const size_t nxy = (size_t)g.Nx * g.Ny;
+    const int nx = g.Nx, ny = g.Ny, nz = g.Nz, n2 = 2 * nz;
+    const size_t nxy = (size_t)nx * ny;
     const int comp = blockIdx.y, b = blockIdx.z;
     const size_t L0 = (size_t)blockIdx.x * F32_LB;
-    float* in = reinterpret_cast<float*>(smem_raw);                      // [nz][F32_LB]
-    C2<float>* A = reinterpret_cast<C2<float>*>(in + (size_t)nz * F32_LB);   // [F32_LB/2][n2]
-    C2<float>* Bf = A + (size_t)(F32_LB / 2) * n2;
+    float* in = reinterpret_cast<float*>(smem_raw);                          // [nz][F32_LB]
+    C2<float>* tw = reinterpret_cast<C2<float>*>(in + (size_t)nz * F32_LB);   // [n2]
+    C2<float>* zs = tw + n2;                                                 // [nz]
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) tw[e] = twz[e];
+    for (int e = threadIdx.x; e < nz; e += blockDim.x) zs[e] = zsh[e];
     const float* src = R + ((size_t)b * 3 + comp) * nz * nxy + L0;
     for (int e = threadIdx.x; e < nz * F32_LB; e += blockDim.x) {
         const int m = e / F32_LB, l = e % F32_LB;
         in[e] = (L0 + l < nxy) ? src[(size_t)m * nxy + l] : 0.f;
     }
     __syncthreads();
-    // pack lines (2p, 2p+1) as real and imaginary parts; build the length-2Nz sequence
-    for (int e = threadIdx.x; e < (F32_LB / 2) * nz; e += blockDim.x) {
-        const int p = e / nz, m = e % nz;
-        C2<float>* d = A + (size_t)p * n2;
-        const C2<float> c = {in[m * F32_LB + 2 * p], in[m * F32_LB + 2 * p + 1]};
-        const C2<float> ez = zsh[m];
-        const C2<float> ezc = {ez.x, -ez.y};
-        if (comp < 2) {            // cosine series
-            if (m == 0) { d[0] = c; d[nz] = {0.f, 0.f}; }
-            else { d[m] = cmul(c, ez); d[n2 - m] = cmul(c, ezc); }
-        } else {                   // sine series: d_m = C e/(2i), d_{2N-m} = -C ec/(2i)
-            if (m == 0) { d[0] = {0.f, 0.f}; d[nz] = {0.f, 0.f}; }
-            else {
-                const C2<float> t1 = cmul(c, ez), t2 = cmul(c, ezc);
-                d[m] = {0.5f * t1.y, -0.5f * t1.x};
-                d[n2 - m] = {-0.5f * t2.y, 0.5f * t2.x};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = n2 / RZ, G = 32 / W, grp = lane / W, gl = lane % W;
+    const int k2 = warp_fft_k2(gl, W);
+    float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
+    for (int base = warp * G; base < F32_LB / 2; base += 8 * G) {
+        const int f = base + grp;                 // lines 2f, 2f+1 of this block
+        C2<float> v[RZ];
+#pragma unroll
+        for (int j1 = 0; j1 < RZ; ++j1) {
+            const int j = j1 + RZ * gl;
+            C2<float> d = {0.f, 0.f};
+            if (j != nz) {
+                const int m = j < nz ? j : n2 - j;
+                const C2<float> c = {in[m * F32_LB + 2 * f], in[m * F32_LB + 2 * f + 1]};
+                if (comp < 2) {
+                    if (j == 0) d = c;
+                    else d = j < nz ? cmul(c, zs[m]) : cmul(c, C2<float>{zs[m].x, -zs[m].y});
+                } else if (j != 0) {
+                    if (j < nz) { const C2<float> t = cmul(c, zs[m]); d = {0.5f * t.y, -0.5f * t.x}; }
+                    else { const C2<float> t = cmul(c, C2<float>{zs[m].x, -zs[m].y}); d = {-0.5f * t.y, 0.5f * t.x}; }
+                }
             }
+            v[j1] = d;
         }
-    }
-    __syncthreads();
-    C2<float>* res = fft_lines<float>(A, Bf, n2, F32_LB / 2, pz, twz);
-    float* o = out + (size_t)b * out_sb + (size_t)comp * out_sc + L0 * nz;
-    for (int e = threadIdx.x; e < F32_LB * nz; e += blockDim.x) {
-        const int l = e / nz, z = e % nz;
-        if (L0 + l < nxy) {
-            const C2<float> v = res[(size_t)(l >> 1) * n2 + z];
-            o[(size_t)l * nz + z] = (l & 1) ? v.y : v.x;
+        warp_fft<RZ>(v, gl, W, tw, n2);
+        const size_t La = L0 + 2 * f, Lb = La + 1;
+        const bool a_ok = La < nxy, b_ok = Lb < nxy;
+        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
+        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
+#pragma unroll
+        for (int k1 = 0; k1 < RZ; ++k1) {
+            const int z = k2 + W * k1;
+            if (z < nz) {
+                if (a_ok) ob[pa + z] = v[k1].x;
+                if (b_ok) ob[pb + z] = v[k1].y;
+            }
         }
     }
 }
@@ -190,19 +228,38 @@ __global__ void f32_twiddle_kernel(float* tw, int N) {
 }
 
 static size_t plane_smem(const GridDev& g) {
-    const int nxh = g.Nx / 2 + 1, nmax = g.Nx > g.Ny ? g.Nx : g.Ny;
-    return ((size_t)nxh * (g.Ny + 1) + 2 * (size_t)F32_NL * nmax) * sizeof(C2<float>);
+    const int nxh = g.Nx / 2 + 1;
+    return ((size_t)nxh * (g.Ny + 1) + g.Ny + g.Nx) * sizeof(C2<float>);
 }
 static size_t zpass_smem(const GridDev& g) {
-    return (size_t)g.Nz * F32_LB * sizeof(float) + 2 * (size_t)(F32_LB / 2) * 2 * g.Nz * sizeof(C2<float>);
+    return (size_t)g.Nz * F32_LB * sizeof(float) + (size_t)3 * g.Nz * sizeof(C2<float>);
+}
+static size_t deposit_smem(const GridDev& g, int n_cols) {
+    return (size_t)n_cols * (g.Nx / 2 + 1 + g.Ny) * sizeof(C2<float>);
+}
+
+// Register-FFT lengths compiled in: elements per lane R = N / W.
+#define WT_FOR_EACH_R(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(24)
+
+static bool supported_r(int r) {
+    switch (r) {
+#define WT_CASE(R) case R:
+        WT_FOR_EACH_R(WT_CASE)
+#undef WT_CASE
+        return true;
+        default: return false;
+    }
 }
 
 void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s) {
     g = gd;
     n_cols = (int)xy.size() / 2;
-    py = make_plan(g.Ny);
-    px = make_plan(g.Nx);
-    pz = make_plan(2 * g.Nz);
+    if (g.Nx != g.Ny) fail(WT_ERR_UNSUPPORTED, "the FP32 fast path needs Nx == Ny");
+    int w;
+    warp_fft_shape(g.Nx, &w, &rxy);
+    warp_fft_shape(2 * g.Nz, &w, &rz);
+    if (!supported_r(rxy) || !supported_r(rz))
+        fail(WT_ERR_UNSUPPORTED, "FFT length not covered by the register FFT (N / W in {1..10, 12, 14, 15, 16, 24})");
     const int nxh = g.Nx / 2 + 1;
     DBuf<double> dxy;
     dxy.upload(xy.data(), xy.size(), s);
@@ -212,17 +269,27 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
     const int n = std::max(n_cols * std::max(nxh, g.Ny), g.Nz);
     f32_tables_kernel<<<(n + 127) / 128, 128, 0, s>>>(dxy.p, n_cols, nxh, g.Ny, g.Nz, g.Lx, g.Ly, phx.p, phy.p,
                                                       zsh.p);
-    tw_y.alloc(2 * (size_t)py.N);
-    tw_x.alloc(2 * (size_t)px.N);
-    tw_z.alloc(2 * (size_t)pz.N);
-    f32_twiddle_kernel<<<(py.N + 127) / 128, 128, 0, s>>>(tw_y.p, py.N);
-    f32_twiddle_kernel<<<(px.N + 127) / 128, 128, 0, s>>>(tw_x.p, px.N);
-    f32_twiddle_kernel<<<(pz.N + 127) / 128, 128, 0, s>>>(tw_z.p, pz.N);
+    tw_y.alloc(2 * (size_t)g.Ny);
+    tw_x.alloc(2 * (size_t)g.Nx);
+    tw_z.alloc(2 * (size_t)2 * g.Nz);
+    f32_twiddle_kernel<<<(g.Ny + 127) / 128, 128, 0, s>>>(tw_y.p, g.Ny);
+    f32_twiddle_kernel<<<(g.Nx + 127) / 128, 128, 0, s>>>(tw_x.p, g.Nx);
+    f32_twiddle_kernel<<<(2 * g.Nz + 127) / 128, 128, 0, s>>>(tw_z.p, 2 * g.Nz);
     WT_LAUNCH("fast32 tables");
-    const size_t sp = plane_smem(g), sz = zpass_smem(g);
-    if (sp > 227 * 1024 || sz > 227 * 1024) fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
-    WT_CUDA(cudaFuncSetAttribute(f32_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
-    WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz));
+    const size_t sp = plane_smem(g), sz = zpass_smem(g), sd = deposit_smem(g, n_cols);
+    if (sp > 227 * 1024 || sz > 227 * 1024 || sd > 227 * 1024)
+        fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
+    switch (rxy) {
+#define WT_CASE(R) case R: { WT_CUDA(cudaFuncSetAttribute(f32_plane_kernel<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp)); break; }
+        WT_FOR_EACH_R(WT_CASE)
+#undef WT_CASE
+    }
+    switch (rz) {
+#define WT_CASE(R) case R: { WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); break; }
+        WT_FOR_EACH_R(WT_CASE)
+#undef WT_CASE
+    }
+    WT_CUDA(cudaFuncSetAttribute(f32_deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
     WT_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -230,17 +297,27 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
                     cudaStream_t s) const {
     C2<float>* rc = reinterpret_cast<C2<float>*>(rho);
     dim3 gd(g.Nz, nb);
-    f32_deposit_kernel<<<gd, 256, n_cols * sizeof(float), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
-                                                               reinterpret_cast<const C2<float>*>(phy.p), Zc, rc);
+    f32_deposit_kernel<<<gd, 256, deposit_smem(g, n_cols), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
+                                                                reinterpret_cast<const C2<float>*>(phy.p), Zc, rc);
     WT_LAUNCH("f32_deposit");
     dim3 gp(g.Nz, 3, nb);
-    f32_plane_kernel<<<gp, 256, plane_smem(g), s>>>(g, rc, py, px, reinterpret_cast<const C2<float>*>(tw_y.p),
-                                                    reinterpret_cast<const C2<float>*>(tw_x.p), R);
+    const C2<float>* ty = reinterpret_cast<const C2<float>*>(tw_y.p);
+    const C2<float>* tx = reinterpret_cast<const C2<float>*>(tw_x.p);
+    switch (rxy) {
+#define WT_CASE(RR) case RR: f32_plane_kernel<RR, RR><<<gp, 256, plane_smem(g), s>>>(g, rc, ty, tx, R); break;
+        WT_FOR_EACH_R(WT_CASE)
+#undef WT_CASE
+    }
     WT_LAUNCH("f32_plane");
     const size_t nxy = (size_t)g.Nx * g.Ny;
     dim3 gz((unsigned)((nxy + F32_LB - 1) / F32_LB), 3, nb);
-    f32_zpass_kernel<<<gz, 256, zpass_smem(g), s>>>(g, R, pz, reinterpret_cast<const C2<float>*>(tw_z.p),
-                                                    reinterpret_cast<const C2<float>*>(zsh.p), out, out_sb, out_sc);
+    const C2<float>* tz = reinterpret_cast<const C2<float>*>(tw_z.p);
+    const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
+    switch (rz) {
+#define WT_CASE(RR) case RR: f32_zpass_kernel<RR><<<gz, 256, zpass_smem(g), s>>>(g, R, tz, zz, out, out_sb, out_sc); break;
+        WT_FOR_EACH_R(WT_CASE)
+#undef WT_CASE
+    }
     WT_LAUNCH("f32_zpass");
 }
 

@@ -1,0 +1,108 @@
+// Warp-level FFT held in registers (inverse sign exp(+i), unnormalised).
+//
+// A line of length N = W * R is owned by W lanes of a warp (W a power of two
+// <= 32), R elements per lane: lane l (0 <= l < W) starts with
+// v[j1] = x[j1 + R l].  Decomposition j = j1 + R j2, k = k2 + W k1:
+//   X[k2 + W k1] = sum_j1 w_R^{j1 k1} w_N^{j1 k2} sum_j2 x[j1 + R j2] w_W^{j2 k2}
+// (1) W-point DFTs across lanes (decimation in frequency with __shfl_xor,
+//     output bit-reversed across lanes), (2) twiddles w_N^{j1 k2},
+// (3) R-point DFTs in registers.  On return lane l holds
+// v[k1] = X[bitrev_W(l) + W k1].  32/W lines share a warp (lane groups).
+// tw: table of w_N^k = exp(+2 pi i k / N), k < N.
+#pragma once
+#include "fft_core.cuh"
+
+namespace wt {
+
+// R-point DFT in registers (exp(+i)); w_R^m = tw[(m mod R) * (N / R)].
+template <int R>
+__device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __restrict__ tw, int N) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        const C2<float> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const C2<float> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const C2<float> s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        const C2<float> id13 = {-d13.y, d13.x};
+        v[0] = cadd(s02, s13);
+        v[1] = cadd(d02, id13);
+        v[2] = csub(s02, s13);
+        v[3] = csub(d02, id13);
+    } else if constexpr (R == 3 || R == 5 || R == 7) {
+        C2<float> o[R];
+        const int st = N / R;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            C2<float> acc = v[0];
+#pragma unroll
+            for (int j = 1; j < R; ++j) acc = cadd(acc, cmul(v[j], tw[((j * k) % R) * st]));
+            o[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = o[k];
+    } else {
+        // R = A * B: B-point DFTs over x[j1 + A j2], twiddle w_R^{j1 k2}, A-point DFTs
+        constexpr int A = (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : (R % 3 == 0) ? 3 : (R % 5 == 0) ? 5 : 7;
+        constexpr int B = R / A;
+        static_assert(A * B == R, "unsupported register DFT length");
+        C2<float> y[A][B];
+#pragma unroll
+        for (int j1 = 0; j1 < A; ++j1) {
+            C2<float> t[B];
+#pragma unroll
+            for (int j2 = 0; j2 < B; ++j2) t[j2] = v[j1 + A * j2];
+            reg_dft<B>(t, tw, N);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) y[j1][k2] = (j1 && k2) ? cmul(t[k2], tw[((j1 * k2) % R) * (N / R)]) : t[k2];
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            C2<float> t[A];
+#pragma unroll
+            for (int j1 = 0; j1 < A; ++j1) t[j1] = y[j1][k2];
+            reg_dft<A>(t, tw, N);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[k2 + B * k1] = t[k1];
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_fft(C2<float> (&v)[R], int gl, int W, const C2<float>* __restrict__ tw, int N) {
+    // (1) W-point DFTs across the lane group, one per j1
+    for (int h = W >> 1; h >= 1; h >>= 1) {
+        const bool bottom = gl & h;
+        const C2<float> w = tw[(gl & (h - 1)) * (N / (2 * h))];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const C2<float> a = v[j];
+            const C2<float> b = {__shfl_xor_sync(0xffffffffu, a.x, h), __shfl_xor_sync(0xffffffffu, a.y, h)};
+            v[j] = bottom ? cmul(csub(b, a), w) : cadd(a, b);
+        }
+    }
+    // (2) twiddles w_N^{j1 k2}, k2 = bit-reversed lane
+    const int lw = 31 - __clz(W);                 // log2 W
+    const int k2 = lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;
+#pragma unroll
+    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], tw[(j * k2) % N]);
+    // (3) R-point DFTs in registers: X[k2 + W k1] = sum_j1 w_R^{j1 k1} ...
+    reg_dft<R>(v, tw, N);
+}
+
+__device__ __forceinline__ int warp_fft_k2(int gl, int W) {
+    const int lw = 31 - __clz(W);
+    return lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;
+}
+
+// Lanes per line (largest power of two <= 32 dividing N) and elements per lane.
+inline void warp_fft_shape(int N, int* W, int* R) {
+    int w = 32;
+    while (N % w) w >>= 1;
+    *W = w;
+    *R = N / w;
+}
+
+}  // namespace wt
