@@ -29,9 +29,9 @@ listed in the module docstrings:
 * ``eq1``      the Ramo-Shockley-Riegler convolution, Eq. 1.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
-except the brute-force finite-difference comparison (``bruteforce``), which is
-a loose consistency check between two different discretisations: parity
-unpinned for that one comparison.
+except the brute-force finite-difference model (``bruteforce``), which is a
+loose consistency check between two different discretisations (agreement to
+~4-9 % on the single cell): parity unpinned for that one comparison.
 """
-from . import greens, geometry, fit, relax, extend, eq1  # noqa: F401
+from . import greens, geometry, fit, relax, extend, eq1, bruteforce  # noqa: F401
 from .pipeline import solve, Solution  # noqa: F401
