@@ -20,17 +20,18 @@ struct Eq1Lag {
 
 constexpr int EQ1_MC = 16;   // track steps per chunk
 
-__global__ void __launch_bounds__(256) eq1_kernel(const float* __restrict__ H, int Nx, int Ny, int Nz, int nt,
-                                                  float inv_hx, float inv_hy, float inv_hz,
+template <class T>
+__global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int Nx, int Ny, int Nz, int nt,
+                                                  T inv_hx, T inv_hy, T inv_hz,
                                                   const float* __restrict__ X, const float* __restrict__ Y,
                                                   const float* __restrict__ Z, const float* __restrict__ VX,
                                                   const float* __restrict__ VY, const float* __restrict__ VZ,
                                                   const float* __restrict__ qtrack, float qconst, int n_steps,
                                                   int n_out, double dt, double inv_vw,
                                                   const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
-    extern __shared__ unsigned char smem_raw[];
-    float* f = reinterpret_cast<float*>(smem_raw);                       // [EQ1_MC][nt]
-    double* Q = reinterpret_cast<double*>(f + EQ1_MC * nt + (EQ1_MC * nt & 1));   // [n_out]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* f = reinterpret_cast<T*>(smem_raw);                               // [EQ1_MC][nt]
+    double* Q = reinterpret_cast<double*>(smem_raw + (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15));   // [n_out]
     const int tr = blockIdx.x;
     const size_t npts = (size_t)Nx * Ny * Nz;
     for (int m = threadIdx.x; m < n_out; m += blockDim.x) Q[m] = 0.0;
@@ -40,28 +41,30 @@ __global__ void __launch_bounds__(256) eq1_kernel(const float* __restrict__ H, i
         for (int e = threadIdx.x; e < mc * nt; e += blockDim.x) {
             const int j = e / nt, n = e % nt;
             const size_t s = (size_t)tr * n_steps + c0 + j;
-            const float vx = VX[s], vy = VY[s], vz = VZ[s];
-            float acc = 0.f;
-            if (vx != 0.f || vy != 0.f || vz != 0.f) {
-                const float fx = X[s] * inv_hx, fy = Y[s] * inv_hy;
-                float fz = fminf(fmaxf(Z[s] * inv_hz - 0.5f, 0.f), (float)(Nz - 1));
-                const float flx = floorf(fx), fly = floorf(fy);
-                int k0 = min((int)floorf(fz), Nz - 2);
-                const float wx = fx - flx, wy = fy - fly, wz = fz - (float)k0;
+            const T vx = VX[s], vy = VY[s], vz = VZ[s];
+            T acc = 0;
+            if (vx != 0 || vy != 0 || vz != 0) {
+                const T one = 1;
+                const T fx = (T)X[s] * inv_hx, fy = (T)Y[s] * inv_hy;
+                T fz = (T)Z[s] * inv_hz - (T)0.5;
+                fz = fz < (T)0 ? (T)0 : (fz > (T)(Nz - 1) ? (T)(Nz - 1) : fz);
+                const T flx = floor(fx), fly = floor(fy);
+                int k0 = min((int)floor(fz), Nz - 2);
+                const T wx = fx - flx, wy = fy - fly, wz = fz - (T)k0;
                 int i0 = ((int)flx % Nx + Nx) % Nx, j0 = ((int)fly % Ny + Ny) % Ny;
                 const int i1 = (i0 + 1) % Nx, j1 = (j0 + 1) % Ny;
-                const float* hb = H + (size_t)n * 3 * npts;
-                float w[3] = {0.f, 0.f, 0.f};
+                const T* hb = H + (size_t)n * 3 * npts;
+                T w[3] = {0, 0, 0};
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float* h = hb + (size_t)c * npts;
+                    const T* h = hb + (size_t)c * npts;
                     const size_t a00 = ((size_t)i0 * Ny + j0) * Nz + k0, a01 = ((size_t)i0 * Ny + j1) * Nz + k0;
                     const size_t a10 = ((size_t)i1 * Ny + j0) * Nz + k0, a11 = ((size_t)i1 * Ny + j1) * Nz + k0;
-                    const float v00 = (1.f - wz) * h[a00] + wz * h[a00 + 1];
-                    const float v01 = (1.f - wz) * h[a01] + wz * h[a01 + 1];
-                    const float v10 = (1.f - wz) * h[a10] + wz * h[a10 + 1];
-                    const float v11 = (1.f - wz) * h[a11] + wz * h[a11 + 1];
-                    w[c] = (1.f - wx) * ((1.f - wy) * v00 + wy * v01) + wx * ((1.f - wy) * v10 + wy * v11);
+                    const T v00 = (one - wz) * h[a00] + wz * h[a00 + 1];
+                    const T v01 = (one - wz) * h[a01] + wz * h[a01 + 1];
+                    const T v10 = (one - wz) * h[a10] + wz * h[a10 + 1];
+                    const T v11 = (one - wz) * h[a11] + wz * h[a11 + 1];
+                    w[c] = (one - wx) * ((one - wy) * v00 + wy * v01) + wx * ((one - wy) * v10 + wy * v11);
                 }
                 acc = w[0] * vx + w[1] * vy + w[2] * vz;
             }
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(256) eq1_kernel(const float* __restrict__ H, i
             const int jmax = min(mc - 1, m - c0);
             for (int j = 0; j <= jmax; ++j) {
                 const Eq1Lag L = lags[m - (c0 + j)];
-                q += (double)L.w0 * f[j * nt + L.n] + (double)L.w1 * f[j * nt + min(L.n + 1, nt - 1)];
+                q += (double)L.w0 * (double)f[j * nt + L.n] + (double)L.w1 * (double)f[j * nt + min(L.n + 1, nt - 1)];
             }
             Q[m] += q * dt;
         }
@@ -86,17 +89,33 @@ __global__ void __launch_bounds__(256) eq1_kernel(const float* __restrict__ H, i
     }
 }
 
+template <class T>
+static void eq1_launch_t(cudaStream_t s, const T* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
+                         const float* x, const float* y, const float* z, const float* vx, const float* vy,
+                         const float* vz, const float* q, float qconst, int n_tracks, int n_steps, int n_out,
+                         double dt, double v_w, const void* lags, float* out) {
+    size_t sh = (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15) + (size_t)n_out * sizeof(double);
+    if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
+    WT_CUDA(cudaFuncSetAttribute(eq1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    eq1_kernel<T><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y, z, vx,
+                                            vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
+                                            static_cast<const Eq1Lag*>(lags), out);
+    WT_LAUNCH("eq1");
+}
 void eq1_launch(cudaStream_t s, const float* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                 const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
                 const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
                 const void* lags, float* out) {
-    size_t sh = (size_t)EQ1_MC * nt * sizeof(float) + 8 + (size_t)n_out * sizeof(double);
-    if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
-    WT_CUDA(cudaFuncSetAttribute(eq1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    eq1_kernel<<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly), (float)(Nz / Lz), x, y,
-                                         z, vx, vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
-                                         static_cast<const Eq1Lag*>(lags), out);
-    WT_LAUNCH("eq1");
+    eq1_launch_t<float>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out,
+                        dt, v_w, lags, out);
+}
+// FP64 field (plain path): interpolation in FP64, the same FP64 accumulation.
+void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
+                  const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
+                  const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
+                  const void* lags, float* out) {
+    eq1_launch_t<double>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out,
+                         dt, v_w, lags, out);
 }
 size_t eq1_lag_size() { return sizeof(Eq1Lag); }
 void eq1_pack_lag(void* dst, int n, float w0, float w1) { *static_cast<Eq1Lag*>(dst) = Eq1Lag{n, w0, w1}; }

@@ -6,27 +6,35 @@
 //   H[t][c][p] = sum_{m < 32} W[t][m] E[c][m][p]
 //
 // One CTA per SM, persistent over work units (128 grid points x one field
-// component).  Per unit the 128 x 32 slice of E is split into TF32 hi/lo
-// parts in shared memory (128-byte swizzled, K-major); the time
-// coefficients W (hi/lo) stay in shared memory for the whole kernel.  Three
-// tcgen05.mma products (hi*hi + hi*lo + lo*hi, kind::tf32, FP32
-// accumulation in tensor memory) give FP32-level accuracy.  The accumulator
-// D[p][t] lives in TMEM (lane = grid point, column = time sample), double
-// buffered in two 256-column halves; four epilogue warps drain it with
-// tcgen05.ld and write H with fully coalesced 128-byte warp stores (32
-// consecutive grid points of one time sample).
+// component).  Per unit the 128 x 32 slice of E arrives by a 2D TMA load
+// (double buffered) and is split into TF32 hi/lo parts in shared memory
+// (128-byte swizzled, K-major); the time coefficients W (hi/lo) stay in
+// shared memory for the whole kernel.  Three tcgen05.mma products
+// (hi*hi + hi*lo + lo*hi, kind::tf32, FP32 accumulation in tensor memory)
+// give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
+// grid point, column = time sample), double buffered in two 256-column
+// halves; eight epilogue warps (two per TMEM lane quadrant, alternate
+// 32-column slices) drain it with tcgen05.ld and write H with fully
+// coalesced 128-byte warp stores (32 consecutive grid points of one time
+// sample).
 //
-// Warp roles: warp 0 producer, warp 1 TMEM owner + MMA issuer, warps 2-5
-// epilogue.  Every mbarrier wait gives up after ~2 s (globaltimer), sets
-// the device error word and lets the CTA unwind, draining its own MMAs
-// before freeing tensor memory.
+// Warp roles: warp 0 producer (TMA issue + hi/lo conversion), warp 1 TMEM
+// owner + MMA issuer, warps 2-9 epilogue.  Every mbarrier wait gives up
+// after ~2 s (globaltimer), sets the device error word and lets the CTA
+// unwind: the producer waits (bounded) for the TMA loads it still has in
+// flight and the MMA thread drains its own MMAs before tensor memory is
+// freed.
 #include "wt_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace wt {
 
 namespace tc {
 
 constexpr int BM = 128;            // grid points per unit (TMEM lanes)
+constexpr int NEPI = 8;            // epilogue warps
 constexpr int KR = 32;             // basis rank (TF32 elements per 128-byte row)
 constexpr int NCH = 256;           // time samples per accumulator half
 constexpr int TILE_BYTES = BM * 128;  // one 128 x 32 TF32 tile
@@ -69,6 +77,28 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
             return false;
         }
     }
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// 2D tiled TMA load into shared memory, completion signalled on an mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Drain wait used while unwinding: ignores the abort flag, still bounded in time.
+__device__ __forceinline__ bool mbar_wait_drain(unsigned long long* b, unsigned parity, int* d_err) {
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try(b, parity)) {
+        if (globaltimer() - t0 > TIMEOUT_NS) {
+            atomicMax(d_err, (int)DERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -119,24 +149,27 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+constexpr int RAW_BYTES = KR * BM * 4;   // one raw FP32 slice [32 basis][128 points]
+
 struct Smem {
-    // tiles first (1024-byte aligned base)
-    // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo]
-    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], drain;
+    // tiles first (1024-byte aligned base):
+    // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo], raw[2][32][128] FP32
+    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain;
     unsigned tmem_base;
     int abort_flag;
 };
 
-__global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restrict__ E, const float* __restrict__ W,
-                                                           int nt, int nt_pad, size_t npts, int n_tiles,
-                                                           float* __restrict__ H, int* __restrict__ d_err) {
+__global__ void __launch_bounds__(64 + 32 * NEPI, 1)
+    expand_tc_kernel(const __grid_constant__ CUtensorMap emap, const float* __restrict__ W, int nt, int nt_pad,
+                     size_t npts, int n_tiles, float* __restrict__ H, int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // align the tile region to 1024 bytes
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char* b_hi = base;
     unsigned char* b_lo = b_hi + (size_t)nt_pad * 128;
     unsigned char* a_tiles = b_lo + (size_t)nt_pad * 128;          // [stage][hi|lo] x TILE_BYTES
-    Smem* S = reinterpret_cast<Smem*>(a_tiles + 4 * TILE_BYTES);
+    float* raw = reinterpret_cast<float*>(a_tiles + 4 * TILE_BYTES);  // [2][KR][BM]
+    Smem* S = reinterpret_cast<Smem*>(reinterpret_cast<unsigned char*>(raw) + 2 * RAW_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_units = n_tiles * 3;
     const int n_chunks = (nt_pad + NCH - 1) / NCH;
@@ -146,7 +179,8 @@ __global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restri
             mbar_init(&S->a_full[i], 32);
             mbar_init(&S->a_empty[i], 1);
             mbar_init(&S->acc_full[i], 1);
-            mbar_init(&S->acc_empty[i], 128);
+            mbar_init(&S->acc_empty[i], 32 * NEPI);
+            mbar_init(&S->raw_full[i], 1);
         }
         mbar_init(&S->drain, 1);
         S->abort_flag = 0;
@@ -173,42 +207,59 @@ __global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restri
     volatile int* abort_flag = &S->abort_flag;
 
     if (warp == 0) {
-        // ---------------- producer: E slice -> hi/lo swizzled A tiles
+        // ---------------- producer: TMA loads of raw E slices, hi/lo conversion into swizzled A tiles
+        int issued = 0;          // raw loads issued (unit k of this CTA goes to buffer k & 1)
+        if (lane == 0)
+            for (; issued < 2; ++issued) {
+                const int u = blockIdx.x + issued * gridDim.x;
+                if (u >= n_units) break;
+                mbar_expect_tx(&S->raw_full[issued], RAW_BYTES);
+                tma_load_2d(raw + issued * KR * BM, &emap, (u / 3) * BM, (u % 3) * KR, &S->raw_full[issued]);
+            }
+        issued = __shfl_sync(0xffffffffu, issued, 0);
         int i = 0;
         for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++i) {
             const int st = i & 1;
             if (!mbar_wait(&S->a_empty[st], ((i >> 1) & 1) ^ 1, abort_flag, d_err)) break;
-            const int tile = u / 3, c = u % 3;
-            const size_t p0 = (size_t)tile * BM;
+            if (!mbar_wait(&S->raw_full[st], (i >> 1) & 1, abort_flag, d_err)) break;
             unsigned char* ah = a_tiles + (size_t)(2 * st) * TILE_BYTES;
             unsigned char* al = ah + TILE_BYTES;
-            const float* src = E + ((size_t)c * KR + lane) * npts + p0;   // lane = k (basis index)
-            const bool full = p0 + BM <= npts;
-#pragma unroll 4
-            for (int r4 = 0; r4 < BM / 4; ++r4) {
-                float4 v;
-                if (full) {
-                    v = __ldg(reinterpret_cast<const float4*>(src) + r4);
-                } else {
-                    const size_t p = p0 + 4 * r4;
-                    v.x = p + 0 < npts ? src[4 * r4 + 0] : 0.f;
-                    v.y = p + 1 < npts ? src[4 * r4 + 1] : 0.f;
-                    v.z = p + 2 < npts ? src[4 * r4 + 2] : 0.f;
-                    v.w = p + 3 < npts ? src[4 * r4 + 3] : 0.f;
-                }
-                const float vv[4] = {v.x, v.y, v.z, v.w};
+            const float* rb = raw + st * KR * BM;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int row = 4 * r4 + j;
-                    const unsigned hi = to_tf32(vv[j]);
-                    const unsigned lo = to_tf32(vv[j] - __uint_as_float(hi));
-                    *reinterpret_cast<unsigned*>(ah + sw128(row, lane)) = hi;
-                    *reinterpret_cast<unsigned*>(al + sw128(row, lane)) = lo;
+            for (int rr = 0; rr < BM / 32; ++rr) {
+                const int row = lane + 32 * rr;                   // lane = grid point
+#pragma unroll
+                for (int c = 0; c < KR / 4; ++c) {
+                    unsigned hi[4], lo[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float x = rb[(4 * c + j) * BM + row];
+                        hi[j] = to_tf32(x);
+                        lo[j] = to_tf32(x - __uint_as_float(hi[j]));
+                    }
+                    const unsigned off = sw128(row, 4 * c);
+                    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(smem_u32(ah + off)), "r"(hi[0]),
+                                 "r"(hi[1]), "r"(hi[2]), "r"(hi[3])
+                                 : "memory");
+                    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(smem_u32(al + off)), "r"(lo[0]),
+                                 "r"(lo[1]), "r"(lo[2]), "r"(lo[3])
+                                 : "memory");
                 }
             }
-            fence_proxy_async();
+            fence_proxy_async();     // A tiles for the tensor core; raw buffer reads before the TMA refill
+            __syncwarp();
+            if (lane == 0) {
+                const int u2 = u + 2 * gridDim.x;
+                if (u2 < n_units) {
+                    mbar_expect_tx(&S->raw_full[st], RAW_BYTES);
+                    tma_load_2d(raw + st * KR * BM, &emap, (u2 / 3) * BM, (u2 % 3) * KR, &S->raw_full[st]);
+                }
+            }
+            if (u + 2 * gridDim.x < n_units) ++issued;
             mbar_arrive(&S->a_full[st]);
         }
+        // loads still in flight after an abort: wait for them (bounded) before the CTA exits
+        for (int k = i; k < issued; ++k) mbar_wait_drain(&S->raw_full[k & 1], (k >> 1) & 1, d_err);
     } else if (warp == 1) {
         // ---------------- MMA issuer (lane 0)
         int i = 0, g = 0;
@@ -248,12 +299,14 @@ __global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restri
         // drain: every MMA this thread issued has completed before TMEM is freed
         if (lane == 0) {
             mma_commit(&S->drain);
-            mbar_wait(&S->drain, 0, abort_flag, d_err);
+            mbar_wait_drain(&S->drain, 0, d_err);
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: TMEM -> H
-        const int q = warp & 3;                      // TMEM lane quadrant of this warp
+        // ---------------- epilogue: TMEM -> H; warps 2..9, quadrant warp & 3, column slice (warp - 2) / 4
+        const int q = warp & 3;
+        const int slice = (warp - 2) >> 2;
+        constexpr int NSL = NEPI / 4;
         int g = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -266,7 +319,7 @@ __global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restri
                 if (!mbar_wait(&S->acc_full[b], (g >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
                 const int n = min(NCH, nt_pad - ch * NCH);
-                for (int j = 0; j < n; j += 32) {
+                for (int j = slice * 32; j < n; j += 32 * NSL) {
                     float v[32];
                     tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), v);
                     const int t0 = ch * NCH + j;
@@ -293,7 +346,20 @@ __global__ void __launch_bounds__(192, 1) expand_tc_kernel(const float* __restri
 bool expand_tc_available() { return true; }
 
 size_t expand_tc_smem(int nt_pad) {
-    return 1024 + (size_t)2 * nt_pad * 128 + 4 * (size_t)tc::TILE_BYTES + sizeof(tc::Smem);
+    return 1024 + (size_t)2 * nt_pad * 128 + 4 * (size_t)tc::TILE_BYTES + 2 * (size_t)tc::RAW_BYTES + sizeof(tc::Smem);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        WT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) fail(WT_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
 }
 
 // E: [3][32][npts] FP32, W: [nt][32] FP32, H: [nt][3][npts] FP32.
@@ -302,14 +368,27 @@ void expand_tc(cudaStream_t s, const float* E, int r_pad, const float* W, int nt
     const int nt_pad = ((nt + 31) / 32) * 32;
     if (nt_pad > 512) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion handles at most 512 time samples");
     if (npts % 4) fail(WT_ERR_UNSUPPORTED, "grid size must be a multiple of 4");
+    if (reinterpret_cast<uintptr_t>(E) % 16) fail(WT_ERR_ARG, "basis fields must be 16-byte aligned");
+    // E viewed as 96 rows (component x basis index) of npts points; one box = 32 rows x 128 points
+    CUtensorMap emap;
+    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)3 * tc::KR};
+    cuuint64_t strides[1] = {(cuuint64_t)npts * sizeof(float)};
+    cuuint32_t box[2] = {tc::BM, tc::KR};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = tensor_map_encoder()(&emap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(E), dims, strides,
+                                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(WT_ERR_CUDA, "tensor map for the basis fields: error " + std::to_string((int)r));
     const size_t sh = expand_tc_smem(nt_pad);
-    int dev = 0, n_sm = 0;
+    int dev = 0, n_sm = 0, max_sh = 0;
     WT_CUDA(cudaGetDevice(&dev));
     WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
     WT_CUDA(cudaFuncSetAttribute(tc::expand_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     const int n_tiles = (int)((npts + tc::BM - 1) / tc::BM);
     const int grid = std::min(n_sm, n_tiles * 3);
-    tc::expand_tc_kernel<<<grid, 192, sh, s>>>(E, W, nt, nt_pad, npts, n_tiles, H, d_err);
+    tc::expand_tc_kernel<<<grid, 64 + 32 * tc::NEPI, sh, s>>>(emap, W, nt, nt_pad, npts, n_tiles, H, d_err);
     WT_LAUNCH("expand_tc");
 }
 

@@ -59,7 +59,7 @@ struct Fast32 {
     size_t rho_elems(int nb) const { return (size_t)nb * g.Nz * (g.Nx / 2 + 1) * g.Ny * 2; }
     size_t r_elems(int nb) const { return (size_t)nb * 3 * g.Nz * g.Nx * g.Ny; }
     void fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
-                cudaStream_t s) const;
+                cudaStream_t s, int mode = 0) const;
 };
 
 }  // namespace wt

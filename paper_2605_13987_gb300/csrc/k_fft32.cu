@@ -72,14 +72,18 @@ __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __res
 // inverse FFT along y for every m_x row, then half spectrum -> real along x.
 // Warp FFTs in registers; the plane stays in shared memory.
 // Output R[b][c][mz][y][x].  grid (Nz, 3, nb).
+// mode 0: the field; mode 1: its derivative with respect to the lateral scale
+// lambda (Lx, Ly, column and grid positions scale together): the multiplier
+// times (-3 + 2 k_perp^2/|k|^2) for W_x, W_y and (-2 + 2 k_perp^2/|k|^2) for W_z.
 template <int RY, int RX>
-__global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
+__global__ void __launch_bounds__(256, 2) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
                                                         const C2<float>* __restrict__ twy,
-                                                        const C2<float>* __restrict__ twx, float* __restrict__ R) {
+                                                        const C2<float>* __restrict__ twx, float* __restrict__ R,
+                                                        int mode) {
     extern __shared__ unsigned char smem_raw[];
     const int nx = g.Nx, ny = g.Ny, nz = g.Nz, nxh = nx / 2 + 1;
     const int mz = blockIdx.x, comp = blockIdx.y, b = blockIdx.z;
-    const int ldp = ny + 1;
+    const int ldp = (ny + 1) | 1;                              // odd pitch: conflict-free column reads
     C2<float>* P = reinterpret_cast<C2<float>*>(smem_raw);     // [nxh][ldp]
     C2<float>* ty = P + (size_t)nxh * ldp;                     // [ny]
     C2<float>* tx = ty + ny;                                   // [nx]
@@ -103,7 +107,8 @@ __global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<floa
             const float k2 = kx * kx + ky * ky + kz * kz;
             if (k2 > 0.f) {
                 const C2<float> r = rp[e];
-                const float gk = pref / k2 * (mx ? 2.f : 1.f);     // x half-spectrum fold
+                float gk = pref / k2 * (mx ? 2.f : 1.f);           // x half-spectrum fold
+                if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + 2.f * (kx * kx + ky * ky) / k2;
                 // cosine components carry no w(m_z) here: the z pass builds
                 // d_m = C e, d_{2N-m} = C e*, which already sums the +-k_z pair
                 if (comp == 0) { const float f = kx * gk; v = {r.y * f, -r.x * f}; }
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<floa
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {   // y: nxh lines of length ny
+    {   // y: nxh lines of length ny (decimation in time: lanes read consecutive elements)
         const int W = ny / RY, G = 32 / W, grp = lane / W, gl = lane % W;
         const int k2 = warp_fft_k2(gl, W);
         for (int base = warp * G; base < nxh; base += 8 * G) {
@@ -123,30 +128,39 @@ __global__ void __launch_bounds__(256) f32_plane_kernel(GridDev g, const C2<floa
             const bool act = mx < nxh;
             C2<float> v[RY];
 #pragma unroll
-            for (int j = 0; j < RY; ++j) v[j] = act ? P[mx * ldp + j + RY * gl] : C2<float>{0.f, 0.f};
-            warp_fft<RY>(v, gl, W, ty, ny);
+            for (int j = 0; j < RY; ++j) v[j] = act ? P[mx * ldp + gl + W * j] : C2<float>{0.f, 0.f};
+            warp_fft_dit<RY>(v, gl, W, ty, ny);
             if (act)
 #pragma unroll
-                for (int k = 0; k < RY; ++k) P[mx * ldp + k2 + W * k] = v[k];
+                for (int k = 0; k < RY; ++k) P[mx * ldp + k + RY * k2] = v[k];
         }
     }
     __syncthreads();
-    {   // x: ny lines of length nx from the half spectrum (m_x >= nx/2 are zero)
+    {   // x: ny lines of length nx from the half spectrum (m_x >= nx/2 are zero); decimation in
+        // time reads consecutive rows per lane; results go through a per-warp line for coalesced stores
         const int W = nx / RX, G = 32 / W, grp = lane / W, gl = lane % W;
         const int k2 = warp_fft_k2(gl, W);
+        float* stg = reinterpret_cast<float*>(tx + nx) + (size_t)warp * 32 / W * nx;
         for (int base = warp * G; base < ny; base += 8 * G) {
             const int y = base + grp;
             const bool act = y < ny;
             C2<float> v[RX];
 #pragma unroll
             for (int j = 0; j < RX; ++j) {
-                const int mx = j + RX * gl;
+                const int mx = gl + W * j;
                 v[j] = (act && mx < nx / 2) ? P[mx * ldp + y] : C2<float>{0.f, 0.f};
             }
-            warp_fft<RX>(v, gl, W, tx, nx);
-            if (act)
+            warp_fft_dit<RX>(v, gl, W, tx, nx);
+            float* st = stg + (size_t)grp * nx;
 #pragma unroll
-                for (int k = 0; k < RX; ++k) Rout[(size_t)y * nx + k2 + W * k] = v[k].x;
+            for (int k = 0; k < RX; ++k) st[k + RX * k2] = v[k].x;
+            __syncwarp();
+            for (int g2 = 0; g2 < G; ++g2) {
+                const int yy = base + g2;
+                if (yy < ny)
+                    for (int x = lane; x < nx; x += 32) Rout[(size_t)yy * nx + x] = stg[(size_t)g2 * nx + x];
+            }
+            __syncwarp();
         }
     }
 }
@@ -157,8 +171,12 @@ constexpr int F32_LB = 32;   // (x, y) lines per z-pass block
 // lines share one length-2Nz complex warp FFT.  Lines L = y Nx + x of the
 // plane kernel's layout; output in H's point order (x Ny + y) Nz + z.
 // grid (ceil(Nx Ny / F32_LB), 3, nb).
+// Skewed index of coefficient m in a staged line pair: a gap every R entries
+// makes the per-lane chunk stride R + 1, so the reads are free of bank conflicts.
+__device__ __forceinline__ int zskew(int m, int R) { return m + m / R; }
+
 template <int RZ>
-__global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
+__global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
                                                         const C2<float>* __restrict__ twz,
                                                         const C2<float>* __restrict__ zsh, float* __restrict__ out,
                                                         size_t out_sb, size_t out_sc) {
@@ -167,15 +185,17 @@ __global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* 
     const size_t nxy = (size_t)nx * ny;
     const int comp = blockIdx.y, b = blockIdx.z;
     const size_t L0 = (size_t)blockIdx.x * F32_LB;
-    float* in = reinterpret_cast<float*>(smem_raw);                          // [nz][F32_LB]
-    C2<float>* tw = reinterpret_cast<C2<float>*>(in + (size_t)nz * F32_LB);   // [n2]
-    C2<float>* zs = tw + n2;                                                 // [nz]
+    const int S = (zskew(nz - 1, RZ) + 1) | 1;                              // odd pair pitch
+    C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [F32_LB/2][S]
+    C2<float>* tw = cs + (size_t)(F32_LB / 2) * S;                          // [n2]
+    C2<float>* zs = tw + n2;                                                // [nz]
     for (int e = threadIdx.x; e < n2; e += blockDim.x) tw[e] = twz[e];
     for (int e = threadIdx.x; e < nz; e += blockDim.x) zs[e] = zsh[e];
     const float* src = R + ((size_t)b * 3 + comp) * nz * nxy + L0;
+    float* csf = reinterpret_cast<float*>(cs);
     for (int e = threadIdx.x; e < nz * F32_LB; e += blockDim.x) {
         const int m = e / F32_LB, l = e % F32_LB;
-        in[e] = (L0 + l < nxy) ? src[(size_t)m * nxy + l] : 0.f;
+        csf[2 * ((l >> 1) * S + zskew(m, RZ)) + (l & 1)] = (L0 + l < nxy) ? src[(size_t)m * nxy + l] : 0.f;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,6 +204,7 @@ __global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* 
     float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
     for (int base = warp * G; base < F32_LB / 2; base += 8 * G) {
         const int f = base + grp;                 // lines 2f, 2f+1 of this block
+        const C2<float>* cf = cs + (size_t)f * S;
         C2<float> v[RZ];
 #pragma unroll
         for (int j1 = 0; j1 < RZ; ++j1) {
@@ -191,7 +212,7 @@ __global__ void __launch_bounds__(256) f32_zpass_kernel(GridDev g, const float* 
             C2<float> d = {0.f, 0.f};
             if (j != nz) {
                 const int m = j < nz ? j : n2 - j;
-                const C2<float> c = {in[m * F32_LB + 2 * f], in[m * F32_LB + 2 * f + 1]};
+                const C2<float> c = cf[zskew(m, RZ)];
                 if (comp < 2) {
                     if (j == 0) d = c;
                     else d = j < nz ? cmul(c, zs[m]) : cmul(c, C2<float>{zs[m].x, -zs[m].y});
@@ -227,12 +248,18 @@ __global__ void f32_twiddle_kernel(float* tw, int N) {
     tw[2 * k + 1] = (float)sn;
 }
 
+static int plane_ldp(const GridDev& g) { return (g.Ny + 1) | 1; }     // odd row pitch (complex units)
 static size_t plane_smem(const GridDev& g) {
     const int nxh = g.Nx / 2 + 1;
-    return ((size_t)nxh * (g.Ny + 1) + g.Ny + g.Nx) * sizeof(C2<float>);
+    int W, R;
+    warp_fft_shape(g.Nx, &W, &R);
+    return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>) + (size_t)8 * (32 / W) * g.Nx * sizeof(float);
 }
 static size_t zpass_smem(const GridDev& g) {
-    return (size_t)g.Nz * F32_LB * sizeof(float) + (size_t)3 * g.Nz * sizeof(C2<float>);
+    int W, R;
+    warp_fft_shape(2 * g.Nz, &W, &R);
+    const size_t S = (size_t)(((g.Nz - 1) + (g.Nz - 1) / R + 1) | 1);
+    return ((size_t)(F32_LB / 2) * S + 3 * (size_t)g.Nz) * sizeof(C2<float>);
 }
 static size_t deposit_smem(const GridDev& g, int n_cols) {
     return (size_t)n_cols * (g.Nx / 2 + 1 + g.Ny) * sizeof(C2<float>);
@@ -294,7 +321,7 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
 }
 
 void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
-                    cudaStream_t s) const {
+                    cudaStream_t s, int mode) const {
     C2<float>* rc = reinterpret_cast<C2<float>*>(rho);
     dim3 gd(g.Nz, nb);
     f32_deposit_kernel<<<gd, 256, deposit_smem(g, n_cols), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
@@ -304,7 +331,7 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     const C2<float>* ty = reinterpret_cast<const C2<float>*>(tw_y.p);
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(tw_x.p);
     switch (rxy) {
-#define WT_CASE(RR) case RR: f32_plane_kernel<RR, RR><<<gp, 256, plane_smem(g), s>>>(g, rc, ty, tx, R); break;
+#define WT_CASE(RR) case RR: f32_plane_kernel<RR, RR><<<gp, 256, plane_smem(g), s>>>(g, rc, ty, tx, R, mode); break;
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }

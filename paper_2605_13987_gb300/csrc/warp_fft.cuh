@@ -14,9 +14,10 @@
 
 namespace wt {
 
-// R-point DFT in registers (exp(+i)); w_R^m = tw[(m mod R) * (N / R)].
+// R-point DFT in registers (exp(+i)); w_R^m = tw[(m mod R) * U] with U = N / R
+// the table's stride for this DFT length (no runtime division inside).
 template <int R>
-__device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __restrict__ tw, int N) {
+__device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __restrict__ tw, int U) {
     if constexpr (R == 1) {
         return;
     } else if constexpr (R == 2) {
@@ -33,12 +34,11 @@ __device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __re
         v[3] = csub(d02, id13);
     } else if constexpr (R == 3 || R == 5 || R == 7) {
         C2<float> o[R];
-        const int st = N / R;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             C2<float> acc = v[0];
 #pragma unroll
-            for (int j = 1; j < R; ++j) acc = cadd(acc, cmul(v[j], tw[((j * k) % R) * st]));
+            for (int j = 1; j < R; ++j) acc = cadd(acc, cmul(v[j], tw[((j * k) % R) * U]));
             o[k] = acc;
         }
 #pragma unroll
@@ -54,16 +54,16 @@ __device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __re
             C2<float> t[B];
 #pragma unroll
             for (int j2 = 0; j2 < B; ++j2) t[j2] = v[j1 + A * j2];
-            reg_dft<B>(t, tw, N);
+            reg_dft<B>(t, tw, U * A);
 #pragma unroll
-            for (int k2 = 0; k2 < B; ++k2) y[j1][k2] = (j1 && k2) ? cmul(t[k2], tw[((j1 * k2) % R) * (N / R)]) : t[k2];
+            for (int k2 = 0; k2 < B; ++k2) y[j1][k2] = (j1 && k2) ? cmul(t[k2], tw[((j1 * k2) % R) * U]) : t[k2];
         }
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
             C2<float> t[A];
 #pragma unroll
             for (int j1 = 0; j1 < A; ++j1) t[j1] = y[j1][k2];
-            reg_dft<A>(t, tw, N);
+            reg_dft<A>(t, tw, U * B);
 #pragma unroll
             for (int k1 = 0; k1 < A; ++k1) v[k2 + B * k1] = t[k1];
         }
@@ -72,10 +72,13 @@ __device__ __forceinline__ void reg_dft(C2<float> (&v)[R], const C2<float>* __re
 
 template <int R>
 __device__ __forceinline__ void warp_fft(C2<float> (&v)[R], int gl, int W, const C2<float>* __restrict__ tw, int N) {
-    // (1) W-point DFTs across the lane group, one per j1
-    for (int h = W >> 1; h >= 1; h >>= 1) {
+    (void)N;
+    // (1) W-point DFTs across the lane group, one per j1; the stage twiddle
+    // w_{2h}^{gl mod h} = tw[(gl mod h) * R * W / (2h)], stride doubling as h halves
+    int step = R;
+    for (int h = W >> 1; h >= 1; h >>= 1, step <<= 1) {
         const bool bottom = gl & h;
-        const C2<float> w = tw[(gl & (h - 1)) * (N / (2 * h))];
+        const C2<float> w = tw[(gl & (h - 1)) * step];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const C2<float> a = v[j];
@@ -87,9 +90,32 @@ __device__ __forceinline__ void warp_fft(C2<float> (&v)[R], int gl, int W, const
     const int lw = 31 - __clz(W);                 // log2 W
     const int k2 = lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;
 #pragma unroll
-    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], tw[(j * k2) % N]);
+    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], tw[j * k2]);          // j k2 < N
     // (3) R-point DFTs in registers: X[k2 + W k1] = sum_j1 w_R^{j1 k1} ...
-    reg_dft<R>(v, tw, N);
+    reg_dft<R>(v, tw, W);
+}
+
+// Decimation-in-time form: lane l starts with v[j1] = x[l + W j1] (consecutive
+// lanes hold consecutive elements) and ends with v[k1] = X[k1 + R bitrev_W(l)]:
+//   X[k1 + R k2] = sum_j2 w_W^{j2 k2} w_N^{j2 k1} sum_j1 x[j2 + W j1] w_R^{j1 k1}.
+template <int R>
+__device__ __forceinline__ void warp_fft_dit(C2<float> (&v)[R], int gl, int W, const C2<float>* __restrict__ tw,
+                                             int N) {
+    (void)N;
+    reg_dft<R>(v, tw, W);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[gl * k]);          // gl k < N
+    int step = R;
+    for (int h = W >> 1; h >= 1; h >>= 1, step <<= 1) {
+        const bool bottom = gl & h;
+        const C2<float> w = tw[(gl & (h - 1)) * step];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const C2<float> a = v[j];
+            const C2<float> b = {__shfl_xor_sync(0xffffffffu, a.x, h), __shfl_xor_sync(0xffffffffu, a.y, h)};
+            v[j] = bottom ? cmul(csub(b, a), w) : cadd(a, b);
+        }
+    }
 }
 
 __device__ __forceinline__ int warp_fft_k2(int gl, int W) {

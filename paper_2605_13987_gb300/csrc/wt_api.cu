@@ -38,6 +38,17 @@ void eq1_launch(cudaStream_t, const float*, int, int, int, int, double, double, 
                 const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
                 double, const void*, float*);
 size_t eq1_lag_size();
+void eq1_launch64(cudaStream_t, const double*, int, int, int, int, double, double, double, const float*, const float*,
+                  const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
+                  double, const void*, float*);
+void green_lateral_deriv(cudaStream_t, const double*, const double*, int, int, int, int, double, double, double, double,
+                         int, double*);
+void modal_inv_gap(cudaStream_t, const double*, int, double*);
+void modal_tangent(cudaStream_t, const double*, const double*, const double*, const double*, const double*,
+                   const double*, int, int, double*);
+void modal_omega(cudaStream_t, const double*, const double*, const double*, int, double*);
+void add_row_const(cudaStream_t, double*, int, int, const double*);
+double dot_f32(cudaStream_t, const float*, const float*, size_t, double*);
 void eq1_noalloc_launch(cudaStream_t, int, const float*, int, int, int, const double*, int, double, double, double,
                         const float*, const float*, const float*, const float*, const float*, const float*,
                         const float*, float, int, int, int, double, double, float*);
@@ -104,6 +115,13 @@ struct wt_ctx {
     DBuf<float> stage32;
     DBuf<double> stage64;
     wt_info info{};
+    // kept from the fit for the derivative (wt_eq1_loss_grad)
+    DBuf<double> fitA, fitD, fitL, fitY;      // scaled fit matrix, column scales, Cholesky factor, scaled solution
+    std::vector<double> f_dxy, f_uxy, f_hzc;  // lateral offsets / radial directions per combo, collocation heights
+    std::vector<int> f_ctoff;
+    std::vector<unsigned char> f_blocks;
+    int f_ncombo = 0, f_maxrows = 0, f_maxcols = 0;
+    std::vector<double> k_diag, k_off, k_k1;  // resistive lines
     // stage timing (wt_set_timing)
     bool timing = false;
     bool use_tc = true;          // WT_EXPAND=simt selects the FP32 FMA expansion
@@ -261,7 +279,7 @@ void do_fit(wt_ctx* c) {
     T.alloc((size_t)(g.Nx / 2) * (g.Ny / 2) * g.Nz);
     green_invk2(s, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, T.p);
     const int n_tg = ncol * n_az;                  // target lateral groups
-    std::vector<double> hdxy;
+    std::vector<double> hdxy, huxy;
     for (int k = 0; k < ncol; ++k)
         for (int a = 0; a < n_az; ++a) {
             const double th = c->opts.az0 + 2.0 * kPi * a / n_az;
@@ -270,6 +288,8 @@ void do_fit(wt_ctx* c) {
             for (int k2 = 0; k2 < ncol; ++k2) {
                 hdxy.push_back(tx - c->cols[k2].x);
                 hdxy.push_back(ty - c->cols[k2].y);
+                huxy.push_back(std::cos(th));
+                huxy.push_back(std::sin(th));
             }
         }
     const int n_combo = n_tg * ncol;
@@ -305,6 +325,14 @@ void do_fit(wt_ctx* c) {
                 max_rows = std::max(max_rows, nh);
                 max_cols = std::max(max_cols, c->cols[k2].n_sources);
             }
+    c->f_dxy = hdxy;
+    c->f_uxy = huxy;
+    c->f_hzc = hzc;
+    c->f_ctoff = ct_off;
+    c->f_blocks = blocks;
+    c->f_ncombo = n_combo;
+    c->f_maxrows = max_rows;
+    c->f_maxcols = max_cols;
     DBuf<unsigned char> dblocks;
     dblocks.upload(blocks.data(), blocks.size(), s);
     P.alloc((size_t)nc * ns);
@@ -410,8 +438,11 @@ void do_fit(wt_ctx* c) {
         for (double x : h) { mx = std::max(mx, std::fabs(x)); mn = std::min(mn, std::fabs(x)); }
         c->info.cond_estimate = mn > 0 ? mx / mn : INFINITY;
     }
-    G.release();
-    P.release();
+    // keep the factors for the derivative of the fit (scaled A, D, Cholesky factor, scaled solution)
+    c->fitY.alloc((size_t)ns * ns);
+    copy_block(s, Y.p, ns, c->fitY.p, ns, ns, ns);
+    c->fitL.take(G);
+    c->fitA.take(P);
     // X = D Y; offsets = row 0; F = H [0; X_1:]
     scale_rows(s, Y.p, ns, ns, ns, dcol.p);
     c->offset.alloc(ns);
@@ -430,6 +461,7 @@ void do_fit(wt_ctx* c) {
     c->info.asymmetry = nF > 0 ? nA / nF : 0.0;
     check_finite(s, c->Cn.p, (size_t)ns * ns, c->d_err.p);
     if (read_err(c)) fail(WT_ERR_NAN, "non-finite capacitance");
+    c->fitD.take(dcol);
     c->info.n_columns = ncol;
     c->info.n_sources = ns;
     c->info.n_colloc = nc;
@@ -451,6 +483,57 @@ void charges_at(wt_ctx* c, const double* d_t, int nt, double* Q) {
     rank1(s, ns, nt, -c->beta, c->hv.p, vz.p, Zf.p, nt);
     dgemm(s, false, false, ns, nt, ns, 1.0, c->Cn.p, ns, Zf.p, nt, 0.0, Q, nt);
     add_column_vector(s, Q, ns, nt, c->qinf.p);
+}
+
+// Rank-r (r <= 32) time basis of a charge history Q [ns][nt] (Gram matrix +
+// Jacobi, singular values above 1e-9 of the largest): basis charge vectors
+// Ub [r][ns] (unit norm) and FP32 coefficients W32 [nt][32] = sigma_m w_m[t].
+void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf<float>& W32, int& rank_out,
+                      double& trunc_out) {
+    cudaStream_t s = c->s;
+    const int ns = c->ns;
+    DBuf<double> Gt, Wg, lam;
+    Gt.alloc((size_t)nt * nt);
+    dgemm(s, true, false, nt, nt, ns, 1.0, Q, nt, Q, nt, 0.0, Gt.p, nt);
+    Wg.alloc((size_t)nt * nt);
+    lam.alloc(nt);
+    clear_err(c);
+    jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver (time basis) did not converge");
+    std::vector<double> hl(nt), hw((size_t)nt * nt);
+    lam.download(hl.data(), nt, s);
+    Wg.download(hw.data(), (size_t)nt * nt, s);
+    WT_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> ord(nt);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return hl[a] > hl[b]; });
+    const double s0 = std::sqrt(std::max(hl[ord[0]], 0.0));
+    const int r_max = std::min(32, nt);
+    int r = 0;
+    while (r < r_max && s0 > 0 && std::sqrt(std::max(hl[ord[r]], 0.0)) > 1e-9 * s0) ++r;
+    if (r < 1) r = 1;
+    rank_out = r;
+    trunc_out = (r < nt && s0 > 0) ? std::sqrt(std::max(hl[ord[r]], 0.0)) / s0 : 0.0;
+    const int rp = 32;
+    std::vector<double> wsel((size_t)nt * r), coef((size_t)nt * rp, 0.0);
+    for (int m = 0; m < r; ++m) {
+        const double sg = std::sqrt(std::max(hl[ord[m]], 0.0));
+        for (int tt = 0; tt < nt; ++tt) {
+            const double wv = hw[(size_t)tt * nt + ord[m]];
+            wsel[(size_t)tt * r + m] = sg > 0 ? wv / sg : 0.0;
+            coef[(size_t)tt * rp + m] = sg * wv;
+        }
+    }
+    DBuf<double> dws, Ubt, dcoef;
+    dws.upload(wsel.data(), wsel.size(), s);
+    Ubt.alloc((size_t)ns * r);
+    dgemm(s, false, false, ns, r, nt, 1.0, Q, nt, dws.p, r, 0.0, Ubt.p, r);
+    Ub.alloc((size_t)r * ns);
+    transpose(s, Ubt.p, ns, r, Ub.p);
+    dcoef.upload(coef.data(), coef.size(), s);
+    W32.alloc(coef.size());
+    to_float(s, dcoef.p, coef.size(), 1.0, W32.p);
+    WT_CUDA(cudaStreamSynchronize(s));
 }
 
 void do_relax(wt_ctx* c, const double* t, int nt) {
@@ -476,6 +559,9 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
         diag[jt] -= 2.0 * gs;
         k1[jt] = -2.0 * gs;                 // K 1: only the terminal leak survives
     }
+    c->k_diag = diag;
+    c->k_off = off;
+    c->k_k1 = k1;
     double s1 = 0;
     for (double x : k1) s1 += x;
     DBuf<double> dd, doff, dk1, K, Am, Sm;
@@ -563,50 +649,8 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
     check_finite(s, c->Qt.p, (size_t)nt * ns, c->d_err.p);
     if (read_err(c)) fail(WT_ERR_NAN, "non-finite charges");
     // S5b: time basis of the charge history (Gram matrix + Jacobi)
-    {
-        DBuf<double> Gt, Wg, lam;
-        Gt.alloc((size_t)nt * nt);
-        dgemm(s, true, false, nt, nt, ns, 1.0, Q.p, nt, Q.p, nt, 0.0, Gt.p, nt);
-        Wg.alloc((size_t)nt * nt);
-        lam.alloc(nt);
-        jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p);
-        if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver (time basis) did not converge");
-        std::vector<double> hl(nt), hw((size_t)nt * nt);
-        lam.download(hl.data(), nt, s);
-        Wg.download(hw.data(), (size_t)nt * nt, s);
-        WT_CUDA(cudaStreamSynchronize(s));
-        std::vector<int> ord(nt);
-        std::iota(ord.begin(), ord.end(), 0);
-        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return hl[a] > hl[b]; });
-        const double s0 = std::sqrt(std::max(hl[ord[0]], 0.0));
-        const int r_max = std::min(32, nt);
-        int r = 0;
-        while (r < r_max && std::sqrt(std::max(hl[ord[r]], 0.0)) > 1e-9 * s0) ++r;
-        if (r < 1) r = 1;
-        c->rank = r;
-        c->r_pad = 32;
-        c->info.trunc_rel = (r < nt && s0 > 0) ? std::sqrt(std::max(hl[ord[r]], 0.0)) / s0 : 0.0;
-        // basis charges u_m = Q w_m / sigma_m ([r][ns]); coefficients sigma_m w_m[t]
-        std::vector<double> wsel((size_t)nt * r), coef((size_t)nt * c->r_pad, 0.0);
-        for (int m = 0; m < r; ++m) {
-            const double sg = std::sqrt(std::max(hl[ord[m]], 0.0));
-            for (int tt = 0; tt < nt; ++tt) {
-                const double wv = hw[(size_t)tt * nt + ord[m]];
-                wsel[(size_t)tt * r + m] = sg > 0 ? wv / sg : 0.0;
-                coef[(size_t)tt * c->r_pad + m] = sg * wv;
-            }
-        }
-        DBuf<double> dws, Ubt, dcoef;
-        dws.upload(wsel.data(), wsel.size(), s);
-        Ubt.alloc((size_t)ns * r);
-        dgemm(s, false, false, ns, r, nt, 1.0, Q.p, nt, dws.p, r, 0.0, Ubt.p, r);
-        c->Ub.alloc((size_t)r * ns);
-        transpose(s, Ubt.p, ns, r, c->Ub.p);
-        dcoef.upload(coef.data(), coef.size(), s);
-        c->W32.alloc(coef.size());
-        to_float(s, dcoef.p, coef.size(), 1.0, c->W32.p);
-        WT_CUDA(cudaStreamSynchronize(s));
-    }
+    c->r_pad = 32;
+    compress_history(c, Q.p, nt, c->Ub, c->W32, c->rank, c->info.trunc_rel);
     c->info.n_t = nt;
     c->info.rank = c->rank;
     c->info.relax_seconds = secs(t0);
@@ -626,6 +670,54 @@ void ensure_spectral(wt_ctx* c) {
     column_cos_table(c->s, c->d_zsrc.p, c->ns, g.Nz, g.Lz, c->zcos.p);
     WT_CUDA(cudaStreamSynchronize(c->s));
     c->sp_ready = true;
+}
+
+// FP32 fast path for a basis of charge vectors Ub [r][ns] and coefficients
+// W32 [nt][32]: column transforms, basis fields (mode 0: the field, 1: its
+// lateral-scale derivative) and the expansion into out [nt][3][npts].
+void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt, float* out, cudaStream_t s, int mode,
+                    int* launches, bool timing) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int ncol = (int)c->cols.size();
+    const int rp = 32;
+    const int nb = 1;     // one charge vector per batch keeps the intermediates in L2
+    c->Zc32.alloc((size_t)rp * ncol * g.Nz);
+    c->rho32.alloc(c->sp32.rho_elems(nb));
+    c->R32.alloc(c->sp32.r_elems(nb));
+    c->E32.alloc((size_t)3 * rp * npts);
+    if (r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
+    column_ztransform<float>(s, Ub, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
+    *launches += 1;
+    if (timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
+    for (int m0 = 0; m0 < r; m0 += nb) {
+        const int b = std::min(nb, r - m0);
+        c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p, c->E32.p + (size_t)m0 * npts,
+                       npts, (size_t)rp * npts, s, mode);
+        *launches += 3;
+    }
+    if (timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
+    if (c->use_tc && expand_tc_available()) expand_tc(s, c->E32.p, rp, W32, nt, npts, out, c->d_err.p);
+    else expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
+    *launches += 1;
+    if (timing) WT_CUDA(cudaEventRecord(c->ev[3], s));
+}
+
+// FP64 plain path: one spectral transform per time sample into out [nt][3][npts].
+void extend64(wt_ctx* c, double* out, cudaStream_t s, int* launches) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int nt = (int)c->times.size(), ncol = (int)c->cols.size();
+    const int nb = 4;
+    c->Zc64.alloc((size_t)nb * ncol * g.Nz);
+    c->G64.alloc(c->sp64.scratch_elems(nb));
+    for (int t0 = 0; t0 < nt; t0 += nb) {
+        const int b = std::min(nb, nt - t0);
+        column_ztransform<double>(s, c->Qt.p + (size_t)t0 * c->ns, b, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol,
+                                  g.Nz, c->Zc64.p);
+        c->sp64.fields(c->Zc64.p, b, c->G64.p, out + (size_t)t0 * 3 * npts, 3 * npts, npts, s);
+        *launches += 4;
+    }
 }
 
 void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t us) {
@@ -653,16 +745,7 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
     int launches = 0;
     if (prec == WT_FP64) {
         double* out = dev ? static_cast<double*>(H) : c->stage64.p;
-        const int nb = 4;
-        c->Zc64.alloc((size_t)nb * ncol * g.Nz);
-        c->G64.alloc(c->sp64.scratch_elems(nb));
-        for (int t0 = 0; t0 < nt; t0 += nb) {
-            const int b = std::min(nb, nt - t0);
-            column_ztransform<double>(s, c->Qt.p + (size_t)t0 * c->ns, b, c->ns, c->ns, c->zcos.p, c->d_col_off.p,
-                                      ncol, g.Nz, c->Zc64.p);
-            c->sp64.fields(c->Zc64.p, b, c->G64.p, out + (size_t)t0 * 3 * npts, 3 * npts, npts, s);
-            launches += 4;
-        }
+        extend64(c, out, s, &launches);
         if (c->timing) {
             WT_CUDA(cudaEventRecord(c->ev[1], s));
             WT_CUDA(cudaEventRecord(c->ev[2], s));
@@ -670,27 +753,7 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
         }
     } else {
         float* out = dev ? static_cast<float*>(H) : c->stage32.p;
-        const int r = c->rank, rp = c->r_pad;
-        const int nb = 1;     // one charge vector per batch keeps the intermediates in L2
-        c->Zc32.alloc((size_t)rp * ncol * g.Nz);
-        c->rho32.alloc(c->sp32.rho_elems(nb));
-        c->R32.alloc(c->sp32.r_elems(nb));
-        c->E32.alloc((size_t)3 * rp * npts);
-        if (r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
-        column_ztransform<float>(s, c->Ub.p, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
-        launches += 1;
-        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
-        for (int m0 = 0; m0 < r; m0 += nb) {
-            const int b = std::min(nb, r - m0);
-            c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p,
-                           c->E32.p + (size_t)m0 * npts, npts, (size_t)rp * npts, s);
-            launches += 3;
-        }
-        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
-        if (c->use_tc && expand_tc_available()) expand_tc(s, c->E32.p, rp, c->W32.p, nt, npts, out, c->d_err.p);
-        else expand_simt(s, c->E32.p, rp, c->W32.p, nt, rp, npts, out);
-        launches += 1;
-        if (c->timing) WT_CUDA(cudaEventRecord(c->ev[3], s));
+        extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, out, s, 0, &launches, c->timing);
     }
     c->last_launches = launches;
     c->ev_recorded = c->timing;
@@ -738,31 +801,14 @@ void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, dou
     }
 }
 
-void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStream_t us) {
-    const wt_grid& g = c->grid;
+// Lag table of Eq. 1: (k + 1/2) dt -> bracketing samples and weights (linear
+// in t; 0 at t = 0; held after the last sample).
+void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cudaStream_t s) {
     const int nt = (int)c->times.size();
-    if (!tr) fail(WT_ERR_ARG, "NULL tracks");
-    if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
-        fail(WT_ERR_ARG, "bad track sizes or dt");
-    if (tr->n_tracks == 0) return;     // nothing to convolve; no pointer is read
-    if (!H || !iout) fail(WT_ERR_ARG, "NULL argument");
-    if (!is_device_ptr(H)) fail(WT_ERR_ARG, "H must be device memory (FP32 output of wt_extend)");
-    if (!tr->x || !tr->y || !tr->z || !tr->vx || !tr->vy || !tr->vz) fail(WT_ERR_ARG, "NULL track array");
-    const size_t nts = (size_t)tr->n_tracks * tr->n_steps;
-    const bool dev_in = is_device_ptr(tr->x);
-    const bool dev_out = is_device_ptr(iout);
-    cudaStream_t s = (dev_in && dev_out) ? us : c->s;
-    const float* arr[7] = {tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz, tr->q};
-    DBuf<float> staged[7];
-    if (!dev_in) {
-        for (int k = 0; k < 6; ++k) { staged[k].upload(arr[k], nts, s); arr[k] = staged[k].p; }
-        if (tr->q) { staged[6].upload(tr->q, tr->n_tracks, s); arr[6] = staged[6].p; }
-    }
-    // lag table: (k + 1/2) dt -> bracketing samples and weights (linear in t; 0 at t = 0; held at the end)
-    std::vector<unsigned char> lag(eq1_lag_size() * (size_t)tr->n_out);
+    std::vector<unsigned char> lag(eq1_lag_size() * (size_t)n_out);
     const std::vector<double>& ts = c->times;
-    for (int k = 0; k < tr->n_out; ++k) {
-        const double L = (k + 0.5) * tr->dt;
+    for (int k = 0; k < n_out; ++k) {
+        const double L = (k + 0.5) * dt;
         int n0 = 0;
         double w0 = 0, w1 = 0;
         if (L <= ts.front()) { n0 = 0; w0 = L / ts.front(); }
@@ -775,17 +821,310 @@ void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStre
         }
         eq1_pack_lag(lag.data() + eq1_lag_size() * k, n0, (float)w0, (float)w1);
     }
-    DBuf<unsigned char> dlag;
     dlag.upload(lag.data(), lag.size(), s);
+}
+
+struct TrackDev {
+    const float *x, *y, *z, *vx, *vy, *vz, *q;
+    float qconst;
+    int n_tracks, n_steps, n_out;
+    double dt;
+};
+
+void check_tracks(const wt_tracks* tr) {
+    if (!tr) fail(WT_ERR_ARG, "NULL tracks");
+    if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
+        fail(WT_ERR_ARG, "bad track sizes or dt");
+}
+
+// Device view of the tracks; host arrays are copied into `keep`.
+TrackDev stage_tracks(wt_ctx* c, const wt_tracks* tr, DBuf<float> (&keep)[7], cudaStream_t s) {
+    if (!tr->x || !tr->y || !tr->z || !tr->vx || !tr->vy || !tr->vz) fail(WT_ERR_ARG, "NULL track array");
+    const size_t nts = (size_t)tr->n_tracks * tr->n_steps;
+    const float* arr[7] = {tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz, tr->q};
+    if (!is_device_ptr(tr->x)) {
+        for (int k = 0; k < 6; ++k) { keep[k].upload(arr[k], nts, s); arr[k] = keep[k].p; }
+        if (tr->q) { keep[6].upload(tr->q, tr->n_tracks, s); arr[6] = keep[6].p; }
+    }
+    return TrackDev{arr[0], arr[1], arr[2], arr[3], arr[4], arr[5], tr->q ? arr[6] : nullptr, (float)tr->charge,
+                    tr->n_tracks, tr->n_steps, tr->n_out, tr->dt};
+}
+
+void eq1_run(wt_ctx* c, const void* H, bool h64, const TrackDev& t, float* out, cudaStream_t s,
+             const float* vz_override = nullptr) {
+    const wt_grid& g = c->grid;
+    const int nt = (int)c->times.size();
+    DBuf<unsigned char> dlag;
+    build_lags(c, t.dt, t.n_out, dlag, s);
+    const float* vz = vz_override ? vz_override : t.vz;
+    if (h64)
+        eq1_launch64(s, static_cast<const double*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx,
+                     t.vy, vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, out);
+    else
+        eq1_launch(s, static_cast<const float*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
+                   vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, out);
+    WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
+}
+
+void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStream_t us) {
+    check_tracks(tr);
+    if (tr->n_tracks == 0) return;     // nothing to convolve; no pointer is read
+    if (!H || !iout) fail(WT_ERR_ARG, "NULL argument");
+    if (!is_device_ptr(H)) fail(WT_ERR_ARG, "H must be device memory (FP32 output of wt_extend)");
+    const bool dev_in = is_device_ptr(tr->x);
+    const bool dev_out = is_device_ptr(iout);
+    cudaStream_t s = (dev_in && dev_out) ? us : c->s;
+    DBuf<float> keep[7];
+    const TrackDev td = stage_tracks(c, tr, keep, s);
     DBuf<float> dout;
     float* o = iout;
     if (!dev_out) { dout.alloc((size_t)tr->n_tracks * tr->n_out); o = dout.p; }
-    eq1_launch(s, static_cast<const float*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, arr[0], arr[1], arr[2], arr[3],
-               arr[4], arr[5], tr->q ? arr[6] : nullptr, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out,
-               tr->dt, c->opts.v_w, dlag.p, o);
-    if (!dev_out) dout.download(iout, (size_t)tr->n_tracks * tr->n_out, s);
-    // staged inputs and the lag table are freed on return: finish first
-    WT_CUDA(cudaStreamSynchronize(s));
+    eq1_run(c, H, false, td, o, s);
+    if (!dev_out) {
+        dout.download(iout, (size_t)tr->n_tracks * tr->n_out, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+// H M (right Householder product) for M rows x ns, in place.
+void house_right(wt_ctx* c, double* M, int rows) {
+    DBuf<double> w;
+    w.alloc(rows);
+    dgemv(c->s, false, rows, c->ns, 1.0, M, c->ns, c->hv.p, 0.0, w.p);
+    rank1(c->s, rows, c->ns, -c->beta, w.p, c->hv.p, M, c->ns);
+}
+// H M (left Householder product) for M ns x cols, in place.
+void house_left(wt_ctx* c, double* M, int cols) {
+    DBuf<double> u;
+    u.alloc(cols);
+    dgemv(c->s, true, c->ns, cols, 1.0, M, cols, c->hv.p, 0.0, u.p);
+    rank1(c->s, c->ns, cols, -c->beta, c->hv.p, u.p, M, cols);
+}
+
+double do_loss(wt_ctx* c, wt_precision prec, const wt_tracks* tr) {
+    check_tracks(tr);
+    ensure_spectral(c);
+    cudaStream_t s = c->s;
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int nt = (int)c->times.size();
+    if (tr->n_tracks == 0) return 0.0;
+    DBuf<float> keep[7];
+    const TrackDev td = stage_tracks(c, tr, keep, s);
+    int launches = 0;
+    const void* H;
+    if (prec == WT_FP64) {
+        c->stage64.alloc((size_t)nt * 3 * npts);
+        extend64(c, c->stage64.p, s, &launches);
+        H = c->stage64.p;
+    } else {
+        c->stage32.alloc((size_t)nt * 3 * npts);
+        extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, c->stage32.p, s, 0, &launches, false);
+        H = c->stage32.p;
+    }
+    const size_t nI = (size_t)tr->n_tracks * tr->n_out;
+    DBuf<float> I;
+    I.alloc(nI);
+    eq1_run(c, H, prec == WT_FP64, td, I.p, s);
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out");
+    return dot_f32(s, I.p, I.p, nI, c->d_scr.p) / (double)nI;
+}
+
+// Derivative of L = mean i^2 with respect to [readout resistivity scale, bias
+// resistivity scale, radius, lateral scale], tangent-linear through the fit,
+// the relaxation modes, the extension and Eq. 1 (see include/wt.h).
+void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
+    check_tracks(tr);
+    if (c->opts.tikhonov > 0.0) fail(WT_ERR_UNSUPPORTED, "the derivative assumes an unregularised fit");
+    ensure_spectral(c);
+    cudaStream_t s = c->s;
+    const wt_grid& g = c->grid;
+    const int ns = c->ns, n1 = ns - 1, nc = c->nc, ncol = (int)c->cols.size();
+    const int nt = (int)c->times.size();
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    for (int k = 0; k < 4; ++k) grad[k] = 0.0;
+    *loss = 0.0;
+    if (tr->n_tracks == 0) return;
+    DBuf<float> keep[7];
+    const TrackDev td = stage_tracks(c, tr, keep, s);
+    const size_t nI = (size_t)tr->n_tracks * tr->n_out;
+    int launches = 0;
+    clear_err(c);
+    // base field and currents
+    c->stage32.alloc((size_t)nt * 3 * npts);
+    extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, c->stage32.p, s, 0, &launches, false);
+    DBuf<float> I, dI;
+    I.alloc(nI);
+    dI.alloc(nI);
+    eq1_run(c, c->stage32.p, false, td, I.p, s);
+    *loss = dot_f32(s, I.p, I.p, nI, c->d_scr.p) / (double)nI;
+    const double gscale = 2.0 / (double)nI;
+
+    // shared pieces: fit residual, modal factors, inverse gaps, potentials Phi(t)
+    DBuf<int> sp, si;
+    DBuf<double> sw, Rs, E, AE, ones, invg, Phi, dphi;
+    sp.upload(c->s_ptr.data(), c->s_ptr.size(), s);
+    si.upload(c->s_idx.data(), c->s_idx.size(), s);
+    sw.upload(c->s_w.data(), c->s_w.size(), s);
+    Rs.alloc((size_t)nc * ns);
+    dgemm(s, false, false, nc, ns, ns, -1.0, c->fitA.p, ns, c->fitY.p, ns, 0.0, Rs.p, ns);
+    fit_add_s(s, Rs.p, ns, ns, sp.p, si.p, sw.p, 1.0);
+    std::vector<double> h1(n1, 1.0);
+    ones.upload(h1.data(), n1, s);
+    E.alloc((size_t)n1 * nt);
+    modal_factors(s, ones.p, c->mu.p, n1, c->d_times.p, nt, E.p);
+    AE.alloc((size_t)n1 * nt);
+    modal_factors(s, c->amp.p, c->mu.p, n1, c->d_times.p, nt, AE.p);
+    invg.alloc((size_t)n1 * n1);
+    modal_inv_gap(s, c->mu.p, n1, invg.p);
+    Phi.alloc((size_t)ns * nt);
+    Phi.zero(s);
+    dgemm(s, false, false, n1, nt, n1, 1.0, c->Vm.p, n1, AE.p, nt, 0.0, Phi.p + nt, nt);
+    house_left(c, Phi.p, nt);
+    dphi.upload(c->phi_dc.data(), ns, s);
+    add_row_const(s, Phi.p, ns, nt, dphi.p);
+    // tables for the derivative of the fit matrix
+    DBuf<double> zc_all, zs_all, Ct, Cs, ddxy, duxy, Ld;
+    DBuf<unsigned char> dblocks;
+    zc_all.upload(c->f_hzc.data(), c->f_hzc.size(), s);
+    zs_all.upload(c->src_z.data(), ns, s);
+    Ct.alloc(c->f_hzc.size() * g.Nz);
+    Cs.alloc((size_t)ns * g.Nz);
+    green_cos_table(s, zc_all.p, (int)c->f_hzc.size(), g.Nz, g.Lz, Ct.p);
+    green_cos_table(s, zs_all.p, ns, g.Nz, g.Lz, Cs.p);
+    ddxy.upload(c->f_dxy.data(), c->f_dxy.size(), s);
+    dblocks.upload(c->f_blocks.data(), c->f_blocks.size(), s);
+    Ld.alloc((size_t)c->f_ncombo * g.Nz);
+    DBuf<float> dH, zeros;
+    dH.alloc((size_t)nt * 3 * npts);
+    zeros.alloc((size_t)td.n_tracks * td.n_steps);
+    zeros.zero(s);
+    DBuf<double> dCn, dKt, T, tmp, dP, Sh, Ah, Om, Mm, cm, dz, dQ, dQq, dgv, dqi;
+    for (int p = 0; p < 4; ++p) {
+        const bool has_dc = p >= 2, has_dk = p <= 2;
+        // ---- fit tangent: dC_n
+        if (has_dc) {
+            std::vector<double> uxy(c->f_uxy);
+            if (p == 3) {      // lateral scale: the radial offset r_c (ux, uy) of the target column
+                const int n_az = c->opts.n_az;
+                for (int cb = 0; cb < c->f_ncombo; ++cb) {
+                    const int k = (cb / ncol) / n_az;
+                    uxy[2 * cb] *= c->cols[k].radius;
+                    uxy[2 * cb + 1] *= c->cols[k].radius;
+                }
+            }
+            duxy.upload(uxy.data(), uxy.size(), s);
+            green_lateral_deriv(s, ddxy.p, duxy.p, c->f_ncombo, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, 1.0, p - 2, Ld.p);
+            dP.alloc((size_t)nc * ns);
+            green_pblocks(s, dblocks.p, c->f_ncombo, c->f_maxrows, c->f_maxcols, Ct.p, Cs.p, Ld.p, g.Nz, c->pref,
+                          dP.p, ns);
+            house_right(c, dP.p, nc);
+            set_column(s, dP.p, nc, ns, 0, 0.0);
+            scale_columns(s, dP.p, nc, ns, ns, c->fitD.p);                    // dA_s
+            tmp.alloc((size_t)nc * ns);
+            dgemm(s, false, false, nc, ns, ns, 1.0, dP.p, ns, c->fitY.p, ns, 0.0, tmp.p, ns);
+            T.alloc((size_t)ns * ns);
+            dgemm(s, true, false, ns, ns, nc, -1.0, c->fitA.p, ns, tmp.p, ns, 0.0, T.p, ns);
+            dgemm(s, true, false, ns, ns, nc, 1.0, dP.p, ns, Rs.p, ns, 1.0, T.p, ns);
+            trsm_lower(s, c->fitL.p, ns, ns, T.p, ns, ns);
+            trsm_lower_t(s, c->fitL.p, ns, ns, T.p, ns, ns);
+            scale_rows(s, T.p, ns, ns, ns, c->fitD.p);                        // dX
+            fill(s, T.p, ns, 0.0);
+            house_left(c, T.p, ns);                                          // dF
+            dCn.alloc((size_t)ns * ns);
+            symmetrize_avg(s, T.p, dCn.p, ns);
+        }
+        // ---- resistive-line tangent: dK~
+        if (has_dk) {
+            std::vector<double> dd(ns, 0.0), doff(ns, 0.0), dk1(ns, 0.0);
+            for (int k = 0; k < ncol; ++k) {
+                const wt_column& col = c->cols[k];
+                double f = 0.0;
+                if (p == 0 && col.terminal_top) f = -1.0;        // G ~ 1/rho: dG/ds = -G
+                if (p == 1 && !col.terminal_top) f = -1.0;
+                if (p == 2) f = 2.0 / col.radius;                  // G ~ r^2
+                for (int j = c->col_off[k]; j < c->col_off[k + 1]; ++j) {
+                    dd[j] = f * c->k_diag[j];
+                    doff[j] = f * c->k_off[j];
+                    dk1[j] = f * c->k_k1[j];
+                }
+            }
+            double s1 = 0, ds1 = 0;
+            for (int j = 0; j < ns; ++j) { s1 += c->k_k1[j]; ds1 += dk1[j]; }
+            DBuf<double> d_dd, d_doff, d_dk1, d_k1;
+            d_dd.upload(dd.data(), ns, s);
+            d_doff.upload(doff.data(), ns, s);
+            d_dk1.upload(dk1.data(), ns, s);
+            d_k1.upload(c->k_k1.data(), ns, s);
+            dKt.alloc((size_t)ns * ns);
+            build_k(s, d_dd.p, d_doff.p, ns, dKt.p);
+            rank1(s, ns, ns, -1.0 / s1, d_dk1.p, d_k1.p, dKt.p, ns);
+            rank1(s, ns, ns, -1.0 / s1, d_k1.p, d_dk1.p, dKt.p, ns);
+            rank1(s, ns, ns, ds1 / (s1 * s1), d_k1.p, d_k1.p, dKt.p, ns);
+            WT_CUDA(cudaStreamSynchronize(s));
+        }
+        // ---- modal tangent: Omega = V^T dS_m V - V^T dA_m V diag(mu)
+        tmp.alloc((size_t)n1 * n1);
+        Om.alloc((size_t)n1 * n1);
+        Sh.alloc((size_t)n1 * n1);
+        Sh.zero(s);
+        if (has_dk) {
+            householder_two_sided(c, dKt.p, ns);
+            dgemm(s, false, false, n1, n1, n1, -1.0, dKt.p + ns + 1, ns, c->Vm.p, n1, 0.0, tmp.p, n1);   // dS_m V
+            dgemm(s, true, false, n1, n1, n1, 1.0, c->Vm.p, n1, tmp.p, n1, 0.0, Sh.p, n1);
+        }
+        Ah.alloc((size_t)n1 * n1);
+        Ah.zero(s);
+        if (has_dc) {
+            DBuf<double> HC;
+            HC.alloc((size_t)ns * ns);
+            copy_block(s, dCn.p, ns, HC.p, ns, ns, ns);
+            householder_two_sided(c, HC.p, ns);
+            dgemm(s, false, false, n1, n1, n1, 1.0, HC.p + ns + 1, ns, c->Vm.p, n1, 0.0, tmp.p, n1);
+            dgemm(s, true, false, n1, n1, n1, 1.0, c->Vm.p, n1, tmp.p, n1, 0.0, Ah.p, n1);
+        }
+        modal_omega(s, Sh.p, has_dc ? Ah.p : nullptr, c->mu.p, n1, Om.p);
+        // c_mod = V^T dg - Ah amp, dg = -(H dq_inf)[1:], dq_inf = dC_n phi_DC
+        cm.alloc(n1);
+        cm.zero(s);
+        if (has_dc) {
+            dqi.alloc(ns);
+            dgemv(s, false, ns, ns, 1.0, dCn.p, ns, dphi.p, 0.0, dqi.p);
+            house_left(c, dqi.p, 1);
+            dgemv(s, true, n1, n1, -1.0, c->Vm.p, n1, dqi.p + 1, 0.0, cm.p);
+            dgemv(s, false, n1, n1, -1.0, Ah.p, n1, c->amp.p, 1.0, cm.p);
+        }
+        dz.alloc((size_t)n1 * nt);
+        modal_tangent(s, Om.p, c->amp.p, invg.p, E.p, c->d_times.p, cm.p, n1, nt, dz.p);
+        // dQ = C_n H [0; V dzeta] + dC_n Phi      [ns][nt]
+        dQ.alloc((size_t)ns * nt);
+        dQ.zero(s);
+        dgemm(s, false, false, n1, nt, n1, 1.0, c->Vm.p, n1, dz.p, nt, 0.0, dQ.p + nt, nt);
+        house_left(c, dQ.p, nt);
+        dQq.alloc((size_t)ns * nt);
+        dgemm(s, false, false, ns, nt, ns, 1.0, c->Cn.p, ns, dQ.p, nt, 0.0, dQq.p, nt);
+        if (has_dc) dgemm(s, false, false, ns, nt, ns, 1.0, dCn.p, ns, Phi.p, nt, 1.0, dQq.p, nt);
+        check_finite(s, dQq.p, (size_t)ns * nt, c->d_err.p);
+        // field and current tangents
+        DBuf<double> dUb;
+        DBuf<float> dW;
+        int dr = 0;
+        double dtr = 0.0;
+        compress_history(c, dQq.p, nt, dUb, dW, dr, dtr);
+        extend32_basis(c, dUb.p, dr, dW.p, nt, dH.p, s, 0, &launches, false);
+        eq1_run(c, dH.p, false, td, dI.p, s);
+        double acc = dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
+        if (p == 3) {
+            // derivative of the field operator itself, and of the lateral velocities
+            extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, dH.p, s, 1, &launches, false);
+            eq1_run(c, dH.p, false, td, dI.p, s);
+            acc += dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
+            eq1_run(c, c->stage32.p, false, td, dI.p, s, zeros.p);
+            acc += dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
+        }
+        grad[p] = gscale * acc;
+        if (read_err(c)) fail(WT_ERR_NAN, "non-finite or timed-out tangent");
+    }
 }
 
 }  // namespace
@@ -909,6 +1248,25 @@ wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tr, float
         eq1_noalloc_launch(static_cast<cudaStream_t>(stream), ctx->dev, H, g.Nx, g.Ny, g.Nz, ctx->d_times.p,
                            (int)ctx->times.size(), g.Lx, g.Ly, g.Lz, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz,
                            tr->q, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out, tr->dt, ctx->opts.v_w, i);
+    });
+}
+
+wt_status wt_eq1_loss(wt_ctx* ctx, wt_precision prec, const wt_tracks* tracks, double* loss) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_loss", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_loss needs wt_relax first");
+        if (!loss) fail(WT_ERR_ARG, "NULL output");
+        if (prec != WT_FP32 && prec != WT_FP64) fail(WT_ERR_ARG, "bad precision");
+        *loss = do_loss(ctx, prec, tracks);
+    });
+}
+
+wt_status wt_eq1_loss_grad(wt_ctx* ctx, const wt_tracks* tracks, double* loss, double* grad) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_loss_grad", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_loss_grad needs wt_relax first");
+        if (!loss || !grad) fail(WT_ERR_ARG, "NULL output");
+        do_loss_grad(ctx, tracks, loss, grad);
     });
 }
 

@@ -67,6 +67,13 @@ struct DBuf {
         n = count;
     }
     void zero(cudaStream_t s) { if (n) WT_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
+    void take(DBuf& o) {
+        release();
+        p = o.p;
+        n = o.n;
+        o.p = nullptr;
+        o.n = 0;
+    }
     void upload(const T* host, size_t count, cudaStream_t s) {
         alloc(count);
         if (count) WT_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
