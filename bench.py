@@ -40,6 +40,8 @@ WORKLOADS = {
     "c1": "c1: single cell 55x55x100 um, grid 32x32x64, 2 columns x 64 sources, 64 time samples",
     "small": "small: single cell 55x55x100 um, grid 64x64x64, 2 columns x 64 sources, 512 time samples "
              "(profiling case: H = 1.6 GB > L2)",
+    "c3": "c3: 64 single cells, pitch 40-110 um, thickness 300-500 um, radius 4-10 um, grids 64^2x128 to "
+          "128^2x256 (uneven), 256 time samples each; batched in waves through an H arena",
 }
 
 
@@ -181,6 +183,97 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "point-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "setup_s": setup}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """c3: 64 geometries through wt_batch_run, in waves whose H fits an arena
+    of --arena-gb; one captured graph (one persistent expansion launch) per
+    wave.  A step = every wave once (all 64 sensors' H written once)."""
+    import torch
+    import paper_2605_13987_gb300 as P
+    import workloads as W
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load_library()
+    ws = W.c3_batch(seed=3)
+    t0 = time.perf_counter()
+    sens = []
+    for w in ws:
+        s_ = P.Sensor(w.grid, w.columns, device=local)
+        s_.fit()
+        s_.relax(w.times)
+        sens.append(s_)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    sizes = [len(w.times) * 3 * w.grid.Nx * w.grid.Ny * w.grid.Nz for w in ws]     # floats of H
+    ps_step = sum(n // 3 for n in sizes)
+    # waves: consecutive sensors while their H fits the arena (256-byte aligned slices)
+    cap = int(args.arena_gb * 2 ** 30 // 4)
+    waves, cur, used = [], [], 0
+    for i, n in enumerate(sizes):
+        n_al = (n + 63) // 64 * 64
+        if cur and used + n_al > cap:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append((i, used))
+        used += n_al
+    waves.append(cur)
+    arena = torch.empty(max(sum((sizes[i] + 63) // 64 * 64 for i, _ in wv) for wv in waves), dtype=torch.float32,
+                        device=dev)
+    outs = [[arena[o:o + sizes[i]].view(sens[i].h_shape()) for i, o in wv] for wv in waves]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for wv, ob in zip(waves, outs):
+            P.extend_batch([sens[i] for i, _ in wv], outs=ob, stream=stream)
+
+    t1 = time.perf_counter()
+    step()                      # first call: autotuning and graph capture
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t1
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = a.elapsed_time(b) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    value = world * ps_step / (ms_max / 1e3)
+    peak, peak_kind = peaks()
+    tun = {}
+    for s_, w in zip(sens, ws):
+        tun[f"{w.grid.Nx}x{w.grid.Ny}x{w.grid.Nz}"] = s_.tuning()
+    if rank == 0:
+        line = {
+            "metric": "H grid-point*time-samples/sec (FP32 extension, 12 B/point-sample written once)",
+            "value": value, "unit": "point-samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c3"], "l2": "inputs and outputs (377 GB of H per step) far above L2",
+                       "parallelism": f"replicas x{world}", "waves": len(waves), "arena_gb": args.arena_gb,
+                       "sensors": len(ws), "point_samples": ps_step},
+            "roofline": {"bound": "hbm", "achieved": 12.0 * ps_step / (ms_max / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": 12.0 * ps_step / (ms_max / 1e3) / 1e9 / peak, "traffic": None,
+                         "kernel": "whole step (graphs of spectral passes + persistent expansion)",
+                         "peak_kind": peak_kind},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "clocks": clk.summary(local), "setup_s": setup, "first_call_s": capture_s, "tuning": tun,
+        }
+        print(json.dumps(line), flush=True)
+    for s_ in sens:
+        s_.close()
     return 0
 
 
@@ -332,6 +425,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--arena-gb", type=float, default=96.0, help="c3: device memory for one wave's H")
     ap.add_argument("--profile", action="store_true",
                     help="wrap only the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off); "
                          "skips the CPU baseline and e2e")
@@ -339,6 +433,8 @@ def main():
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -117,6 +117,8 @@ typedef struct {
     double trunc_rel;            /* sigma_{rank+1} / sigma_1 of the charge history */
     double mu_min, mu_max;       /* relaxation rates [1/s] */
     double fit_seconds, relax_seconds;
+    double grad_trunc_rel;       /* largest relative truncation of the charge tangents in the
+                                    last wt_eq1_loss_grad (rank-32 time bases) */
 } wt_info;
 
 /* Create a context on CUDA device `cuda_device` for the given grid.
@@ -195,6 +197,57 @@ wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, 
  * cuda_stream. */
 #define WT_EQ1_NOALLOC_MAX_OUT 16384
 wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tracks, float* i, void* cuda_stream);
+
+/* Loss of Eq. 1 currents, L = mean over tracks and output times of i(tau)^2
+ * (Sec. 4's current of each track with its own charge, Eq. 1), computed in
+ * one call: the field of the relaxed charges (WT_FP32: the fast path of
+ * wt_extend; WT_FP64: the plain FP64 path) into an internal buffer, then
+ * Eq. 1 on it.  Track arrays may be host or device memory (layout as in
+ * wt_eq1).  Synchronous; *loss written on success.  Needs wt_relax. */
+wt_status wt_eq1_loss(wt_ctx* ctx, wt_precision prec, const wt_tracks* tracks, double* loss);
+
+/* Gradient of the loss of wt_eq1_loss (FP32 field) with respect to four
+ * design parameters, by hand-written tangent-linear differentiation of the
+ * whole chain: the constrained least-squares fit (Sec. 3), the capacitance
+ * and resistive-line pencil and its modal solution (Sec. 5, derivative of
+ * the matrix exponential in the modal basis), the field extension and Eq. 1.
+ *   grad[0] = dL/ds_R   resistivity of the readout columns (terminal at the
+ *                       top) scaled by s_R, at s_R = 1;
+ *   grad[1] = dL/ds_B   the same for the bias columns (terminal at the bottom);
+ *   grad[2] = dL/dr     every column radius moved by dr [per metre];
+ *   grad[3] = dL/dlambda  lateral scale at lambda = 1: Lx, Ly, column centres
+ *                       and the tracks' x, y, vx, vy scale together (z,
+ *                       times and source counts fixed).
+ * The source counts per column stay fixed under every perturbation.  The
+ * fit must be unregularised (tikhonov = 0; WT_ERR_UNSUPPORTED otherwise).
+ * *loss receives L (FP32 field), grad[4] the gradient.  Synchronous;
+ * allocates device workspaces for the tangents and frees them on return. */
+wt_status wt_eq1_loss_grad(wt_ctx* ctx, const wt_tracks* tracks, double* loss, double* grad);
+
+/* Bulk extension of many sensors at once (FP32: the fast path of wt_extend
+ * for every context, batched; the paper runs one geometry at a time, so
+ * this is a property of the library).  ctxs[0..n-1]: relaxed contexts on
+ * one device, each at most once; H[i]: device buffer of context i, layout
+ * and size as wt_extend's.  FP32: the column transforms and spectral passes
+ * of every context and one persistent tensor-core expansion launch over all
+ * of them (one per 64 contexts) are captured once as a CUDA graph, kept on
+ * ctxs[0] (the four most recently used batches) and replayed by later calls
+ * with the same contexts, outputs and context states; a wt_relax on any of
+ * them re-captures.  Before the first capture of a grid shape (Nx, Ny, Nz,
+ * n_t) the autotuner times the candidate launch shapes on that context and
+ * keeps the fastest for the process (see wt_get_tuning); tuning writes into
+ * that context's H buffer.  The results equal wt_extend's bit for bit.
+ * FP64: the plain path of each context in turn.  Asynchronous on
+ * cuda_stream, ordered after the contexts' own pending work; the contexts'
+ * FP32 work buffers are shared with wt_extend, so do not run either on the
+ * same context concurrently. */
+wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
+
+/* Launch shapes the FP32 path of this context uses (set by the autotuner of
+ * wt_batch_run; defaults 1, 32, 256): shape3[0] charge vectors per spectral
+ * launch, shape3[1] (x, y) lines per z-pass block, shape3[2] time samples per
+ * expansion accumulator chunk. */
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape3);
 
 /* Copy intermediate results to host memory (for checks and diagnostics):
  * q: [n_t][n_sources] node charges (after wt_relax);

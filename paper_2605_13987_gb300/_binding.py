@@ -52,7 +52,8 @@ class wt_info(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("n_sources", C.c_int), ("n_colloc", C.c_int), ("n_t", C.c_int),
                 ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
                 ("asymmetry", C.c_double), ("trunc_rel", C.c_double), ("mu_min", C.c_double),
-                ("mu_max", C.c_double), ("fit_seconds", C.c_double), ("relax_seconds", C.c_double)]
+                ("mu_max", C.c_double), ("fit_seconds", C.c_double), ("relax_seconds", C.c_double),
+                ("grad_trunc_rel", C.c_double)]
 
 
 # name -> (restype, argtypes); the ABI of include/wt.h
@@ -66,6 +67,11 @@ SIGNATURES = {
                               C.POINTER(C.c_double)]),
     "wt_eq1": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
     "wt_eq1_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
+    "wt_eq1_loss": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(wt_tracks), C.POINTER(C.c_double)]),
+    "wt_eq1_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
+    "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_capacitance": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_modes": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -178,12 +184,17 @@ def wt_sample_H(ctx, xyz, times):
     return out
 
 
+def _tracks_struct(tracks):
+    """wt_tracks over the arrays of a track dict (the dict keeps them alive)."""
+    return wt_tracks(int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"]),
+                     float(tracks["dt"]), float(tracks.get("charge", 1.0)),
+                     _ptr(tracks["x"]), _ptr(tracks["y"]), _ptr(tracks["z"]),
+                     _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
+
+
 def wt_eq1(ctx, H, tracks, i_out, stream=None):
     lib = load_library()
-    tr = wt_tracks(int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"]),
-                   float(tracks["dt"]), float(tracks.get("charge", 1.0)),
-                   _ptr(tracks["x"]), _ptr(tracks["y"]), _ptr(tracks["z"]),
-                   _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
+    tr = _tracks_struct(tracks)
     st = _stream_handle(stream) if (hasattr(i_out, "is_cuda") and i_out.is_cuda) else None
     _check(lib.wt_eq1(ctx, _ptr(H), C.byref(tr), _ptr(i_out), st), ctx)
 
@@ -191,11 +202,42 @@ def wt_eq1(ctx, H, tracks, i_out, stream=None):
 def wt_eq1_noalloc(ctx, H, tracks, i_out, stream=None):
     """Eq. 1 with no device allocation: every buffer must be device memory."""
     lib = load_library()
-    tr = wt_tracks(int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"]),
-                   float(tracks["dt"]), float(tracks.get("charge", 1.0)),
-                   _ptr(tracks["x"]), _ptr(tracks["y"]), _ptr(tracks["z"]),
-                   _ptr(tracks["vx"]), _ptr(tracks["vy"]), _ptr(tracks["vz"]), _ptr(tracks.get("q")))
+    tr = _tracks_struct(tracks)
     _check(lib.wt_eq1_noalloc(ctx, _ptr(H), C.byref(tr), _ptr(i_out), _stream_handle(stream)), ctx)
+
+
+def wt_eq1_loss(ctx, precision, tracks):
+    lib = load_library()
+    tr = _tracks_struct(tracks)
+    out = C.c_double(0.0)
+    _check(lib.wt_eq1_loss(ctx, int(precision), C.byref(tr), C.byref(out)), ctx)
+    return out.value
+
+
+def wt_eq1_loss_grad(ctx, tracks):
+    """(loss, grad[4]) with grad = dL/d(s_R, s_B, r, lambda)."""
+    lib = load_library()
+    tr = _tracks_struct(tracks)
+    out = C.c_double(0.0)
+    g = np.zeros(4)
+    _check(lib.wt_eq1_loss_grad(ctx, C.byref(tr), C.byref(out), _dptr(g)), ctx)
+    return out.value, g
+
+
+def wt_batch_run(ctxs, precision, H_list, stream=None):
+    """Bulk extension of several relaxed contexts into their device buffers H_list."""
+    lib = load_library()
+    n = len(ctxs)
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    harr = (C.c_void_p * n)(*[h.data_ptr() for h in H_list])
+    _check(lib.wt_batch_run(carr, n, int(precision), harr, _stream_handle(stream)), ctxs[0])
+
+
+def wt_get_tuning(ctx):
+    lib = load_library()
+    out = (C.c_int * 3)()
+    _check(lib.wt_get_tuning(ctx, out), ctx)
+    return dict(nb=out[0], lb=out[1], nch=out[2])
 
 
 def wt_get_charges(ctx, n_t, n_sources):

@@ -156,6 +156,33 @@ __global__ void dot_f32_kernel(const float* __restrict__ a, const float* __restr
         if (threadIdx.x == 0) atomicAdd(out, acc);
     }
 }
+__global__ void dot_f64_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t n, double* out) {
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x / 32] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < blockDim.x / 32 ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+double dot_f64(cudaStream_t s, const double* a, const double* b, size_t n, double* d_scratch) {
+    WT_CUDA(cudaMemsetAsync(d_scratch, 0, sizeof(double), s));
+    if (n) {
+        int blocks = (int)std::min<size_t>(1024, (n + 255) / 256);
+        dot_f64_kernel<<<blocks, 256, 0, s>>>(a, b, n, d_scratch);
+        WT_LAUNCH("dot_f64");
+    }
+    double h = 0;
+    WT_CUDA(cudaMemcpyAsync(&h, d_scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+    WT_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
 double dot_f32(cudaStream_t s, const float* a, const float* b, size_t n, double* d_scratch) {
     WT_CUDA(cudaMemsetAsync(d_scratch, 0, sizeof(double), s));
     if (n) {

@@ -436,7 +436,7 @@ __device__ __forceinline__ int circle_player(int pos, int round, int m) {
 }
 
 __global__ void jacobi_angles_kernel(const double* __restrict__ A, int m, int lda, int n_real, int round,
-                                     double* __restrict__ cs, unsigned long long* __restrict__ n_rot) {
+                                     double abs_tol, double* __restrict__ cs, unsigned long long* __restrict__ n_rot) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m / 2) return;
     int p = circle_player(i, round, m), q = circle_player(m - 1 - i, round, m);
@@ -444,8 +444,9 @@ __global__ void jacobi_angles_kernel(const double* __restrict__ A, int m, int ld
     double c = 1.0, sn = 0.0, t = 0.0;
     if (q < n_real) {
         double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q], apq = A[(size_t)p * lda + q];
-        // rotate only when the coupling is above rounding relative to the diagonal
-        if (fabs(apq) > 1e-15 * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > 1e-300) {
+        // rotate only when the coupling is above rounding relative to the diagonal (and above
+        // the caller's absolute floor: couplings between rounding-level directions never settle)
+        if (fabs(apq) > 1e-15 * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > fmax(abs_tol, 1e-300)) {
             double tau = (aqq - app) / (2.0 * apq);
             t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
@@ -522,7 +523,8 @@ __global__ void eye_kernel(double* V, int n, int ld) {
     V[(size_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
 }
 
-int jacobi_eig(cudaStream_t s, double* A_in, int n, double* w, double* V_out, int* d_err, int max_sweeps) {
+int jacobi_eig(cudaStream_t s, double* A_in, int n, double* w, double* V_out, int* d_err, int max_sweeps,
+               double abs_tol) {
     // work on an even-sized copy (a padded index has zero coupling and never rotates)
     int m = n + (n & 1);
     if (m < 2) m = 2;
@@ -542,7 +544,7 @@ int jacobi_eig(cudaStream_t s, double* A_in, int n, double* w, double* V_out, in
     for (; sweeps < max_sweeps && !converged; ++sweeps) {
         WT_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
         for (int r = 0; r < m - 1; ++r) {
-            jacobi_angles_kernel<<<(half + 127) / 128, 128, 0, s>>>(A.p, m, m, n, r, cs.p, cnt.p);
+            jacobi_angles_kernel<<<(half + 127) / 128, 128, 0, s>>>(A.p, m, m, n, r, abs_tol, cs.p, cnt.p);
             size_t nb = (size_t)half * half;
             jacobi_apply_kernel<<<(nb + 255) / 256, 256, 0, s>>>(A.p, m, m, r, cs.p);
             size_t nv = (size_t)m * half;

@@ -17,10 +17,16 @@ struct Eq1Lag {
     int n;          // lower time sample
     float w0, w1;   // weights of samples n and n+1
 };
+// FP64 weights, for the FP64 field of the loss
+struct Eq1Lag64 {
+    int n;
+    double w0, w1;
+};
 
 constexpr int EQ1_MC = 16;   // track steps per chunk
 
-template <class T>
+// T: field type; L: lag table entry; TO: current type
+template <class T, class L, class TO>
 __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int Nx, int Ny, int Nz, int nt,
                                                   T inv_hx, T inv_hy, T inv_hz,
                                                   const float* __restrict__ X, const float* __restrict__ Y,
@@ -28,7 +34,7 @@ __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int N
                                                   const float* __restrict__ VY, const float* __restrict__ VZ,
                                                   const float* __restrict__ qtrack, float qconst, int n_steps,
                                                   int n_out, double dt, double inv_vw,
-                                                  const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
+                                                  const L* __restrict__ lags, TO* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* f = reinterpret_cast<T*>(smem_raw);                               // [EQ1_MC][nt]
     double* Q = reinterpret_cast<double*>(smem_raw + (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15));   // [n_out]
@@ -75,8 +81,8 @@ __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int N
             double q = 0.0;
             const int jmax = min(mc - 1, m - c0);
             for (int j = 0; j <= jmax; ++j) {
-                const Eq1Lag L = lags[m - (c0 + j)];
-                q += (double)L.w0 * (double)f[j * nt + L.n] + (double)L.w1 * (double)f[j * nt + min(L.n + 1, nt - 1)];
+                const L lg = lags[m - (c0 + j)];
+                q += (double)lg.w0 * (double)f[j * nt + lg.n] + (double)lg.w1 * (double)f[j * nt + min(lg.n + 1, nt - 1)];
             }
             Q[m] += q * dt;
         }
@@ -85,40 +91,42 @@ __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int N
     const float qc = qtrack ? qtrack[tr] : qconst;
     for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
         const double dq = Q[m] - (m ? Q[m - 1] : 0.0);
-        out[(size_t)tr * n_out + m] = (float)(-(double)qc * inv_vw * dq / dt);
+        out[(size_t)tr * n_out + m] = (TO)(-(double)qc * inv_vw * dq / dt);
     }
 }
 
-template <class T>
+template <class T, class L, class TO>
 static void eq1_launch_t(cudaStream_t s, const T* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                          const float* x, const float* y, const float* z, const float* vx, const float* vy,
                          const float* vz, const float* q, float qconst, int n_tracks, int n_steps, int n_out,
-                         double dt, double v_w, const void* lags, float* out) {
+                         double dt, double v_w, const void* lags, TO* out) {
     size_t sh = (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15) + (size_t)n_out * sizeof(double);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
-    WT_CUDA(cudaFuncSetAttribute(eq1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    eq1_kernel<T><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y, z, vx,
-                                            vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
-                                            static_cast<const Eq1Lag*>(lags), out);
+    WT_CUDA(cudaFuncSetAttribute(eq1_kernel<T, L, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    eq1_kernel<T, L, TO><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y,
+                                                   z, vx, vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
+                                                   static_cast<const L*>(lags), out);
     WT_LAUNCH("eq1");
 }
 void eq1_launch(cudaStream_t s, const float* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                 const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
                 const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
                 const void* lags, float* out) {
-    eq1_launch_t<float>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out,
-                        dt, v_w, lags, out);
+    eq1_launch_t<float, Eq1Lag, float>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks,
+                                       n_steps, n_out, dt, v_w, lags, out);
 }
-// FP64 field (plain path): interpolation in FP64, the same FP64 accumulation.
+// FP64 field (plain path): interpolation, time weights and currents in FP64 (lags: FP64 table).
 void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                   const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
                   const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
-                  const void* lags, float* out) {
-    eq1_launch_t<double>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out,
-                         dt, v_w, lags, out);
+                  const void* lags, double* out) {
+    eq1_launch_t<double, Eq1Lag64, double>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst,
+                                           n_tracks, n_steps, n_out, dt, v_w, lags, out);
 }
 size_t eq1_lag_size() { return sizeof(Eq1Lag); }
 void eq1_pack_lag(void* dst, int n, float w0, float w1) { *static_cast<Eq1Lag*>(dst) = Eq1Lag{n, w0, w1}; }
+size_t eq1_lag64_size() { return sizeof(Eq1Lag64); }
+void eq1_pack_lag64(void* dst, int n, double w0, double w1) { *static_cast<Eq1Lag64*>(dst) = Eq1Lag64{n, w0, w1}; }
 
 // ------------------------------------------------------------------------
 // Allocation-free variant (wt_eq1_noalloc).  The per-call lag table lives in

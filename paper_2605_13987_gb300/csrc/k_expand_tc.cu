@@ -14,9 +14,17 @@
 // give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
 // grid point, column = time sample), double buffered in two 256-column
 // halves; eight epilogue warps (two per TMEM lane quadrant, alternate
-// 32-column slices) drain it with tcgen05.ld and write H with fully
-// coalesced 128-byte warp stores (32 consecutive grid points of one time
-// sample).
+// 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
+// lane quads by shuffles and write H with 16-byte stores: each warp store
+// covers 4 time samples x 32 consecutive grid points (four full 128-byte
+// lines), a quarter of the store instructions of one float per lane.
+//
+// A launch may cover several expansions at once (one per sensor geometry of a
+// batch, each with its own basis fields, coefficients, grid size and time
+// count): the units of all jobs form one sequence that the persistent CTAs
+// share round-robin.  When a CTA moves on to the next job, the producer waits
+// until the MMAs of the previous job have completed and rewrites the
+// coefficient tiles in shared memory.
 //
 // Warp roles: warp 0 producer (TMA issue + hi/lo conversion), warp 1 TMEM
 // owner + MMA issuer, warps 2-9 epilogue.  Every mbarrier wait gives up
@@ -36,9 +44,10 @@ namespace tc {
 constexpr int BM = 128;            // grid points per unit (TMEM lanes)
 constexpr int NEPI = 8;            // epilogue warps
 constexpr int KR = 32;             // basis rank (TF32 elements per 128-byte row)
-constexpr int NCH = 256;           // time samples per accumulator half
+constexpr int NCH = 256;           // time samples per accumulator half (at most; the chunk is a launch argument)
 constexpr int TILE_BYTES = BM * 128;  // one 128 x 32 TF32 tile
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
+constexpr int MAX_JOBS = 64;       // expansion jobs per launch
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -151,28 +160,79 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
 
 constexpr int RAW_BYTES = KR * BM * 4;   // one raw FP32 slice [32 basis][128 points]
 
+// 4 x 4 transposes within lane quads: on entry lane 4g + i holds v[4b + j] =
+// D[point 4g + i][time 4b + j]; on return v[4b + j] = D[point 4g + j][time 4b + i],
+// so that each lane can store 4 consecutive points of one time sample.
+// Two butterfly exchanges per block (lanes i ^ 2, then i ^ 1).
+__device__ __forceinline__ void quad_transpose(float (&v)[32], int lane) {
+    const bool b1 = lane & 2, b0 = lane & 1;
+#pragma unroll
+    for (int bb = 0; bb < 8; ++bb) {
+        float* m = v + 4 * bb;
+        const float s0 = b1 ? m[0] : m[2], s1 = b1 ? m[1] : m[3];
+        const float r0 = __shfl_xor_sync(0xffffffffu, s0, 2), r1 = __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (b1) { m[0] = r0; m[1] = r1; } else { m[2] = r0; m[3] = r1; }
+        const float u0 = b0 ? m[0] : m[1], u1 = b0 ? m[2] : m[3];
+        const float w0 = __shfl_xor_sync(0xffffffffu, u0, 1), w1 = __shfl_xor_sync(0xffffffffu, u1, 1);
+        if (b0) { m[0] = w0; m[2] = w1; } else { m[1] = w0; m[3] = w1; }
+    }
+}
+
 struct Smem {
     // tiles first (1024-byte aligned base):
     // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo], raw[2][32][128] FP32
-    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain;
+    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain, b_free;
     unsigned tmem_base;
     int abort_flag;
 };
 
+// Expansion jobs of one launch (kernel parameter; the tensor maps must live
+// in parameter space).  Job j covers units [unit_end[j-1], unit_end[j]).
+struct Jobs {
+    CUtensorMap emap[MAX_JOBS];
+    const float* W[MAX_JOBS];
+    float* H[MAX_JOBS];
+    unsigned long long npts[MAX_JOBS];
+    int nt[MAX_JOBS];
+    int r[MAX_JOBS];             // basis vectors in use (rows >= r of E are not read)
+    int unit_end[MAX_JOBS];
+    int n_jobs;
+};
+
+__device__ __forceinline__ int job_of(const Jobs& J, int u, int from) {
+    int j = from;
+    while (j + 1 < J.n_jobs && u >= J.unit_end[j]) ++j;
+    return j;
+}
+__device__ __forceinline__ int unit0_of(const Jobs& J, int j) { return j ? J.unit_end[j - 1] : 0; }
+__device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
+
+// time coefficients of one job, split hi/lo, into the swizzled B tiles
+// (rows = time samples); threads [t0, t0 + nthr) of the CTA take part
+__device__ __forceinline__ void load_coeffs(const float* __restrict__ W, int nt, int nt_pad, unsigned char* b_hi,
+                                            unsigned char* b_lo, int tid, int nthr) {
+    for (int e = tid; e < nt_pad * KR; e += nthr) {
+        const int t = e / KR, k = e % KR;
+        const float v = t < nt ? W[(size_t)t * KR + k] : 0.f;
+        const unsigned hi = to_tf32(v);
+        const unsigned lo = to_tf32(v - __uint_as_float(hi));
+        *reinterpret_cast<unsigned*>(b_hi + sw128(t, k)) = hi;
+        *reinterpret_cast<unsigned*>(b_lo + sw128(t, k)) = lo;
+    }
+}
+
 __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
-    expand_tc_kernel(const __grid_constant__ CUtensorMap emap, const float* __restrict__ W, int nt, int nt_pad,
-                     size_t npts, int n_tiles, float* __restrict__ H, int* __restrict__ d_err) {
+    expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // align the tile region to 1024 bytes
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char* b_hi = base;
-    unsigned char* b_lo = b_hi + (size_t)nt_pad * 128;
-    unsigned char* a_tiles = b_lo + (size_t)nt_pad * 128;          // [stage][hi|lo] x TILE_BYTES
+    unsigned char* b_lo = b_hi + (size_t)nt_pad_max * 128;
+    unsigned char* a_tiles = b_lo + (size_t)nt_pad_max * 128;      // [stage][hi|lo] x TILE_BYTES
     float* raw = reinterpret_cast<float*>(a_tiles + 4 * TILE_BYTES);  // [2][KR][BM]
     Smem* S = reinterpret_cast<Smem*>(reinterpret_cast<unsigned char*>(raw) + 2 * RAW_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_units = n_tiles * 3;
-    const int n_chunks = (nt_pad + NCH - 1) / NCH;
+    const int job0 = job_of(J, blockIdx.x, 0);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -183,18 +243,11 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             mbar_init(&S->raw_full[i], 1);
         }
         mbar_init(&S->drain, 1);
+        mbar_init(&S->b_free, 1);
         S->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // time coefficients, split hi/lo, into the swizzled B tiles (rows = time samples)
-    for (int e = threadIdx.x; e < nt_pad * KR; e += blockDim.x) {
-        const int t = e / KR, k = e % KR;
-        const float v = t < nt ? W[(size_t)t * KR + k] : 0.f;
-        const unsigned hi = to_tf32(v);
-        const unsigned lo = to_tf32(v - __uint_as_float(hi));
-        *reinterpret_cast<unsigned*>(b_hi + sw128(t, k)) = hi;
-        *reinterpret_cast<unsigned*>(b_lo + sw128(t, k)) = lo;
-    }
+    load_coeffs(J.W[job0], J.nt[job0], pad32(J.nt[job0]), b_hi, b_lo, threadIdx.x, blockDim.x);
     fence_proxy_async();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&S->tmem_base)));
@@ -210,21 +263,32 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         // ---------------- producer: TMA loads of raw E slices, hi/lo conversion into swizzled A tiles
         int issued = 0;          // raw loads issued (unit k of this CTA goes to buffer k & 1)
         if (lane == 0)
-            for (; issued < 2; ++issued) {
+            for (int jl = job0; issued < 2; ++issued) {
                 const int u = blockIdx.x + issued * gridDim.x;
                 if (u >= n_units) break;
+                jl = job_of(J, u, jl);
+                const int v = u - unit0_of(J, jl);
                 mbar_expect_tx(&S->raw_full[issued], RAW_BYTES);
-                tma_load_2d(raw + issued * KR * BM, &emap, (u / 3) * BM, (u % 3) * KR, &S->raw_full[issued]);
+                tma_load_2d(raw + issued * KR * BM, &J.emap[jl], (v / 3) * BM, (v % 3) * KR, &S->raw_full[issued]);
             }
         issued = __shfl_sync(0xffffffffu, issued, 0);
-        int i = 0;
+        int i = 0, cur = job0, jnext = job0, n_changes = 0;
         for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++i) {
             const int st = i & 1;
+            const int j = job_of(J, u, cur);
+            if (j != cur) {
+                // new job: wait until the MMAs of the previous one are done, then its coefficients
+                if (!mbar_wait(&S->b_free, n_changes & 1, abort_flag, d_err)) break;
+                ++n_changes;
+                load_coeffs(J.W[j], J.nt[j], pad32(J.nt[j]), b_hi, b_lo, lane, 32);
+                cur = j;
+            }
             if (!mbar_wait(&S->a_empty[st], ((i >> 1) & 1) ^ 1, abort_flag, d_err)) break;
             if (!mbar_wait(&S->raw_full[st], (i >> 1) & 1, abort_flag, d_err)) break;
             unsigned char* ah = a_tiles + (size_t)(2 * st) * TILE_BYTES;
             unsigned char* al = ah + TILE_BYTES;
             const float* rb = raw + st * KR * BM;
+            const int rk = J.r[cur];
 #pragma unroll
             for (int rr = 0; rr < BM / 32; ++rr) {
                 const int row = lane + 32 * rr;                   // lane = grid point
@@ -233,7 +297,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                     unsigned hi[4], lo[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float x = rb[(4 * c + j) * BM + row];
+                        const float x = (4 * c + j) < rk ? rb[(4 * c + j) * BM + row] : 0.f;
                         hi[j] = to_tf32(x);
                         lo[j] = to_tf32(x - __uint_as_float(hi[j]));
                     }
@@ -248,12 +312,12 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             }
             fence_proxy_async();     // A tiles for the tensor core; raw buffer reads before the TMA refill
             __syncwarp();
-            if (lane == 0) {
-                const int u2 = u + 2 * gridDim.x;
-                if (u2 < n_units) {
-                    mbar_expect_tx(&S->raw_full[st], RAW_BYTES);
-                    tma_load_2d(raw + st * KR * BM, &emap, (u2 / 3) * BM, (u2 % 3) * KR, &S->raw_full[st]);
-                }
+            const int u2 = u + 2 * gridDim.x;
+            if (u2 < n_units) jnext = job_of(J, u2, max(jnext, cur));
+            if (lane == 0 && u2 < n_units) {
+                const int v2 = u2 - unit0_of(J, jnext);
+                mbar_expect_tx(&S->raw_full[st], RAW_BYTES);
+                tma_load_2d(raw + st * KR * BM, &J.emap[jnext], (v2 / 3) * BM, (v2 % 3) * KR, &S->raw_full[st]);
             }
             if (u + 2 * gridDim.x < n_units) ++issued;
             mbar_arrive(&S->a_full[st]);
@@ -262,10 +326,13 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         for (int k = i; k < issued; ++k) mbar_wait_drain(&S->raw_full[k & 1], (k >> 1) & 1, d_err);
     } else if (warp == 1) {
         // ---------------- MMA issuer (lane 0)
-        int i = 0, g = 0;
+        int i = 0, g = 0, cur = job0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++i) {
             const int st = i & 1;
+            cur = job_of(J, u, cur);
+            const int nt_pad = pad32(J.nt[cur]);
+            const int n_chunks = (nt_pad + nch - 1) / nch;
             if (!mbar_wait(&S->a_full[st], (i >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
             tc_fence_after();
             const unsigned a_hi = smem_u32(a_tiles + (size_t)(2 * st) * TILE_BYTES);
@@ -274,12 +341,12 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 const int b = g & 1;
                 if (!mbar_wait(&S->acc_empty[b], ((g >> 1) & 1) ^ 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
-                const int n = min(NCH, nt_pad - ch * NCH);
+                const int n = min(nch, nt_pad - ch * nch);
                 const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) |
                                        ((unsigned)(BM >> 4) << 24);
                 if (lane == 0) {
-                    const unsigned bh = smem_u32(b_hi + (size_t)ch * NCH * 128);
-                    const unsigned bl = smem_u32(b_lo + (size_t)ch * NCH * 128);
+                    const unsigned bh = smem_u32(b_hi + (size_t)ch * nch * 128);
+                    const unsigned bl = smem_u32(b_lo + (size_t)ch * nch * 128);
                     const unsigned d = tmem + (unsigned)(b * NCH);
 #pragma unroll
                     for (int ks = 0; ks < KR / 8; ++ks) {
@@ -293,7 +360,12 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 __syncwarp();
             }
             if (!ok) break;
-            if (lane == 0) mma_commit(&S->a_empty[st]);
+            if (lane == 0) {
+                mma_commit(&S->a_empty[st]);
+                // last unit of this job for this CTA: its coefficient tiles may be replaced once these MMAs finish
+                const int un = u + gridDim.x;
+                if (un < n_units && job_of(J, un, cur) != cur) mma_commit(&S->b_free);
+            }
             __syncwarp();
         }
         // drain: every MMA this thread issued has completed before TMEM is freed
@@ -307,26 +379,35 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         const int q = warp & 3;
         const int slice = (warp - 2) >> 2;
         constexpr int NSL = NEPI / 4;
-        int g = 0;
+        int g = 0, cur = job0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const int tile = u / 3, c = u % 3;
-            const size_t p = (size_t)tile * BM + q * 32 + lane;
-            const bool in = p < npts;
-            float* hp = H + (size_t)c * npts + p;
+            cur = job_of(J, u, cur);
+            const int v = u - unit0_of(J, cur);
+            const int tile = v / 3, c = v % 3;
+            const size_t npts = J.npts[cur];
+            const int nt = J.nt[cur], nt_pad = pad32(nt);
+            const int n_chunks = (nt_pad + nch - 1) / nch;
+            // after the quad transpose lane 4g + i stores points 4g..4g+3 (16 bytes) of time 4b + i
+            const size_t p4 = (size_t)tile * BM + q * 32 + 4 * (lane >> 2);
+            const bool in = p4 < npts;                 // npts is a multiple of 4
+            float* hp = J.H[cur] + (size_t)c * npts + p4;
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
                 const int b = g & 1;
                 if (!mbar_wait(&S->acc_full[b], (g >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
-                const int n = min(NCH, nt_pad - ch * NCH);
+                const int n = min(nch, nt_pad - ch * nch);
                 for (int j = slice * 32; j < n; j += 32 * NSL) {
                     float v[32];
                     tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), v);
-                    const int t0 = ch * NCH + j;
+                    quad_transpose(v, lane);
+                    const int t0 = ch * nch + j + (lane & 3);
                     if (in) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            if (t0 + e < nt) hp[(size_t)(t0 + e) * 3 * npts] = v[e];
+                        for (int bb = 0; bb < 8; ++bb)
+                            if (t0 + 4 * bb < nt)
+                                *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
+                                    make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
                     }
                 }
                 tc_fence_before();
@@ -362,34 +443,68 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// E: [3][32][npts] FP32, W: [nt][32] FP32, H: [nt][3][npts] FP32.
-void expand_tc(cudaStream_t s, const float* E, int r_pad, const float* W, int nt, size_t npts, float* H, int* d_err) {
-    if (r_pad != tc::KR) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion needs rank padded to 32");
-    const int nt_pad = ((nt + 31) / 32) * 32;
-    if (nt_pad > 512) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion handles at most 512 time samples");
-    if (npts % 4) fail(WT_ERR_UNSUPPORTED, "grid size must be a multiple of 4");
-    if (reinterpret_cast<uintptr_t>(E) % 16) fail(WT_ERR_ARG, "basis fields must be 16-byte aligned");
+static void encode_basis_map(CUtensorMap* m, const float* E, size_t npts) {
     // E viewed as 96 rows (component x basis index) of npts points; one box = 32 rows x 128 points
-    CUtensorMap emap;
     cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)3 * tc::KR};
     cuuint64_t strides[1] = {(cuuint64_t)npts * sizeof(float)};
     cuuint32_t box[2] = {tc::BM, tc::KR};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = tensor_map_encoder()(&emap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(E), dims, strides,
-                                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(E), dims, strides, box,
+                                      es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) fail(WT_ERR_CUDA, "tensor map for the basis fields: error " + std::to_string((int)r));
-    const size_t sh = expand_tc_smem(nt_pad);
+}
+
+int expand_tc_max_jobs() { return tc::MAX_JOBS; }
+
+// jobs[j]: E [3][32][npts] FP32, W [nt][32] FP32, H [nt][3][npts] FP32; all
+// expansions in one persistent launch of at most `max_ctas` CTAs (0: one per SM).
+void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err) {
+    if (n_jobs < 1) return;
+    if (nch != 64 && nch != 128 && nch != 256) fail(WT_ERR_ARG, "expansion time chunk must be 64, 128 or 256");
+    if (n_jobs > tc::MAX_JOBS) fail(WT_ERR_UNSUPPORTED, "too many expansion jobs for one launch");
+    tc::Jobs J;             // kernel parameter block (about 10 KB)
+    int nt_pad_max = 32, units = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ExpandJob& jb = jobs[j];
+        if (jb.r_pad != tc::KR) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion needs rank padded to 32");
+        if (jb.r < 0 || jb.r > tc::KR) fail(WT_ERR_ARG, "basis rank out of range");
+        const int nt_pad = ((jb.nt + 31) / 32) * 32;
+        if (jb.nt < 1 || nt_pad > 512) fail(WT_ERR_UNSUPPORTED, "tensor-core expansion handles 1 to 512 time samples");
+        if (jb.npts % 4) fail(WT_ERR_UNSUPPORTED, "grid size must be a multiple of 4");
+        if (reinterpret_cast<uintptr_t>(jb.E) % 16) fail(WT_ERR_ARG, "basis fields must be 16-byte aligned");
+        if (reinterpret_cast<uintptr_t>(jb.H) % 16) fail(WT_ERR_ARG, "H must be 16-byte aligned");
+        const size_t n_tiles = (jb.npts + tc::BM - 1) / tc::BM;
+        if ((size_t)units + 3 * n_tiles > (size_t)INT32_MAX) fail(WT_ERR_UNSUPPORTED, "expansion batch too large");
+        encode_basis_map(&J.emap[j], jb.E, jb.npts);
+        J.W[j] = jb.W;
+        J.H[j] = jb.H;
+        J.npts[j] = jb.npts;
+        J.nt[j] = jb.nt;
+        J.r[j] = jb.r;
+        units += (int)(3 * n_tiles);
+        J.unit_end[j] = units;
+        nt_pad_max = std::max(nt_pad_max, nt_pad);
+    }
+    J.n_jobs = n_jobs;
+    const size_t sh = expand_tc_smem(nt_pad_max);
     int dev = 0, n_sm = 0, max_sh = 0;
     WT_CUDA(cudaGetDevice(&dev));
     WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
     WT_CUDA(cudaFuncSetAttribute(tc::expand_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    const int n_tiles = (int)((npts + tc::BM - 1) / tc::BM);
-    const int grid = std::min(n_sm, n_tiles * 3);
-    tc::expand_tc_kernel<<<grid, 64 + 32 * tc::NEPI, sh, s>>>(emap, W, nt, nt_pad, npts, n_tiles, H, d_err);
+    int grid = std::min(n_sm, units);
+    if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    tc::expand_tc_kernel<<<grid, 64 + 32 * tc::NEPI, sh, s>>>(J, nt_pad_max, units, nch, d_err);
     WT_LAUNCH("expand_tc");
+}
+
+// E: [3][32][npts] FP32 (rows >= r unused), W: [nt][32] FP32, H: [nt][3][npts] FP32.
+void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W, int nt, size_t npts, float* H,
+               int* d_err) {
+    ExpandJob jb{E, r_pad, r, W, nt, npts, H};
+    expand_tc_jobs(s, &jb, 1, 0, tc::NCH, d_err);
 }
 
 }  // namespace wt

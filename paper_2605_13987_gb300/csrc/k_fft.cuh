@@ -58,8 +58,9 @@ struct Fast32 {
     // rho scratch: nb * Nz * (Nx/2+1) * Ny complex; R scratch: nb * 3 * Nz * Nx * Ny real.
     size_t rho_elems(int nb) const { return (size_t)nb * g.Nz * (g.Nx / 2 + 1) * g.Ny * 2; }
     size_t r_elems(int nb) const { return (size_t)nb * 3 * g.Nz * g.Nx * g.Ny; }
+    // mode 0: the field, 1: its lateral-scale derivative; lb: (x, y) lines per z-pass block (16, 32, 64)
     void fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
-                cudaStream_t s, int mode = 0) const;
+                cudaStream_t s, int mode = 0, int lb = 32) const;
 };
 
 }  // namespace wt

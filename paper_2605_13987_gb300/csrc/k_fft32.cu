@@ -165,17 +165,15 @@ __global__ void __launch_bounds__(256, 2) f32_plane_kernel(GridDev g, const C2<f
     }
 }
 
-constexpr int F32_LB = 32;   // (x, y) lines per z-pass block
-
-// Cosine (W_x, W_y) or sine (W_z) series along z for F32_LB lines; two real
+// Cosine (W_x, W_y) or sine (W_z) series along z for LB (x, y) lines per block; two real
 // lines share one length-2Nz complex warp FFT.  Lines L = y Nx + x of the
 // plane kernel's layout; output in H's point order (x Ny + y) Nz + z.
-// grid (ceil(Nx Ny / F32_LB), 3, nb).
+// grid (ceil(Nx Ny / LB), 3, nb).
 // Skewed index of coefficient m in a staged line pair: a gap every R entries
 // makes the per-lane chunk stride R + 1, so the reads are free of bank conflicts.
 __device__ __forceinline__ int zskew(int m, int R) { return m + m / R; }
 
-template <int RZ>
+template <int RZ, int LB>
 __global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
                                                         const C2<float>* __restrict__ twz,
                                                         const C2<float>* __restrict__ zsh, float* __restrict__ out,
@@ -184,17 +182,17 @@ __global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const floa
     const int nx = g.Nx, ny = g.Ny, nz = g.Nz, n2 = 2 * nz;
     const size_t nxy = (size_t)nx * ny;
     const int comp = blockIdx.y, b = blockIdx.z;
-    const size_t L0 = (size_t)blockIdx.x * F32_LB;
+    const size_t L0 = (size_t)blockIdx.x * LB;
     const int S = (zskew(nz - 1, RZ) + 1) | 1;                              // odd pair pitch
-    C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [F32_LB/2][S]
-    C2<float>* tw = cs + (size_t)(F32_LB / 2) * S;                          // [n2]
+    C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [LB/2][S]
+    C2<float>* tw = cs + (size_t)(LB / 2) * S;                              // [n2]
     C2<float>* zs = tw + n2;                                                // [nz]
     for (int e = threadIdx.x; e < n2; e += blockDim.x) tw[e] = twz[e];
     for (int e = threadIdx.x; e < nz; e += blockDim.x) zs[e] = zsh[e];
     const float* src = R + ((size_t)b * 3 + comp) * nz * nxy + L0;
     float* csf = reinterpret_cast<float*>(cs);
-    for (int e = threadIdx.x; e < nz * F32_LB; e += blockDim.x) {
-        const int m = e / F32_LB, l = e % F32_LB;
+    for (int e = threadIdx.x; e < nz * LB; e += blockDim.x) {
+        const int m = e / LB, l = e % LB;
         csf[2 * ((l >> 1) * S + zskew(m, RZ)) + (l & 1)] = (L0 + l < nxy) ? src[(size_t)m * nxy + l] : 0.f;
     }
     __syncthreads();
@@ -202,7 +200,7 @@ __global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const floa
     const int W = n2 / RZ, G = 32 / W, grp = lane / W, gl = lane % W;
     const int k2 = warp_fft_k2(gl, W);
     float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
-    for (int base = warp * G; base < F32_LB / 2; base += 8 * G) {
+    for (int base = warp * G; base < LB / 2; base += 8 * G) {
         const int f = base + grp;                 // lines 2f, 2f+1 of this block
         const C2<float>* cf = cs + (size_t)f * S;
         C2<float> v[RZ];
@@ -255,11 +253,11 @@ static size_t plane_smem(const GridDev& g) {
     warp_fft_shape(g.Nx, &W, &R);
     return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>) + (size_t)8 * (32 / W) * g.Nx * sizeof(float);
 }
-static size_t zpass_smem(const GridDev& g) {
+static size_t zpass_smem(const GridDev& g, int lb) {
     int W, R;
     warp_fft_shape(2 * g.Nz, &W, &R);
     const size_t S = (size_t)(((g.Nz - 1) + (g.Nz - 1) / R + 1) | 1);
-    return ((size_t)(F32_LB / 2) * S + 3 * (size_t)g.Nz) * sizeof(C2<float>);
+    return ((size_t)(lb / 2) * S + 3 * (size_t)g.Nz) * sizeof(C2<float>);
 }
 static size_t deposit_smem(const GridDev& g, int n_cols) {
     return (size_t)n_cols * (g.Nx / 2 + 1 + g.Ny) * sizeof(C2<float>);
@@ -303,7 +301,7 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
     f32_twiddle_kernel<<<(g.Nx + 127) / 128, 128, 0, s>>>(tw_x.p, g.Nx);
     f32_twiddle_kernel<<<(2 * g.Nz + 127) / 128, 128, 0, s>>>(tw_z.p, 2 * g.Nz);
     WT_LAUNCH("fast32 tables");
-    const size_t sp = plane_smem(g), sz = zpass_smem(g), sd = deposit_smem(g, n_cols);
+    const size_t sp = plane_smem(g), sz = zpass_smem(g, 64), sd = deposit_smem(g, n_cols);
     if (sp > 227 * 1024 || sz > 227 * 1024 || sd > 227 * 1024)
         fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
     switch (rxy) {
@@ -312,7 +310,10 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
 #undef WT_CASE
     }
     switch (rz) {
-#define WT_CASE(R) case R: { WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); break; }
+#define WT_CASE(R) case R: { \
+        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); break; }
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }
@@ -321,7 +322,8 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
 }
 
 void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
-                    cudaStream_t s, int mode) const {
+                    cudaStream_t s, int mode, int lb) const {
+    if (lb != 16 && lb != 32 && lb != 64) fail(WT_ERR_ARG, "z-pass lines per block must be 16, 32 or 64");
     C2<float>* rc = reinterpret_cast<C2<float>*>(rho);
     dim3 gd(g.Nz, nb);
     f32_deposit_kernel<<<gd, 256, deposit_smem(g, n_cols), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
@@ -337,11 +339,15 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     }
     WT_LAUNCH("f32_plane");
     const size_t nxy = (size_t)g.Nx * g.Ny;
-    dim3 gz((unsigned)((nxy + F32_LB - 1) / F32_LB), 3, nb);
+    dim3 gz((unsigned)((nxy + lb - 1) / lb), 3, nb);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(tw_z.p);
     const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
     switch (rz) {
-#define WT_CASE(RR) case RR: f32_zpass_kernel<RR><<<gz, 256, zpass_smem(g), s>>>(g, R, tz, zz, out, out_sb, out_sc); break;
+#define WT_CASE(RR) case RR: \
+        if (lb == 16) f32_zpass_kernel<RR, 16><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else if (lb == 32) f32_zpass_kernel<RR, 32><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else f32_zpass_kernel<RR, 64><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        break;
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }

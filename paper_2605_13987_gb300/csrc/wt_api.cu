@@ -5,7 +5,12 @@
 #include "k_fft.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -40,7 +45,7 @@ void eq1_launch(cudaStream_t, const float*, int, int, int, int, double, double, 
 size_t eq1_lag_size();
 void eq1_launch64(cudaStream_t, const double*, int, int, int, int, double, double, double, const float*, const float*,
                   const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
-                  double, const void*, float*);
+                  double, const void*, double*);
 void green_lateral_deriv(cudaStream_t, const double*, const double*, int, int, int, int, double, double, double, double,
                          int, double*);
 void modal_inv_gap(cudaStream_t, const double*, int, double*);
@@ -53,8 +58,9 @@ void eq1_noalloc_launch(cudaStream_t, int, const float*, int, int, int, const do
                         const float*, const float*, const float*, const float*, const float*, const float*,
                         const float*, float, int, int, int, double, double, float*);
 void eq1_pack_lag(void*, int, float, float);
-bool expand_tc_available();
-void expand_tc(cudaStream_t, const float*, int, const float*, int, size_t, float*, int*);
+size_t eq1_lag64_size();
+void eq1_pack_lag64(void*, int, double, double);
+double dot_f64(cudaStream_t, const double*, const double*, size_t, double*);
 
 void fail(wt_status code, const std::string& msg) { throw Error{code, msg}; }
 
@@ -128,6 +134,13 @@ struct wt_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     int last_launches = 0;
+    // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
+    // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
+    int tune_nb = 1, tune_lb = 32, tune_nch = 256;
+    // identity and state counter, for the captured graphs of wt_batch_run
+    unsigned long long uid = 0, version = 0;
+    std::vector<std::unique_ptr<struct BatchPlan>> plans;
+    ~wt_ctx();
 };
 
 namespace {
@@ -497,8 +510,17 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
     dgemm(s, true, false, nt, nt, ns, 1.0, Q, nt, Q, nt, 0.0, Gt.p, nt);
     Wg.alloc((size_t)nt * nt);
     lam.alloc(nt);
+    // couplings below the rounding level of the Gram matrix (1e-15 of its trace) are left alone
+    DBuf<double> dg;
+    dg.alloc(nt);
+    get_diag(s, Gt.p, nt, nt, dg.p);
+    std::vector<double> hd(nt);
+    dg.download(hd.data(), nt, s);
+    WT_CUDA(cudaStreamSynchronize(s));
+    double trace = 0;
+    for (double x : hd) trace += x;
     clear_err(c);
-    jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p);
+    jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p, 40, 1e-15 * trace);
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver (time basis) did not converge");
     std::vector<double> hl(nt), hw((size_t)nt * nt);
     lam.download(hl.data(), nt, s);
@@ -538,6 +560,7 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
 
 void do_relax(wt_ctx* c, const double* t, int nt) {
     auto t0 = clk::now();
+    ++c->version;
     cudaStream_t s = c->s;
     const int ns = c->ns, n1 = ns - 1;
     if (n1 < 1) fail(WT_ERR_GEOMETRY, "need at least two sources");
@@ -681,24 +704,30 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size();
     const int rp = 32;
-    const int nb = 1;     // one charge vector per batch keeps the intermediates in L2
+    const int nb = c->tune_nb;      // charge vectors per spectral launch (1 keeps the intermediates in L2)
+    const bool tc = c->use_tc && expand_tc_available();
     c->Zc32.alloc((size_t)rp * ncol * g.Nz);
     c->rho32.alloc(c->sp32.rho_elems(nb));
     c->R32.alloc(c->sp32.r_elems(nb));
     c->E32.alloc((size_t)3 * rp * npts);
-    if (r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
+    // the tensor-core expansion reads only the r rows in use; the FMA one reads all 32
+    if (!tc && r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
     column_ztransform<float>(s, Ub, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
     *launches += 1;
     if (timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
     for (int m0 = 0; m0 < r; m0 += nb) {
         const int b = std::min(nb, r - m0);
         c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p, c->E32.p + (size_t)m0 * npts,
-                       npts, (size_t)rp * npts, s, mode);
+                       npts, (size_t)rp * npts, s, mode, c->tune_lb);
         *launches += 3;
     }
     if (timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
-    if (c->use_tc && expand_tc_available()) expand_tc(s, c->E32.p, rp, W32, nt, npts, out, c->d_err.p);
-    else expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
+    if (tc) {
+        ExpandJob jb{c->E32.p, rp, r, W32, nt, npts, out};
+        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p);
+    } else {
+        expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
+    }
     *launches += 1;
     if (timing) WT_CUDA(cudaEventRecord(c->ev[3], s));
 }
@@ -803,9 +832,10 @@ void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, dou
 
 // Lag table of Eq. 1: (k + 1/2) dt -> bracketing samples and weights (linear
 // in t; 0 at t = 0; held after the last sample).
-void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cudaStream_t s) {
+void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cudaStream_t s, bool f64 = false) {
     const int nt = (int)c->times.size();
-    std::vector<unsigned char> lag(eq1_lag_size() * (size_t)n_out);
+    const size_t esz = f64 ? eq1_lag64_size() : eq1_lag_size();
+    std::vector<unsigned char> lag(esz * (size_t)n_out);
     const std::vector<double>& ts = c->times;
     for (int k = 0; k < n_out; ++k) {
         const double L = (k + 0.5) * dt;
@@ -819,7 +849,8 @@ void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cuda
             w0 = 1.0 - f;
             w1 = f;
         }
-        eq1_pack_lag(lag.data() + eq1_lag_size() * k, n0, (float)w0, (float)w1);
+        if (f64) eq1_pack_lag64(lag.data() + esz * k, n0, w0, w1);
+        else eq1_pack_lag(lag.data() + esz * k, n0, (float)w0, (float)w1);
     }
     dlag.upload(lag.data(), lag.size(), s);
 }
@@ -850,19 +881,22 @@ TrackDev stage_tracks(wt_ctx* c, const wt_tracks* tr, DBuf<float> (&keep)[7], cu
                     tr->n_tracks, tr->n_steps, tr->n_out, tr->dt};
 }
 
-void eq1_run(wt_ctx* c, const void* H, bool h64, const TrackDev& t, float* out, cudaStream_t s,
+// h64: FP64 field, FP64 lag weights and FP64 currents (out is double*); else all FP32 (float*).
+void eq1_run(wt_ctx* c, const void* H, bool h64, const TrackDev& t, void* out, cudaStream_t s,
              const float* vz_override = nullptr) {
     const wt_grid& g = c->grid;
     const int nt = (int)c->times.size();
     DBuf<unsigned char> dlag;
-    build_lags(c, t.dt, t.n_out, dlag, s);
+    build_lags(c, t.dt, t.n_out, dlag, s, h64);
     const float* vz = vz_override ? vz_override : t.vz;
     if (h64)
         eq1_launch64(s, static_cast<const double*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx,
-                     t.vy, vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, out);
+                     t.vy, vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p,
+                     static_cast<double*>(out));
     else
         eq1_launch(s, static_cast<const float*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
-                   vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, out);
+                   vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p,
+                   static_cast<float*>(out));
     WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
 }
 
@@ -923,11 +957,20 @@ double do_loss(wt_ctx* c, wt_precision prec, const wt_tracks* tr) {
         H = c->stage32.p;
     }
     const size_t nI = (size_t)tr->n_tracks * tr->n_out;
-    DBuf<float> I;
-    I.alloc(nI);
-    eq1_run(c, H, prec == WT_FP64, td, I.p, s);
+    double sum;
+    if (prec == WT_FP64) {
+        DBuf<double> I;
+        I.alloc(nI);
+        eq1_run(c, H, true, td, I.p, s);
+        sum = dot_f64(s, I.p, I.p, nI, c->d_scr.p);
+    } else {
+        DBuf<float> I;
+        I.alloc(nI);
+        eq1_run(c, H, false, td, I.p, s);
+        sum = dot_f32(s, I.p, I.p, nI, c->d_scr.p);
+    }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out");
-    return dot_f32(s, I.p, I.p, nI, c->d_scr.p) / (double)nI;
+    return sum / (double)nI;
 }
 
 // Derivative of L = mean i^2 with respect to [readout resistivity scale, bias
@@ -950,6 +993,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
     const size_t nI = (size_t)tr->n_tracks * tr->n_out;
     int launches = 0;
     clear_err(c);
+    c->info.grad_trunc_rel = 0.0;
     // base field and currents
     c->stage32.alloc((size_t)nt * 3 * npts);
     extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, c->stage32.p, s, 0, &launches, false);
@@ -1111,6 +1155,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
         int dr = 0;
         double dtr = 0.0;
         compress_history(c, dQq.p, nt, dUb, dW, dr, dtr);
+        c->info.grad_trunc_rel = std::max(c->info.grad_trunc_rel, dtr);
         extend32_basis(c, dUb.p, dr, dW.p, nt, dH.p, s, 0, &launches, false);
         eq1_run(c, dH.p, false, td, dI.p, s);
         double acc = dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
@@ -1125,6 +1170,248 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
         grad[p] = gscale * acc;
         if (read_err(c)) fail(WT_ERR_NAN, "non-finite or timed-out tangent");
     }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- batched FP32 path
+// One entry per context of a captured batch: what the graph's nodes point at.
+struct BatchEntry {
+    wt_ctx* c;
+    unsigned long long uid, version;
+    const void* H;
+    const void *E, *Zc, *rho, *R, *Ub, *W;
+    int nb, lb;
+    bool operator==(const BatchEntry& o) const {
+        return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
+               rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb;
+    }
+};
+
+struct BatchPlan {
+    std::vector<BatchEntry> ents;
+    int nch = 256;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long last_use = 0;
+    ~BatchPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+wt_ctx::~wt_ctx() = default;
+
+namespace {
+
+struct TuneResult {
+    int nb, lb, nch;
+    double spectral_ms, expand_ms;
+};
+using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune;
+std::atomic<unsigned long long> g_plan_clock{0};
+
+TuneKey tune_key(const wt_ctx* c) {
+    return TuneKey{c->dev, c->grid.Nx, c->grid.Ny, c->grid.Nz, (int)c->times.size()};
+}
+
+// Buffers of the FP32 path at the context's launch shapes.
+void alloc_fast32(wt_ctx* c) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    c->Zc32.alloc((size_t)32 * c->cols.size() * g.Nz);
+    c->rho32.alloc(c->sp32.rho_elems(c->tune_nb));
+    c->R32.alloc(c->sp32.r_elems(c->tune_nb));
+    c->E32.alloc((size_t)3 * 32 * npts);
+}
+
+// Spectral passes (deposit, plane, z) of all basis vectors of one context.
+void spectral_all(wt_ctx* c, cudaStream_t s) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int ncol = (int)c->cols.size();
+    for (int m0 = 0; m0 < c->rank; m0 += c->tune_nb) {
+        const int b = std::min(c->tune_nb, c->rank - m0);
+        c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p, c->E32.p + (size_t)m0 * npts,
+                       npts, (size_t)32 * npts, s, 0, c->tune_lb);
+    }
+}
+
+template <class F>
+float time_min(cudaStream_t s, int reps, F&& f) {
+    cudaEvent_t a, b;
+    WT_CUDA(cudaEventCreate(&a));
+    WT_CUDA(cudaEventCreate(&b));
+    f();                                    // warm-up
+    float best = 1e30f;
+    for (int i = 0; i < reps; ++i) {
+        WT_CUDA(cudaEventRecord(a, s));
+        f();
+        WT_CUDA(cudaEventRecord(b, s));
+        WT_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        WT_CUDA(cudaEventElapsedTime(&ms, a, b));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// Autotuner: times every candidate launch shape of the FP32 path on this
+// context (its own basis vectors, writing into H) and keeps the fastest:
+// spectral batch nb in {1, 2, 4} x z-pass lines per block in {16, 32, 64},
+// then the expansion's time chunk in {64, 128, 256}.  Results are cached per
+// (device, grid, n_t) for the process.
+TuneResult autotune(wt_ctx* c, float* H) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(tune_key(c));
+        if (it != g_tune.end()) return it->second;
+    }
+    cudaStream_t s = c->s;
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
+    TuneResult best{1, 32, 256, 1e30, 1e30};
+    c->tune_nb = 1;
+    alloc_fast32(c);
+    column_ztransform<float>(s, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
+    for (int nb : {1, 2, 4}) {
+        if (nb > 1 && nb > c->rank) break;
+        c->tune_nb = nb;
+        alloc_fast32(c);
+        for (int lb : {16, 32, 64}) {
+            c->tune_lb = lb;
+            const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
+            if (ms < best.spectral_ms) { best.spectral_ms = ms; best.nb = nb; best.lb = lb; }
+        }
+    }
+    c->tune_nb = best.nb;
+    c->tune_lb = best.lb;
+    alloc_fast32(c);
+    spectral_all(c, s);
+    for (int nch : {64, 128, 256}) {
+        ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
+        const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p); });
+        if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; }
+    }
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out while tuning");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[tune_key(c)] = best;
+    return best;
+}
+
+BatchEntry entry_of(wt_ctx* c, const void* H) {
+    return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
+                      c->tune_nb, c->tune_lb};
+}
+
+// Records the whole batch (column transforms, spectral passes of every
+// context, one persistent expansion launch per 64 contexts) as a CUDA graph.
+void capture_batch(BatchPlan& P, wt_ctx* const* ctxs, int n, float* const* H) {
+    cudaStream_t cs = ctxs[0]->s;
+    WT_CUDA(cudaStreamSynchronize(cs));
+    WT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        std::vector<ExpandJob> jobs;
+        for (int i = 0; i < n; ++i) {
+            wt_ctx* c = ctxs[i];
+            const wt_grid& g = c->grid;
+            const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+            const int ncol = (int)c->cols.size();
+            column_ztransform<float>(cs, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz,
+                                     c->Zc32.p);
+            spectral_all(c, cs);
+            jobs.push_back(ExpandJob{c->E32.p, 32, c->rank, c->W32.p, (int)c->times.size(), npts, H[i]});
+        }
+        const int mj = expand_tc_max_jobs();
+        for (int j0 = 0; j0 < n; j0 += mj)
+            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p);
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        cudaGetLastError();
+        throw;
+    }
+    WT_CUDA(cudaStreamEndCapture(cs, &P.graph));
+    WT_CUDA(cudaGraphInstantiate(&P.exec, P.graph, 0));
+}
+
+void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cudaStream_t us) {
+    wt_ctx* c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        wt_ctx* c = ctxs[i];
+        if (!c) fail(WT_ERR_ARG, "NULL context in the batch");
+        if (c->stage < 2) fail(WT_ERR_STATE, "every context of a batch must be relaxed");
+        if (c->dev != c0->dev) fail(WT_ERR_ARG, "all contexts of a batch must be on one device");
+        if (!H[i] || !is_device_ptr(H[i])) fail(WT_ERR_ARG, "batch outputs must be device memory");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c) fail(WT_ERR_ARG, "a context appears twice in the batch");
+    }
+    if (prec == WT_FP64) {       // plain path: one extension after the other
+        for (int i = 0; i < n; ++i) {
+            const wt_grid& g = ctxs[i]->grid;
+            const size_t need = ctxs[i]->times.size() * 3 * (size_t)g.Nx * g.Ny * g.Nz * sizeof(double);
+            do_extend(ctxs[i], WT_FP64, H[i], need, us);
+        }
+        return;
+    }
+    if (!expand_tc_available()) fail(WT_ERR_UNSUPPORTED, "the batched path needs the tensor-core expansion");
+    // launch shapes: tuned once per (grid, n_t), then every context at its shape's values
+    std::map<TuneKey, TuneResult> shapes;
+    for (int i = 0; i < n; ++i) {
+        wt_ctx* c = ctxs[i];
+        ensure_spectral(c);
+        const TuneKey k = tune_key(c);
+        if (!shapes.count(k)) shapes[k] = autotune(c, static_cast<float*>(H[i]));
+        const TuneResult& t = shapes[k];
+        c->tune_nb = t.nb;
+        c->tune_lb = t.lb;
+        c->tune_nch = t.nch;
+        alloc_fast32(c);
+    }
+    // one time chunk for the shared expansion launch: the one most of the units asked for
+    std::map<int, double> votes;
+    for (int i = 0; i < n; ++i) {
+        const wt_grid& g = ctxs[i]->grid;
+        votes[ctxs[i]->tune_nch] += (double)g.Nx * g.Ny * g.Nz;
+    }
+    int nch = 256;
+    double top = -1;
+    for (auto& v : votes)
+        if (v.second > top) { top = v.second; nch = v.first; }
+    std::vector<BatchEntry> want;
+    for (int i = 0; i < n; ++i) want.push_back(entry_of(ctxs[i], H[i]));
+    BatchPlan* plan = nullptr;
+    for (auto& p : c0->plans)
+        if (p->nch == nch && p->ents == want) plan = p.get();
+    if (!plan) {
+        auto P = std::make_unique<BatchPlan>();
+        P->ents = want;
+        P->nch = nch;
+        capture_batch(*P, ctxs, n, reinterpret_cast<float* const*>(H));
+        if (c0->plans.size() >= 4) {         // keep the four most recently used graphs
+            auto old = std::min_element(c0->plans.begin(), c0->plans.end(),
+                                        [](const auto& a, const auto& b) { return a->last_use < b->last_use; });
+            c0->plans.erase(old);
+        }
+        c0->plans.push_back(std::move(P));
+        plan = c0->plans.back().get();
+    }
+    plan->last_use = ++g_plan_clock;
+    // the graph runs on the caller's stream after the contexts' own pending work
+    cudaEvent_t ev;
+    WT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    for (int i = 0; i < n; ++i) {
+        WT_CUDA(cudaEventRecord(ev, ctxs[i]->s));
+        WT_CUDA(cudaStreamWaitEvent(us, ev, 0));
+    }
+    cudaEventDestroy(ev);
+    WT_CUDA(cudaGraphLaunch(plan->exec, us));
 }
 
 }  // namespace
@@ -1149,6 +1436,8 @@ wt_status wt_create(wt_ctx** out, const wt_grid* grid, int cuda_device) {
         WT_CUDA(cudaSetDevice(cuda_device));
         wt_ctx* c = new wt_ctx();
         c->dev = cuda_device;
+        static std::atomic<unsigned long long> next_uid{1};
+        c->uid = next_uid++;
         if (const char* e = std::getenv("WT_EXPAND")) c->use_tc = std::strcmp(e, "simt") != 0;
         c->grid = g;
         try {
@@ -1267,6 +1556,24 @@ wt_status wt_eq1_loss_grad(wt_ctx* ctx, const wt_tracks* tracks, double* loss, d
         if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_loss_grad needs wt_relax first");
         if (!loss || !grad) fail(WT_ERR_ARG, "NULL output");
         do_loss_grad(ctx, tracks, loss, grad);
+    });
+}
+
+wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* stream) {
+    if (!ctxs || n < 1 || !H || !ctxs[0]) return WT_ERR_ARG;
+    return run(ctxs[0], "wt_batch_run", [&] {
+        if (prec != WT_FP32 && prec != WT_FP64) fail(WT_ERR_ARG, "bad precision");
+        do_batch(ctxs, n, prec, H, static_cast<cudaStream_t>(stream));
+    });
+}
+
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape3) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_tuning", [&] {
+        if (!shape3) fail(WT_ERR_ARG, "NULL output");
+        shape3[0] = ctx->tune_nb;
+        shape3[1] = ctx->tune_lb;
+        shape3[2] = ctx->tune_nch;
     });
 }
 

@@ -99,8 +99,11 @@ void trsm_lower(cudaStream_t s, const double* L, int n, int ldl, double* B, int 
 void trsm_lower_t(cudaStream_t s, const double* L, int n, int ldl, double* B, int nrhs, int ldb);
 // Symmetric eigendecomposition by parallel two-sided Jacobi: A (n x n,
 // destroyed) -> eigenvalues w[n] (unsorted), eigenvectors V (n x n, columns).
-// Returns the number of sweeps; sets d_err on non-convergence.
-int jacobi_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err, int max_sweeps = 40);
+// Returns the number of sweeps; sets d_err on non-convergence.  Couplings
+// below abs_tol are not rotated (for rank-deficient Gram matrices, whose
+// rounding-level directions would otherwise keep rotating).
+int jacobi_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err, int max_sweeps = 40,
+               double abs_tol = 0.0);
 // y = alpha * A x + beta * y  (A row-major M x N, or its transpose)
 void dgemv(cudaStream_t s, bool ta, int M, int N, double alpha, const double* A, int lda,
            const double* x, double beta, double* y);
@@ -115,5 +118,23 @@ void scale_columns(cudaStream_t s, double* A, int M, int N, int lda, const doubl
 void scale_rows(cudaStream_t s, double* A, int M, int N, int lda, const double* d);
 void column_norms(cudaStream_t s, const double* A, int M, int N, int lda, double* out);
 void get_diag(cudaStream_t s, const double* A, int n, int lda, double* out);
+
+// One tensor-core expansion H[t][c][p] = sum_m W[t][m] E[c][m][p] (FP32).
+struct ExpandJob {
+    const float* E;      // [3][r_pad][npts], 16-byte aligned
+    int r_pad;           // 32
+    int r;               // rows in use (rows >= r of E may hold anything)
+    const float* W;      // [nt][32]
+    int nt;
+    size_t npts;
+    float* H;            // [nt][3][npts]
+};
+bool expand_tc_available();
+int expand_tc_max_jobs();
+void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W, int nt, size_t npts, float* H,
+               int* d_err);
+// Several expansions in one persistent launch (at most max_ctas CTAs, 0 = one
+// per SM; nch = time samples per accumulator chunk: 64, 128 or 256).
+void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err);
 
 }  // namespace wt

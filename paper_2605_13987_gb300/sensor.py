@@ -6,6 +6,18 @@ import numpy as np
 from . import _binding as B
 
 
+def extend_batch(sensors, precision="fp32", outs=None, stream=None):
+    """Bulk extension of several relaxed sensors in one captured launch sequence
+    (wt_batch_run); returns the list of H tensors."""
+    import torch
+    prec = B.WT_FP64 if precision in ("fp64", B.WT_FP64) else B.WT_FP32
+    if outs is None:
+        dt = torch.float64 if prec == B.WT_FP64 else torch.float32
+        outs = [torch.empty(s.h_shape(), dtype=dt, device=f"cuda:{s.device}") for s in sensors]
+    B.wt_batch_run([s.ctx for s in sensors], prec, outs, stream)
+    return outs
+
+
 class Sensor:
     """Sensor(grid, columns, device=0); then fit() -> relax(times) -> extend()."""
 
@@ -48,6 +60,19 @@ class Sensor:
                               device=f"cuda:{self.device}")
         B.wt_eq1(self.ctx, H, tracks, out, stream)
         return out
+
+    def loss(self, tracks, precision="fp32"):
+        """Mean squared Eq. 1 current over tracks and output times."""
+        prec = B.WT_FP64 if precision in ("fp64", B.WT_FP64) else B.WT_FP32
+        return B.wt_eq1_loss(self.ctx, prec, tracks)
+
+    def loss_grad(self, tracks):
+        """(loss, dL/d[s_R, s_B, r, lambda]) by the library's tangent-linear derivative."""
+        return B.wt_eq1_loss_grad(self.ctx, tracks)
+
+    def tuning(self):
+        """Launch shapes of the FP32 path (nb, lb, nch), set by the batch autotuner."""
+        return B.wt_get_tuning(self.ctx)
 
     def charges(self):
         return B.wt_get_charges(self.ctx, len(self.times), self.n_sources)
