@@ -40,6 +40,8 @@ WORKLOADS = {
     "c1": "c1: single cell 55x55x100 um, grid 32x32x64, 2 columns x 64 sources, 64 time samples",
     "small": "small: single cell 55x55x100 um, grid 64x64x64, 2 columns x 64 sources, 512 time samples "
              "(profiling case: H = 1.6 GB > L2)",
+    "prof": "prof: c2's geometry and grid (128x128x256, 18 columns) with 16 time samples "
+            "(profiling case: the spectral kernels at c2 sizes, about 2.5 GB on the device)",
     "c3": "c3: 64 single cells, pitch 40-110 um, thickness 300-500 um, radius 4-10 um, grids 64^2x128 to "
           "128^2x256 (uneven), 256 time samples each; batched in waves through an H arena",
 }
@@ -49,6 +51,10 @@ def make_workload(name):
     import workloads as W
     if name == "small":
         return W.tiny_cell(nx=64, nz=64, n_t=512, radius=6e-6)
+    if name == "prof":
+        from dataclasses import replace
+        w = W.workload("c2")
+        return replace(w, times=W.log_times(16))
     return W.workload(name)
 
 

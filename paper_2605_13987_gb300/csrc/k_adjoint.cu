@@ -110,7 +110,7 @@ void modal_tangent(cudaStream_t s, const double* Om, const double* amp, const do
                    const double* t, const double* c, int n, int nt, double* out) {
     size_t sh = 2 * (size_t)n * sizeof(double);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "modal tangent: too many modes for shared memory");
-    WT_CUDA(cudaFuncSetAttribute(modal_tangent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dyn_smem(modal_tangent_kernel, sh);
     modal_tangent_kernel<<<n, 256, sh, s>>>(Om, amp, inv, E, t, c, n, nt, out);
     WT_LAUNCH("modal_tangent");
 }

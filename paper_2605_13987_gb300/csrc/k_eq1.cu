@@ -102,7 +102,7 @@ static void eq1_launch_t(cudaStream_t s, const T* H, int Nx, int Ny, int Nz, int
                          double dt, double v_w, const void* lags, TO* out) {
     size_t sh = (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15) + (size_t)n_out * sizeof(double);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
-    WT_CUDA(cudaFuncSetAttribute(eq1_kernel<T, L, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dyn_smem(eq1_kernel<T, L, TO>, sh);
     eq1_kernel<T, L, TO><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y,
                                                    z, vx, vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
                                                    static_cast<const L*>(lags), out);

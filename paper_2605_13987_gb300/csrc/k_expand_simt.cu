@@ -31,10 +31,10 @@ void expand_simt(cudaStream_t s, const float* E, int r_pad, const float* W, int 
     dim3 grid((unsigned)((npts + 255) / 256), 3);
     size_t sh = (size_t)nt * r_pad * sizeof(float);
     if (r_pad == 32) {
-        WT_CUDA(cudaFuncSetAttribute(expand_simt_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        allow_dyn_smem(expand_simt_kernel<32>, sh);
         expand_simt_kernel<32><<<grid, 256, sh, s>>>(E, W, nt, ldw, npts, H);
     } else if (r_pad == 64) {
-        WT_CUDA(cudaFuncSetAttribute(expand_simt_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        allow_dyn_smem(expand_simt_kernel<64>, sh);
         expand_simt_kernel<64><<<grid, 256, sh, s>>>(E, W, nt, ldw, npts, H);
     } else {
         fail(WT_ERR_UNSUPPORTED, "expansion rank must be padded to 32 or 64");

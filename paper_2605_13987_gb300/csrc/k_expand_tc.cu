@@ -493,7 +493,7 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
-    WT_CUDA(cudaFuncSetAttribute(tc::expand_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dyn_smem(tc::expand_tc_kernel, sh);
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
     tc::expand_tc_kernel<<<grid, 64 + 32 * tc::NEPI, sh, s>>>(J, nt_pad_max, units, nch, d_err);

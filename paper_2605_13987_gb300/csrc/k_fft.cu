@@ -231,9 +231,9 @@ void Spectral<T>::init(const GridDev& gd, const std::vector<double>& xy, cudaStr
     size_t smz = (size_t)(6 * 2 * g.Nz) * sizeof(C2<T>) + (size_t)n_cols * sizeof(C2<T>);
     size_t smy = (size_t)2 * ZC * (g.Ny + 1) * sizeof(C2<T>);
     size_t smx = (size_t)2 * ZC * (g.Nx + 1) * sizeof(C2<T>);
-    WT_CUDA(cudaFuncSetAttribute(pass_z_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-    WT_CUDA(cudaFuncSetAttribute(pass_y_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy));
-    WT_CUDA(cudaFuncSetAttribute(pass_x_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+    allow_dyn_smem(pass_z_kernel<T>, smz);
+    allow_dyn_smem(pass_y_kernel<T>, smy);
+    allow_dyn_smem(pass_x_kernel<T, T>, smx);
 }
 
 template <class T>

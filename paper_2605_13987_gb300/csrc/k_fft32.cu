@@ -76,7 +76,7 @@ __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __res
 // lambda (Lx, Ly, column and grid positions scale together): the multiplier
 // times (-3 + 2 k_perp^2/|k|^2) for W_x, W_y and (-2 + 2 k_perp^2/|k|^2) for W_z.
 template <int RY, int RX>
-__global__ void __launch_bounds__(256, 2) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
+__global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
                                                         const C2<float>* __restrict__ twy,
                                                         const C2<float>* __restrict__ twx, float* __restrict__ R,
                                                         int mode) {
@@ -120,9 +120,11 @@ __global__ void __launch_bounds__(256, 2) f32_plane_kernel(GridDev g, const C2<f
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {   // y: nxh lines of length ny (decimation in time: lanes read consecutive elements)
-        const int W = ny / RY, G = 32 / W, grp = lane / W, gl = lane % W;
-        const int k2 = warp_fft_k2(gl, W);
+    const int Wy = ny / RY;
+    {   // y: nxh lines of length ny (decimation in time: lanes read consecutive elements).  Lane gl
+        // ends with Y[k + RY bitrev(gl)] and writes it back at row position gl + Wy k (consecutive
+        // lanes, no bank conflicts): Y[y] sits at column sigma(y) = bitrev(y / RY) + Wy (y % RY).
+        const int W = Wy, G = 32 / W, grp = lane / W, gl = lane % W;
         for (int base = warp * G; base < nxh; base += 8 * G) {
             const int mx = base + grp;
             const bool act = mx < nxh;
@@ -132,63 +134,107 @@ __global__ void __launch_bounds__(256, 2) f32_plane_kernel(GridDev g, const C2<f
             warp_fft_dit<RY>(v, gl, W, ty, ny);
             if (act)
 #pragma unroll
-                for (int k = 0; k < RY; ++k) P[mx * ldp + k + RY * k2] = v[k];
+                for (int k = 0; k < RY; ++k) P[mx * ldp + gl + W * k] = v[k];
         }
     }
     __syncthreads();
-    {   // x: ny lines of length nx from the half spectrum (m_x >= nx/2 are zero); decimation in
-        // time reads consecutive rows per lane; results go through a per-warp line for coalesced stores
+    {   // x: ny real lines of length nx from the half spectrum, two lines (y = 2p, 2p + 1) per
+        // complex FFT: Z[m] = A'[m] + i B'[m] with the Hermitian completions A'[0] = Re a[0],
+        // A'[m] = a[m] / 2, A'[nx - m] = conj(a[m]) / 2 (0 < m < nx/2; a carries the x fold
+        // factor 2), A'[nx/2] = 0, so that FFT(Z) = out_a + i out_b.  Decimation in time reads
+        // consecutive rows per lane; the two output lines are staged in the pair's own columns
+        // of P for coalesced stores.
         const int W = nx / RX, G = 32 / W, grp = lane / W, gl = lane % W;
         const int k2 = warp_fft_k2(gl, W);
-        float* stg = reinterpret_cast<float*>(tx + nx) + (size_t)warp * 32 / W * nx;
-        for (int base = warp * G; base < ny; base += 8 * G) {
-            const int y = base + grp;
-            const bool act = y < ny;
+        const int nxq = nx / 2;
+        for (int base = warp * G; base < ny / 2; base += 8 * G) {
+            const int pp = base + grp;
+            const bool act = pp < ny / 2;
+            const int ya = 2 * pp, yb = ya + 1;
+            const int ca = warp_fft_k2(ya / RY, Wy) + Wy * (ya % RY);     // columns sigma(ya), sigma(yb)
+            const int cb = warp_fft_k2(yb / RY, Wy) + Wy * (yb % RY);
             C2<float> v[RX];
 #pragma unroll
             for (int j = 0; j < RX; ++j) {
                 const int mx = gl + W * j;
-                v[j] = (act && mx < nx / 2) ? P[mx * ldp + y] : C2<float>{0.f, 0.f};
+                C2<float> z = {0.f, 0.f};
+                if (act) {
+                    if (mx == 0) {
+                        z = {P[ca].x, P[cb].x};
+                    } else if (mx < nxq) {
+                        const C2<float> a = P[mx * ldp + ca], bb = P[mx * ldp + cb];
+                        z = {0.5f * (a.x - bb.y), 0.5f * (a.y + bb.x)};          // (a + i b) / 2
+                    } else if (mx > nxq) {
+                        const C2<float> a = P[(nx - mx) * ldp + ca], bb = P[(nx - mx) * ldp + cb];
+                        z = {0.5f * (a.x + bb.y), 0.5f * (bb.x - a.y)};          // (conj a + i conj b) / 2
+                    }
+                }
+                v[j] = z;
             }
             warp_fft_dit<RX>(v, gl, W, tx, nx);
-            float* st = stg + (size_t)grp * nx;
+            // the pair's own two columns of P (read only by this lane group, now consumed) hold the
+            // two output lines: x -> float (x & 1) of P[x / 2][y]
+            __syncwarp();
+            if (act)
 #pragma unroll
-            for (int k = 0; k < RX; ++k) st[k + RX * k2] = v[k].x;
+                for (int k = 0; k < RX; ++k) {
+                    const int x = k + RX * k2;
+                    reinterpret_cast<float*>(&P[(x >> 1) * ldp + ca])[x & 1] = v[k].x;
+                    reinterpret_cast<float*>(&P[(x >> 1) * ldp + cb])[x & 1] = v[k].y;
+                }
             __syncwarp();
-            for (int g2 = 0; g2 < G; ++g2) {
-                const int yy = base + g2;
-                if (yy < ny)
-                    for (int x = lane; x < nx; x += 32) Rout[(size_t)yy * nx + x] = stg[(size_t)g2 * nx + x];
+            if (act) {
+                float* ra = Rout + (size_t)ya * nx;
+                for (int x = gl; x < nx; x += W) {
+                    ra[x] = reinterpret_cast<const float*>(&P[(x >> 1) * ldp + ca])[x & 1];
+                    ra[nx + x] = reinterpret_cast<const float*>(&P[(x >> 1) * ldp + cb])[x & 1];
+                }
             }
-            __syncwarp();
         }
     }
 }
 
-// Cosine (W_x, W_y) or sine (W_z) series along z for LB (x, y) lines per block; two real
-// lines share one length-2Nz complex warp FFT.  Lines L = y Nx + x of the
-// plane kernel's layout; output in H's point order (x Ny + y) Nz + z.
+// Cosine (W_x, W_y) or sine (W_z) series along z at the cell centres,
+//   cos: f(z_n) = X_0 + 2 sum_{m>0} X_m cos(pi m (2n+1) / 2N)
+//   sin: f(z_n) = sum_{m>0} S_m sin(pi m (2n+1) / 2N),        N = Nz,
+// for LB (x, y) lines per block, two real lines (a, b) per complex N-point
+// warp FFT (Makhoul's reordering of the DCT-III):
+//   Y_m = (c_m - i c_{N-m}) e^{i pi m / 2N},  c = X^a + i X^b,  c_N = 0,
+//   y = sum_m Y_m e^{2 pi i m k / N}  (Hermitian per line: y^a + i y^b),
+//   f(z_{2k}) = y_k,  f(z_{2k+1}) = y_{N-1-k}.
+// The sine series is the cosine series of the reversed coefficients
+// (X'_m = S_{N-m}) with signs (-1)^n: Y_m = (c_{N-m} - i c_m) e^{i pi m / 2N}
+// and f(z_n) = (-1)^n y_n / 2 after the same reordering.
+// Lines L = y Nx + x of the plane kernel's layout; output in H's point
+// order (x Ny + y) Nz + z, staged per line pair for coalesced stores.
 // grid (ceil(Nx Ny / LB), 3, nb).
 // Skewed index of coefficient m in a staged line pair: a gap every R entries
 // makes the per-lane chunk stride R + 1, so the reads are free of bank conflicts.
 __device__ __forceinline__ int zskew(int m, int R) { return m + m / R; }
+// Row pitch of a staged line pair: room for the skewed inputs and the skewed outputs.
+__host__ __device__ __forceinline__ int zpass_pitch(int nz, int R) {
+    const int a = (nz - 1) + (nz - 1) / R + 1, b = (nz - 1) + ((nz - 1) >> 4) + 1;
+    return (a > b ? a : b) | 1;
+}
 
 template <int RZ, int LB>
-__global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
+__global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
                                                         const C2<float>* __restrict__ twz,
                                                         const C2<float>* __restrict__ zsh, float* __restrict__ out,
                                                         size_t out_sb, size_t out_sc) {
     extern __shared__ unsigned char smem_raw[];
-    const int nx = g.Nx, ny = g.Ny, nz = g.Nz, n2 = 2 * nz;
+    const int nx = g.Nx, ny = g.Ny, nz = g.Nz;
     const size_t nxy = (size_t)nx * ny;
     const int comp = blockIdx.y, b = blockIdx.z;
     const size_t L0 = (size_t)blockIdx.x * LB;
-    const int S = (zskew(nz - 1, RZ) + 1) | 1;                              // odd pair pitch
+    const int S = zpass_pitch(nz, RZ);                                      // odd pair pitch
     C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [LB/2][S]
-    C2<float>* tw = cs + (size_t)(LB / 2) * S;                              // [n2]
-    C2<float>* zs = tw + n2;                                                // [nz]
-    for (int e = threadIdx.x; e < n2; e += blockDim.x) tw[e] = twz[e];
-    for (int e = threadIdx.x; e < nz; e += blockDim.x) zs[e] = zsh[e];
+    C2<float>* tw = cs + (size_t)(LB / 2) * S;                              // [nz]
+    C2<float>* zs = tw + nz;                                                // [nz]
+    for (int e = threadIdx.x; e < nz; e += blockDim.x) {
+        tw[e] = twz[e];
+        zs[e] = zsh[e];
+    }
     const float* src = R + ((size_t)b * 3 + comp) * nz * nxy + L0;
     float* csf = reinterpret_cast<float*>(cs);
     for (int e = threadIdx.x; e < nz * LB; e += blockDim.x) {
@@ -197,43 +243,43 @@ __global__ void __launch_bounds__(256, 2) f32_zpass_kernel(GridDev g, const floa
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int W = n2 / RZ, G = 32 / W, grp = lane / W, gl = lane % W;
+    const int W = nz / RZ, G = 32 / W, grp = lane / W, gl = lane % W;
     const int k2 = warp_fft_k2(gl, W);
+    const bool sine = comp == 2;
     float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
     for (int base = warp * G; base < LB / 2; base += 8 * G) {
         const int f = base + grp;                 // lines 2f, 2f+1 of this block
-        const C2<float>* cf = cs + (size_t)f * S;
+        C2<float>* cf = cs + (size_t)f * S;
         C2<float> v[RZ];
 #pragma unroll
         for (int j1 = 0; j1 < RZ; ++j1) {
-            const int j = j1 + RZ * gl;
-            C2<float> d = {0.f, 0.f};
-            if (j != nz) {
-                const int m = j < nz ? j : n2 - j;
-                const C2<float> c = cf[zskew(m, RZ)];
-                if (comp < 2) {
-                    if (j == 0) d = c;
-                    else d = j < nz ? cmul(c, zs[m]) : cmul(c, C2<float>{zs[m].x, -zs[m].y});
-                } else if (j != 0) {
-                    if (j < nz) { const C2<float> t = cmul(c, zs[m]); d = {0.5f * t.y, -0.5f * t.x}; }
-                    else { const C2<float> t = cmul(c, C2<float>{zs[m].x, -zs[m].y}); d = {-0.5f * t.y, 0.5f * t.x}; }
-                }
-            }
-            v[j1] = d;
+            const int m = j1 + RZ * gl;
+            const C2<float> cm = cf[zskew(m, RZ)];
+            const C2<float> cr = m ? cf[zskew(nz - m, RZ)] : C2<float>{0.f, 0.f};
+            const C2<float> p = sine ? cr : cm, q = sine ? cm : cr;     // Y = (p - i q) e^{i pi m / 2N}
+            v[j1] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
         }
-        warp_fft<RZ>(v, gl, W, tw, n2);
-        const size_t La = L0 + 2 * f, Lb = La + 1;
-        const bool a_ok = La < nxy, b_ok = Lb < nxy;
-        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
-        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
+        warp_fft<RZ>(v, gl, W, tw, nz);
+        __syncwarp();                             // every lane of the group has read its inputs
 #pragma unroll
         for (int k1 = 0; k1 < RZ; ++k1) {
-            const int z = k2 + W * k1;
-            if (z < nz) {
-                if (a_ok) ob[pa + z] = v[k1].x;
-                if (b_ok) ob[pb + z] = v[k1].y;
+            const int j = k2 + W * k1;
+            const int z = 2 * j < nz ? 2 * j : 2 * nz - 2 * j - 1;
+            C2<float> y = v[k1];
+            if (sine) {
+                const float sg = (z & 1) ? -0.5f : 0.5f;
+                y = {sg * y.x, sg * y.y};
             }
+            cf[z + (z >> 4)] = y;                 // z order with a gap every 16: conflict-free both ways
         }
+        __syncwarp();
+        const size_t La = L0 + 2 * f, Lb = La + 1;
+        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
+        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
+        if (La < nxy)
+            for (int z = gl; z < nz; z += W) ob[pa + z] = cf[z + (z >> 4)].x;
+        if (Lb < nxy)
+            for (int z = gl; z < nz; z += W) ob[pb + z] = cf[z + (z >> 4)].y;
     }
 }
 
@@ -251,13 +297,14 @@ static size_t plane_smem(const GridDev& g) {
     const int nxh = g.Nx / 2 + 1;
     int W, R;
     warp_fft_shape(g.Nx, &W, &R);
-    return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>) + (size_t)8 * (32 / W) * g.Nx * sizeof(float);
+    (void)W;
+    return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>);
 }
 static size_t zpass_smem(const GridDev& g, int lb) {
     int W, R;
-    warp_fft_shape(2 * g.Nz, &W, &R);
-    const size_t S = (size_t)(((g.Nz - 1) + (g.Nz - 1) / R + 1) | 1);
-    return ((size_t)(lb / 2) * S + 3 * (size_t)g.Nz) * sizeof(C2<float>);
+    warp_fft_shape(g.Nz, &W, &R);
+    const size_t S = (size_t)zpass_pitch(g.Nz, R);
+    return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz) * sizeof(C2<float>);
 }
 static size_t deposit_smem(const GridDev& g, int n_cols) {
     return (size_t)n_cols * (g.Nx / 2 + 1 + g.Ny) * sizeof(C2<float>);
@@ -282,7 +329,7 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
     if (g.Nx != g.Ny) fail(WT_ERR_UNSUPPORTED, "the FP32 fast path needs Nx == Ny");
     int w;
     warp_fft_shape(g.Nx, &w, &rxy);
-    warp_fft_shape(2 * g.Nz, &w, &rz);
+    warp_fft_shape(g.Nz, &w, &rz);
     if (!supported_r(rxy) || !supported_r(rz))
         fail(WT_ERR_UNSUPPORTED, "FFT length not covered by the register FFT (N / W in {1..10, 12, 14, 15, 16, 24})");
     const int nxh = g.Nx / 2 + 1;
@@ -296,28 +343,28 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
                                                       zsh.p);
     tw_y.alloc(2 * (size_t)g.Ny);
     tw_x.alloc(2 * (size_t)g.Nx);
-    tw_z.alloc(2 * (size_t)2 * g.Nz);
+    tw_z.alloc(2 * (size_t)g.Nz);
     f32_twiddle_kernel<<<(g.Ny + 127) / 128, 128, 0, s>>>(tw_y.p, g.Ny);
     f32_twiddle_kernel<<<(g.Nx + 127) / 128, 128, 0, s>>>(tw_x.p, g.Nx);
-    f32_twiddle_kernel<<<(2 * g.Nz + 127) / 128, 128, 0, s>>>(tw_z.p, 2 * g.Nz);
+    f32_twiddle_kernel<<<(g.Nz + 127) / 128, 128, 0, s>>>(tw_z.p, g.Nz);
     WT_LAUNCH("fast32 tables");
     const size_t sp = plane_smem(g), sz = zpass_smem(g, 64), sd = deposit_smem(g, n_cols);
     if (sp > 227 * 1024 || sz > 227 * 1024 || sd > 227 * 1024)
         fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
     switch (rxy) {
-#define WT_CASE(R) case R: { WT_CUDA(cudaFuncSetAttribute(f32_plane_kernel<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp)); break; }
+#define WT_CASE(R) case R: { allow_dyn_smem(f32_plane_kernel<R, R>, sp); break; }
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }
     switch (rz) {
 #define WT_CASE(R) case R: { \
-        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
-        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
-        WT_CUDA(cudaFuncSetAttribute(f32_zpass_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); break; }
+        allow_dyn_smem(f32_zpass_kernel<R, 16>, sz); \
+        allow_dyn_smem(f32_zpass_kernel<R, 32>, sz); \
+        allow_dyn_smem(f32_zpass_kernel<R, 64>, sz); break; }
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }
-    WT_CUDA(cudaFuncSetAttribute(f32_deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+    allow_dyn_smem(f32_deposit_kernel, sd);
     WT_CUDA(cudaStreamSynchronize(s));
 }
 

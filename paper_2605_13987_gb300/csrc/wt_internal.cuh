@@ -40,6 +40,24 @@ void cuda_check(cudaError_t e, const char* what);
 #define WT_CUDA(call) ::wt::cuda_check((call), #call)
 #define WT_LAUNCH(what) ::wt::cuda_check(cudaGetLastError(), what)
 
+// Let `kernel` take up to `bytes` of dynamic shared memory (fails if the
+// device cannot).  The limit is raised to the device's opt-in maximum and
+// never lowered: it is a per-function setting shared by every context and by
+// launches already captured in CUDA graphs.
+template <class K>
+void allow_dyn_smem(K* kernel, size_t bytes) {
+    int dev = 0, optin = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
+    cudaFuncAttributes fa{};
+    cuda_check(cudaFuncGetAttributes(&fa, kernel), "cudaFuncGetAttributes");
+    const int room = optin - (int)fa.sharedSizeBytes;
+    if ((long long)bytes > room) fail(WT_ERR_UNSUPPORTED, "kernel needs more shared memory than the device has");
+    if (fa.maxDynamicSharedSizeBytes < room)
+        cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, room),
+                   "cudaFuncSetAttribute");
+}
+
 // Owning device buffer.
 template <class T>
 struct DBuf {

@@ -108,7 +108,7 @@ def test_relax_again_recaptures(P, torch):
 
 def test_more_than_one_expansion_launch(P, torch):
     """65 contexts: the graph holds two persistent expansion launches."""
-    ws = W.c3_batch(seed=13, n_sensors=65, nx_choices=(8, 12, 16), n_t=8)
+    ws = W.c3_batch(seed=13, n_sensors=65, nx_choices=(24, 28, 32), n_t=8)
     sens = _sensors(P, ws)
     try:
         Hb = P.extend_batch(sens)

@@ -185,12 +185,12 @@ def c5_large(seed: int = 5, n_tracks: int = 100_000) -> Workload:
 
 
 def _box_band_radius(r: float, h: float, rng: np.random.Generator) -> float:
-    """r, or a redraw from U(4, 10) um, such that sin(pi r / h) >= 0.3.  With
+    """r, or a redraw from U(4, 10) um, such that sin(pi r / h) >= 0.5.  With
     the box-band kernel the fitted capacitance turns indefinite in windows of
     r / h where sin(pi r / h) is negative (found at r/h = 1.45, 1.75, 3.49,
     5.82); every configuration used so far that fits has sin(pi r / h) > 0."""
     for _ in range(10_000):
-        if math.sin(math.pi * r / h) >= 0.3:
+        if math.sin(math.pi * r / h) >= 0.5:
             return r
         r = rng.uniform(4, 10) * UM
     raise ValueError(f"no radius in 4-10 um avoids the indefinite windows at h = {h}")
