@@ -155,7 +155,10 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * point-sample).  H may be device memory (written on cuda_stream, a
  * cudaStream_t or NULL; asynchronous) or host memory (the library computes
  * into an internal device buffer and copies out; returns after the copy).
- * H_bytes must be >= n_t * 3 * Nx*Ny*Nz * sizeof(element), else WT_ERR_ARG. */
+ * H_bytes must be >= n_t * 3 * Nx*Ny*Nz * sizeof(element), else WT_ERR_ARG.
+ * The first FP32 extension of a context (unless wt_batch_run came first)
+ * runs the autotuner of wt_batch_run on it, writing trial results into H,
+ * and returns only after that tuning; later calls reuse the choice. */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
 /* Exact FP64 point evaluation of H (the band-limited spectral sum, no grid
@@ -223,6 +226,25 @@ wt_status wt_eq1_loss(wt_ctx* ctx, wt_precision prec, const wt_tracks* tracks, d
  * *loss receives L (FP32 field), grad[4] the gradient.  Synchronous;
  * allocates device workspaces for the tangents and frees them on return. */
 wt_status wt_eq1_loss_grad(wt_ctx* ctx, const wt_tracks* tracks, double* loss, double* grad);
+
+/* Depth-dependent resistivity of one column (Sec. 5 names a depth-dependent
+ * conductivity profile as a further improvement): rho[j] > 0 [Ohm*m] is
+ * the resistivity of node j's cell, j = 0..n_sources-1 from z0 upward (n
+ * must equal the column's n_sources).  Neighbouring nodes are joined
+ * through two half cells, R = (rho_j + rho_j+1) dz / (2 pi r^2); the
+ * terminal node reaches the electrode end through half a cell.  A uniform
+ * profile gives the uniform column exactly.  rho = NULL returns to the
+ * column's uniform resistivity.  Takes effect at the next wt_relax. */
+wt_status wt_set_resistivity_profile(wt_ctx* ctx, int column, const double* rho, int n);
+
+/* Directional derivative of the loss of wt_eq1_loss (FP32 field) along a
+ * relative change of the node resistivities, rho_j -> rho_j (1 + eps
+ * delta_j) (delta: host array of n_sources values in the order the columns
+ * were added, each column's nodes from z0 upward), by the tangent-linear
+ * chain of wt_eq1_loss_grad restricted to the resistive lines.  *loss
+ * receives L, *dL = dL/deps at eps = 0.  Synchronous. */
+wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const double* delta, double* loss,
+                                   double* dL);
 
 /* Bulk extension of many sensors at once (FP32: the fast path of wt_extend
  * for every context, batched; the paper runs one geometry at a time, so

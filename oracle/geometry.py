@@ -118,8 +118,25 @@ def interp_matrix(columns, lay: Layout):
     return S
 
 
+def node_resistivities(c):
+    """Resistivity of each node's cell: the column's profile (Sec. 5's
+    depth-dependent conductivity), else its uniform value."""
+    if getattr(c, "rho_profile", None) is not None:
+        rho = np.asarray(c.rho_profile, dtype=float)
+        if rho.shape != (c.n_sources,):
+            raise ValueError("rho_profile needs one value per source node")
+        return rho
+    return np.full(c.n_sources, float(c.resistivity))
+
+
 def resistive_line(columns, lay: Layout, v_w=1.0):
-    """K [Ns, Ns] and b [Ns] of the resistive columns."""
+    """K [Ns, Ns] and b [Ns] of the resistive columns.  Node j is the centre
+    of a cell of height dz with resistivity rho_j; two neighbouring nodes are
+    joined through two half cells, R = (rho_j + rho_j+1) dz / (2 pi r^2), and
+    the terminal node reaches the electrode end through half a cell,
+    R = rho_t dz / (2 pi r^2).  For a uniform column these are the segment
+    conductance pi r^2 / (rho dz) of Sec. 5's R = 4 rho L / (pi d^2) and twice
+    it at the terminal."""
     n = lay.n_src
     K = np.zeros((n, n))
     b = np.zeros(n)
@@ -127,16 +144,20 @@ def resistive_line(columns, lay: Layout, v_w=1.0):
         m = c.n_sources
         dz = (c.z1 - c.z0) / m
         off = lay.col_off[ci]
-        g = math.pi * c.radius ** 2 / (c.resistivity * dz)
+        rho = node_resistivities(c)
+        area = math.pi * c.radius ** 2
         for j in range(m - 1):
+            g = area / (0.5 * (rho[j] + rho[j + 1]) * dz)
             p, q = off + j, off + j + 1
             K[p, p] -= g
             K[q, q] -= g
             K[p, q] += g
             K[q, p] += g
-        jt = off + (m - 1 if c.terminal_top else 0)
-        K[jt, jt] -= 2.0 * g
-        b[jt] += 2.0 * g * (v_w if c.driven else 0.0)
+        jl = m - 1 if c.terminal_top else 0
+        gt = area / (0.5 * rho[jl] * dz)
+        jt = off + jl
+        K[jt, jt] -= gt
+        b[jt] += gt * (v_w if c.driven else 0.0)
     return K, b
 
 

@@ -70,6 +70,9 @@ SIGNATURES = {
     "wt_eq1_loss": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(wt_tracks), C.POINTER(C.c_double)]),
     "wt_eq1_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]),
+    "wt_set_resistivity_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
+    "wt_eq1_loss_grad_profile": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
     "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -222,6 +225,27 @@ def wt_eq1_loss_grad(ctx, tracks):
     g = np.zeros(4)
     _check(lib.wt_eq1_loss_grad(ctx, C.byref(tr), C.byref(out), _dptr(g)), ctx)
     return out.value, g
+
+
+def wt_set_resistivity_profile(ctx, column, rho):
+    """Per-node resistivities [Ohm*m] of one column (None: back to uniform)."""
+    lib = load_library()
+    if rho is None:
+        _check(lib.wt_set_resistivity_profile(ctx, int(column), None, 0), ctx)
+        return
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    _check(lib.wt_set_resistivity_profile(ctx, int(column), _dptr(r), len(r)), ctx)
+
+
+def wt_eq1_loss_grad_profile(ctx, tracks, delta):
+    """(loss, dL/deps) along rho_j -> rho_j (1 + eps delta_j)."""
+    lib = load_library()
+    tr = _tracks_struct(tracks)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    out = C.c_double(0.0)
+    g = C.c_double(0.0)
+    _check(lib.wt_eq1_loss_grad_profile(ctx, C.byref(tr), _dptr(d), C.byref(out), C.byref(g)), ctx)
+    return out.value, g.value
 
 
 def wt_batch_run(ctxs, precision, H_list, stream=None):

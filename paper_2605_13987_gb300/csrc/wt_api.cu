@@ -83,6 +83,7 @@ struct wt_ctx {
     cudaStream_t s = nullptr;
     wt_grid grid{};
     std::vector<wt_column> cols;
+    std::vector<std::vector<double>> rho_prof;   // per column: node resistivities (empty: uniform)
     wt_fit_opts opts{};
     std::string err;
     int stage = 0;                   // 0 created, 1 fitted, 2 relaxed
@@ -137,6 +138,7 @@ struct wt_ctx {
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
     int tune_nb = 1, tune_lb = 32, tune_nch = 256;
+    bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
     std::vector<std::unique_ptr<struct BatchPlan>> plans;
@@ -567,20 +569,25 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
     clear_err(c);
     c->times.assign(t, t + nt);
     // resistive lines (Sec. 5): G_seg = pi r^2 / (rho Delta), terminal 2 G_seg
+    // node j is the centre of a cell of height dz and resistivity rho_j: neighbours are joined
+    // through two half cells, the terminal node reaches the electrode end through one
     std::vector<double> diag(ns, 0.0), off(ns, 0.0), k1(ns, 0.0);
     for (size_t k = 0; k < c->cols.size(); ++k) {
         const wt_column& col = c->cols[k];
         const int m = col.n_sources, o = c->col_off[k];
         const double dz = (col.z1 - col.z0) / m;
-        const double gs = kPi * col.radius * col.radius / (col.resistivity * dz);
+        const double area = kPi * col.radius * col.radius;
+        auto rho = [&](int j) { return c->rho_prof[k].empty() ? col.resistivity : c->rho_prof[k][j]; };
         for (int j = 0; j + 1 < m; ++j) {
+            const double gs = area / (0.5 * (rho(j) + rho(j + 1)) * dz);
             off[o + j] = gs;
             diag[o + j] -= gs;
             diag[o + j + 1] -= gs;
         }
-        const int jt = o + (col.terminal_top ? m - 1 : 0);
-        diag[jt] -= 2.0 * gs;
-        k1[jt] = -2.0 * gs;                 // K 1: only the terminal leak survives
+        const int jl = col.terminal_top ? m - 1 : 0;
+        const double gt = area / (0.5 * rho(jl) * dz);
+        diag[o + jl] -= gt;
+        k1[o + jl] = -gt;                   // K 1: only the terminal leak survives
     }
     c->k_diag = diag;
     c->k_off = off;
@@ -749,6 +756,8 @@ void extend64(wt_ctx* c, double* out, cudaStream_t s, int* launches) {
     }
 }
 
+void tune_context(wt_ctx* c, float* H);
+
 void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t us) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
@@ -782,6 +791,17 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
         }
     } else {
         float* out = dev ? static_cast<float*>(H) : c->stage32.p;
+        if (!c->tuned) {
+            // first FP32 extension: pick the launch shapes, writing trial results into out, after
+            // the caller's pending work on its stream and before this extension
+            cudaEvent_t e;
+            WT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            WT_CUDA(cudaEventRecord(e, s));
+            WT_CUDA(cudaStreamWaitEvent(c->s, e, 0));
+            cudaEventDestroy(e);
+            tune_context(c, out);
+            if (c->timing) WT_CUDA(cudaEventRecord(c->ev[0], s));
+        }
         extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, out, s, 0, &launches, c->timing);
     }
     c->last_launches = launches;
@@ -976,7 +996,34 @@ double do_loss(wt_ctx* c, wt_precision prec, const wt_tracks* tr) {
 // Derivative of L = mean i^2 with respect to [readout resistivity scale, bias
 // resistivity scale, radius, lateral scale], tangent-linear through the fit,
 // the relaxation modes, the extension and Eq. 1 (see include/wt.h).
-void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
+// Per-segment derivative of the resistive line along a relative node-resistivity
+// perturbation delta (rho_j -> rho_j (1 + eps delta_j)): dd, doff, dk1 as K's diag,
+// off-diagonal and K 1 (conductances ~ 1 / (rho_j + rho_j+1), terminal ~ 1 / rho_t).
+void kline_direction(const wt_ctx* c, const double* delta, std::vector<double>& dd, std::vector<double>& doff,
+                     std::vector<double>& dk1) {
+    const int ns = c->ns;
+    dd.assign(ns, 0.0);
+    doff.assign(ns, 0.0);
+    dk1.assign(ns, 0.0);
+    for (size_t k = 0; k < c->cols.size(); ++k) {
+        const wt_column& col = c->cols[k];
+        const int m = col.n_sources, o = c->col_off[k];
+        auto rho = [&](int j) { return c->rho_prof[k].empty() ? col.resistivity : c->rho_prof[k][j]; };
+        for (int j = 0; j + 1 < m; ++j) {
+            const double g = c->k_off[o + j];
+            const double dg = -g * (rho(j) * delta[o + j] + rho(j + 1) * delta[o + j + 1]) / (rho(j) + rho(j + 1));
+            doff[o + j] = dg;
+            dd[o + j] -= dg;
+            dd[o + j + 1] -= dg;
+        }
+        const int jt = o + (col.terminal_top ? m - 1 : 0);
+        const double dgt = c->k_k1[jt] * delta[jt];      // k1 = -g_t, d g_t = -g_t delta_t
+        dd[jt] += dgt;
+        dk1[jt] = dgt;
+    }
+}
+
+void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, const double* delta = nullptr) {
     check_tracks(tr);
     if (c->opts.tikhonov > 0.0) fail(WT_ERR_UNSUPPORTED, "the derivative assumes an unregularised fit");
     ensure_spectral(c);
@@ -985,7 +1032,8 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
     const int ns = c->ns, n1 = ns - 1, nc = c->nc, ncol = (int)c->cols.size();
     const int nt = (int)c->times.size();
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
-    for (int k = 0; k < 4; ++k) grad[k] = 0.0;
+    const int n_out_params = delta ? 1 : 4;
+    for (int k = 0; k < n_out_params; ++k) grad[k] = 0.0;
     *loss = 0.0;
     if (tr->n_tracks == 0) return;
     DBuf<float> keep[7];
@@ -1044,8 +1092,10 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
     zeros.alloc((size_t)td.n_tracks * td.n_steps);
     zeros.zero(s);
     DBuf<double> dCn, dKt, T, tmp, dP, Sh, Ah, Om, Mm, cm, dz, dQ, dQq, dgv, dqi;
-    for (int p = 0; p < 4; ++p) {
-        const bool has_dc = p >= 2, has_dk = p <= 2;
+    // parameters 0..3 (s_R, s_B, r, lambda), or 4: the node-resistivity direction delta
+    const int p_first = delta ? 4 : 0, p_last = delta ? 4 : 3;
+    for (int p = p_first; p <= p_last; ++p) {
+        const bool has_dc = p == 2 || p == 3, has_dk = p != 3;
         // ---- fit tangent: dC_n
         if (has_dc) {
             std::vector<double> uxy(c->f_uxy);
@@ -1081,16 +1131,20 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
         // ---- resistive-line tangent: dK~
         if (has_dk) {
             std::vector<double> dd(ns, 0.0), doff(ns, 0.0), dk1(ns, 0.0);
-            for (int k = 0; k < ncol; ++k) {
-                const wt_column& col = c->cols[k];
-                double f = 0.0;
-                if (p == 0 && col.terminal_top) f = -1.0;        // G ~ 1/rho: dG/ds = -G
-                if (p == 1 && !col.terminal_top) f = -1.0;
-                if (p == 2) f = 2.0 / col.radius;                  // G ~ r^2
-                for (int j = c->col_off[k]; j < c->col_off[k + 1]; ++j) {
-                    dd[j] = f * c->k_diag[j];
-                    doff[j] = f * c->k_off[j];
-                    dk1[j] = f * c->k_k1[j];
+            if (p == 4) {
+                kline_direction(c, delta, dd, doff, dk1);
+            } else {
+                for (int k = 0; k < ncol; ++k) {
+                    const wt_column& col = c->cols[k];
+                    double f = 0.0;
+                    if (p == 0 && col.terminal_top) f = -1.0;        // G ~ 1/rho: dG/ds = -G
+                    if (p == 1 && !col.terminal_top) f = -1.0;
+                    if (p == 2) f = 2.0 / col.radius;                  // G ~ r^2
+                    for (int j = c->col_off[k]; j < c->col_off[k + 1]; ++j) {
+                        dd[j] = f * c->k_diag[j];
+                        doff[j] = f * c->k_off[j];
+                        dk1[j] = f * c->k_k1[j];
+                    }
                 }
             }
             double s1 = 0, ds1 = 0;
@@ -1167,7 +1221,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad) {
             eq1_run(c, c->stage32.p, false, td, dI.p, s, zeros.p);
             acc += dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
         }
-        grad[p] = gscale * acc;
+        grad[p - p_first] = gscale * acc;
         if (read_err(c)) fail(WT_ERR_NAN, "non-finite or timed-out tangent");
     }
 }
@@ -1304,6 +1358,15 @@ TuneResult autotune(wt_ctx* c, float* H) {
     return best;
 }
 
+void tune_context(wt_ctx* c, float* H) {
+    const TuneResult t = autotune(c, H);
+    c->tune_nb = t.nb;
+    c->tune_lb = t.lb;
+    c->tune_nch = t.nch;
+    c->tuned = true;
+    alloc_fast32(c);
+}
+
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
                       c->tune_nb, c->tune_lb};
@@ -1372,6 +1435,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_nb = t.nb;
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
+        c->tuned = true;
         alloc_fast32(c);
     }
     // one time chunk for the shared expansion launch: the one most of the units asked for
@@ -1459,7 +1523,10 @@ wt_status wt_add_columns(wt_ctx* ctx, const wt_column* cols, int n) {
     return run(ctx, "wt_add_columns", [&] {
         if (ctx->stage != 0) fail(WT_ERR_STATE, "columns must be added before wt_fit");
         if (n < 0 || (n > 0 && !cols)) fail(WT_ERR_ARG, "bad column array");
-        for (int i = 0; i < n; ++i) ctx->cols.push_back(cols[i]);
+        for (int i = 0; i < n; ++i) {
+            ctx->cols.push_back(cols[i]);
+            ctx->rho_prof.emplace_back();
+        }
     });
 }
 
@@ -1574,6 +1641,33 @@ wt_status wt_get_tuning(wt_ctx* ctx, int* shape3) {
         shape3[0] = ctx->tune_nb;
         shape3[1] = ctx->tune_lb;
         shape3[2] = ctx->tune_nch;
+    });
+}
+
+wt_status wt_set_resistivity_profile(wt_ctx* ctx, int column, const double* rho, int n) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_set_resistivity_profile", [&] {
+        if (column < 0 || column >= (int)ctx->cols.size()) fail(WT_ERR_ARG, "no such column");
+        if (!rho) {
+            ctx->rho_prof[column].clear();
+            return;
+        }
+        if (n != ctx->cols[column].n_sources) fail(WT_ERR_ARG, "the profile needs one value per source node");
+        for (int j = 0; j < n; ++j)
+            if (!(rho[j] > 0.0) || !std::isfinite(rho[j])) fail(WT_ERR_ARG, "resistivities must be finite and > 0");
+        ctx->rho_prof[column].assign(rho, rho + n);
+    });
+}
+
+wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const double* delta, double* loss,
+                                   double* dL) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_loss_grad_profile", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_loss_grad_profile needs wt_relax first");
+        if (!delta || !loss || !dL) fail(WT_ERR_ARG, "NULL argument");
+        for (int j = 0; j < ctx->ns; ++j)
+            if (!std::isfinite(delta[j])) fail(WT_ERR_ARG, "non-finite direction");
+        do_loss_grad(ctx, tracks, loss, dL, delta);
     });
 }
 

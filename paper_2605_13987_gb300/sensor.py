@@ -27,6 +27,10 @@ class Sensor:
         self.device = device
         self.ctx = B.wt_create(grid, device)
         B.wt_add_columns(self.ctx, self.columns)
+        for k, c in enumerate(self.columns):          # depth profiles carried by the column specs
+            prof = getattr(c, "rho_profile", None)
+            if prof is not None:
+                B.wt_set_resistivity_profile(self.ctx, k, prof)
         self.n_sources = sum(int(c.n_sources) for c in self.columns)
         self.times = None
 
@@ -69,6 +73,14 @@ class Sensor:
     def loss_grad(self, tracks):
         """(loss, dL/d[s_R, s_B, r, lambda]) by the library's tangent-linear derivative."""
         return B.wt_eq1_loss_grad(self.ctx, tracks)
+
+    def set_resistivity_profile(self, column, rho):
+        """Per-node resistivities of one column (None: uniform); takes effect at the next relax()."""
+        B.wt_set_resistivity_profile(self.ctx, column, rho)
+
+    def loss_grad_profile(self, tracks, delta):
+        """(loss, dL/deps) along rho_j -> rho_j (1 + eps delta_j)."""
+        return B.wt_eq1_loss_grad_profile(self.ctx, tracks, delta)
 
     def tuning(self):
         """Launch shapes of the FP32 path (nb, lb, nch), set by the batch autotuner."""

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -56,6 +56,7 @@ class ColumnSpec:
     terminal_top: int            # 1: terminal at z1, 0: at z0
     driven: int                  # 1: readout held at V_w
     n_sources: int
+    rho_profile: Optional[Tuple[float, ...]] = None   # per-node resistivity [Ohm*m] (depth profile)
 
 
 @dataclass(frozen=True)
