@@ -265,11 +265,11 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
  * same context concurrently. */
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
-/* Launch shapes the FP32 path of this context uses (set by the autotuner of
- * wt_batch_run; defaults 1, 32, 256): shape3[0] charge vectors per spectral
- * launch, shape3[1] (x, y) lines per z-pass block, shape3[2] time samples per
- * expansion accumulator chunk. */
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape3);
+/* Launch shapes the FP32 path of this context uses (set by the autotuner;
+ * defaults 1, 32, 256, 8): shape4[0] charge vectors per spectral launch,
+ * shape4[1] (x, y) lines per z-pass block, shape4[2] time samples per
+ * expansion accumulator chunk, shape4[3] expansion epilogue warps. */
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape4);
 
 /* Copy intermediate results to host memory (for checks and diagnostics):
  * q: [n_t][n_sources] node charges (after wt_relax);

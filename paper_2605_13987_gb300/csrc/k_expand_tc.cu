@@ -13,8 +13,8 @@
 // (hi*hi + hi*lo + lo*hi, kind::tf32, FP32 accumulation in tensor memory)
 // give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
 // grid point, column = time sample), double buffered in two 256-column
-// halves; eight epilogue warps (two per TMEM lane quadrant, alternate
-// 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
+// halves; eight or sixteen epilogue warps (two or four per TMEM lane quadrant,
+// alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
 // lane quads by shuffles and write H with 16-byte stores: each warp store
 // covers 4 time samples x 32 consecutive grid points (four full 128-byte
 // lines), a quarter of the store instructions of one float per lane.
@@ -42,7 +42,7 @@ namespace wt {
 namespace tc {
 
 constexpr int BM = 128;            // grid points per unit (TMEM lanes)
-constexpr int NEPI = 8;            // epilogue warps
+// epilogue warps: a template parameter of the kernel (8 or 16, chosen by the autotuner)
 constexpr int KR = 32;             // basis rank (TF32 elements per 128-byte row)
 constexpr int NCH = 256;           // time samples per accumulator half (at most; the chunk is a launch argument)
 constexpr int TILE_BYTES = BM * 128;  // one 128 x 32 TF32 tile
@@ -221,6 +221,7 @@ __device__ __forceinline__ void load_coeffs(const float* __restrict__ W, int nt,
     }
 }
 
+template <int NEPI>
 __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -459,7 +460,7 @@ int expand_tc_max_jobs() { return tc::MAX_JOBS; }
 
 // jobs[j]: E [3][32][npts] FP32, W [nt][32] FP32, H [nt][3][npts] FP32; all
 // expansions in one persistent launch of at most `max_ctas` CTAs (0: one per SM).
-void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err) {
+void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err, int nepi) {
     if (n_jobs < 1) return;
     if (nch != 64 && nch != 128 && nch != 256) fail(WT_ERR_ARG, "expansion time chunk must be 64, 128 or 256");
     if (n_jobs > tc::MAX_JOBS) fail(WT_ERR_UNSUPPORTED, "too many expansion jobs for one launch");
@@ -493,10 +494,13 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
-    allow_dyn_smem(tc::expand_tc_kernel, sh);
+    if (nepi != 8 && nepi != 16) fail(WT_ERR_ARG, "expansion epilogue warps must be 8 or 16");
+    if (nepi == 8) allow_dyn_smem(tc::expand_tc_kernel<8>, sh);
+    else allow_dyn_smem(tc::expand_tc_kernel<16>, sh);
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
-    tc::expand_tc_kernel<<<grid, 64 + 32 * tc::NEPI, sh, s>>>(J, nt_pad_max, units, nch, d_err);
+    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, d_err);
+    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, d_err);
     WT_LAUNCH("expand_tc");
 }
 
@@ -504,7 +508,7 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
 void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W, int nt, size_t npts, float* H,
                int* d_err) {
     ExpandJob jb{E, r_pad, r, W, nt, npts, H};
-    expand_tc_jobs(s, &jb, 1, 0, tc::NCH, d_err);
+    expand_tc_jobs(s, &jb, 1, 0, tc::NCH, d_err, 8);
 }
 
 }  // namespace wt

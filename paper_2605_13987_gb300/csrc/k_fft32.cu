@@ -38,17 +38,26 @@ __global__ void f32_tables_kernel(const double* __restrict__ xy, int n_cols, int
     }
 }
 
-// rho^ planes; grid (Nz, nb), threads over (mx, my).  Shared tables:
-// px[c][mx] = e^{-i kx x_c}, qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
+// rho^ planes; grid (Nz, nb, F32_DEP_SPLIT): each block takes a slice of the
+// m_x rows of one plane (warps over rows, lanes over m_y).  Shared tables:
+// px[c][mx] = e^{-i kx x_c} (the block's rows), qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
+constexpr int F32_DEP_SPLIT = 4;
 __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __restrict__ phx,
                                    const C2<float>* __restrict__ phy, const float* __restrict__ Zc,
                                    C2<float>* __restrict__ rho) {
     extern __shared__ unsigned char smem_raw[];
     const int mz = blockIdx.x, b = blockIdx.y;
     const int nxh = g.Nx / 2 + 1, ny = g.Ny;
-    C2<float>* px = reinterpret_cast<C2<float>*>(smem_raw);
-    C2<float>* qy = px + (size_t)n_cols * nxh;
-    for (int e = threadIdx.x; e < n_cols * nxh; e += blockDim.x) px[e] = phx[e];
+    const int rows = (nxh + F32_DEP_SPLIT - 1) / F32_DEP_SPLIT;
+    const int mx0 = blockIdx.z * rows, mx1 = min(nxh, mx0 + rows);
+    if (mx0 >= mx1) return;
+    const int nr = mx1 - mx0;
+    C2<float>* px = reinterpret_cast<C2<float>*>(smem_raw);        // [n_cols][rows]
+    C2<float>* qy = px + (size_t)n_cols * rows;                      // [n_cols][ny]
+    for (int e = threadIdx.x; e < n_cols * nr; e += blockDim.x) {
+        const int c = e / nr, r = e - c * nr;
+        px[c * rows + r] = phx[c * nxh + mx0 + r];
+    }
     for (int e = threadIdx.x; e < n_cols * ny; e += blockDim.x) {
         const float z = Zc[((size_t)b * n_cols + e / ny) * g.Nz + mz];
         const C2<float> p = phy[e];
@@ -56,16 +65,17 @@ __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __res
     }
     __syncthreads();
     C2<float>* out = rho + ((size_t)b * g.Nz + mz) * nxh * ny;
-    for (int e = threadIdx.x; e < nxh * ny; e += blockDim.x) {
-        const int mx = e / ny, my = e % ny;
-        C2<float> acc = {0.f, 0.f};
-        for (int c = 0; c < n_cols; ++c) {
-            const C2<float> a = px[c * nxh + mx], q = qy[c * ny + my];
-            acc.x = fmaf(a.x, q.x, fmaf(-a.y, q.y, acc.x));
-            acc.y = fmaf(a.x, q.y, fmaf(a.y, q.x, acc.y));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < nr; r += nw)
+        for (int my = lane; my < ny; my += 32) {
+            C2<float> acc = {0.f, 0.f};
+            for (int c = 0; c < n_cols; ++c) {
+                const C2<float> a = px[c * rows + r], q = qy[c * ny + my];
+                acc.x = fmaf(a.x, q.x, fmaf(-a.y, q.y, acc.x));
+                acc.y = fmaf(a.x, q.y, fmaf(a.y, q.x, acc.y));
+            }
+            out[(size_t)(mx0 + r) * ny + my] = acc;
         }
-        out[e] = acc;
-    }
 }
 
 // One (k_z plane, component, charge vector) per block: component factor,
@@ -98,28 +108,36 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
     const float ckx = (float)(2.0 * kPi / g.Lx), cky = (float)(2.0 * kPi / g.Ly);
     const float pref = (float)g.pref;
     const C2<float>* rp = rho + ((size_t)b * nz + mz) * nxh * ny;
-    for (int e = threadIdx.x; e < nxh * ny; e += blockDim.x) {
-        const int mx = e / ny, my = e % ny;
-        const int mys = my < ny / 2 ? my : my - ny;
-        C2<float> v = {0.f, 0.f};
-        if (mx != nx / 2 && my != ny / 2) {
-            const float kx = ckx * mx, ky = cky * mys;
-            const float k2 = kx * kx + ky * ky + kz * kz;
-            if (k2 > 0.f) {
-                const C2<float> r = rp[e];
-                float gk = pref / k2 * (mx ? 2.f : 1.f);           // x half-spectrum fold
-                if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + 2.f * (kx * kx + ky * ky) / k2;
-                // cosine components carry no w(m_z) here: the z pass builds
-                // d_m = C e, d_{2N-m} = C e*, which already sums the +-k_z pair
-                if (comp == 0) { const float f = kx * gk; v = {r.y * f, -r.x * f}; }
-                else if (comp == 1) { const float f = ky * gk; v = {r.y * f, -r.x * f}; }
-                else { const float f = 2.f * kz * gk; v = {r.x * f, r.y * f}; }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warps over m_x rows, lanes over m_y (no index division); FP32 fast division: the path's
+    // tolerance is far above its 2-ulp error
+    for (int mx = warp; mx < nxh; mx += 8) {
+        const float kx = ckx * mx;
+        const float fold = mx ? 2.f : 1.f;                        // x half-spectrum fold
+        const C2<float>* rrow = rp + (size_t)mx * ny;
+        C2<float>* prow = P + (size_t)mx * ldp;
+#pragma unroll 4
+        for (int my = lane; my < ny; my += 32) {
+            const int mys = my < ny / 2 ? my : my - ny;
+            C2<float> v = {0.f, 0.f};
+            if (mx != nx / 2 && my != ny / 2) {
+                const float ky = cky * mys;
+                const float kp2 = kx * kx + ky * ky;
+                const float k2 = kp2 + kz * kz;
+                if (k2 > 0.f) {
+                    const C2<float> r = rrow[my];
+                    float gk = __fdividef(pref * fold, k2);
+                    if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + __fdividef(2.f * kp2, k2);
+                    // the z pass's cosine series carries the factor 2 of the +-k_z pair itself
+                    if (comp == 0) { const float f = kx * gk; v = {r.y * f, -r.x * f}; }
+                    else if (comp == 1) { const float f = ky * gk; v = {r.y * f, -r.x * f}; }
+                    else { const float f = 2.f * kz * gk; v = {r.x * f, r.y * f}; }
+                }
             }
+            prow[my] = v;
         }
-        P[mx * ldp + my] = v;
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Wy = ny / RY;
     {   // y: nxh lines of length ny (decimation in time: lanes read consecutive elements).  Lane gl
         // ends with Y[k + RY bitrev(gl)] and writes it back at row position gl + Wy k (consecutive
@@ -235,11 +253,14 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
         tw[e] = twz[e];
         zs[e] = zsh[e];
     }
-    const float* src = R + ((size_t)b * 3 + comp) * nz * nxy + L0;
-    float* csf = reinterpret_cast<float*>(cs);
-    for (int e = threadIdx.x; e < nz * LB; e += blockDim.x) {
-        const int m = e / LB, l = e % LB;
-        csf[2 * ((l >> 1) * S + zskew(m, RZ)) + (l & 1)] = (L0 + l < nxy) ? src[(size_t)m * nxy + l] : 0.f;
+    {   // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
+        constexpr int MS = 256 / LB;
+        const int l = threadIdx.x % LB, m0 = threadIdx.x / LB;
+        const bool lin = L0 + l < nxy;
+        const float* sp = R + ((size_t)b * 3 + comp) * nz * nxy + L0 + l;
+        float* dst = reinterpret_cast<float*>(cs) + 2 * (size_t)(l >> 1) * S + (l & 1);
+#pragma unroll 8
+        for (int m = m0; m < nz; m += MS) dst[2 * zskew(m, RZ)] = lin ? sp[(size_t)m * nxy] : 0.f;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,30 +270,33 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
     float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
     for (int base = warp * G; base < LB / 2; base += 8 * G) {
         const int f = base + grp;                 // lines 2f, 2f+1 of this block
-        C2<float>* cf = cs + (size_t)f * S;
+        const bool act = f < LB / 2;              // groups past the block's pairs only join the shuffles
+        C2<float>* cf = cs + (size_t)(act ? f : 0) * S;
         C2<float> v[RZ];
 #pragma unroll
         for (int j1 = 0; j1 < RZ; ++j1) {
             const int m = j1 + RZ * gl;
-            const C2<float> cm = cf[zskew(m, RZ)];
-            const C2<float> cr = m ? cf[zskew(nz - m, RZ)] : C2<float>{0.f, 0.f};
+            const C2<float> cm = act ? cf[zskew(m, RZ)] : C2<float>{0.f, 0.f};
+            const C2<float> cr = (act && m) ? cf[zskew(nz - m, RZ)] : C2<float>{0.f, 0.f};
             const C2<float> p = sine ? cr : cm, q = sine ? cm : cr;     // Y = (p - i q) e^{i pi m / 2N}
             v[j1] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
         }
         warp_fft<RZ>(v, gl, W, tw, nz);
         __syncwarp();                             // every lane of the group has read its inputs
+        if (act)
 #pragma unroll
-        for (int k1 = 0; k1 < RZ; ++k1) {
-            const int j = k2 + W * k1;
-            const int z = 2 * j < nz ? 2 * j : 2 * nz - 2 * j - 1;
-            C2<float> y = v[k1];
-            if (sine) {
-                const float sg = (z & 1) ? -0.5f : 0.5f;
-                y = {sg * y.x, sg * y.y};
+            for (int k1 = 0; k1 < RZ; ++k1) {
+                const int j = k2 + W * k1;
+                const int z = 2 * j < nz ? 2 * j : 2 * nz - 2 * j - 1;
+                C2<float> y = v[k1];
+                if (sine) {
+                    const float sg = (z & 1) ? -0.5f : 0.5f;
+                    y = {sg * y.x, sg * y.y};
+                }
+                cf[z + (z >> 4)] = y;             // z order with a gap every 16: conflict-free both ways
             }
-            cf[z + (z >> 4)] = y;                 // z order with a gap every 16: conflict-free both ways
-        }
         __syncwarp();
+        if (!act) continue;
         const size_t La = L0 + 2 * f, Lb = La + 1;
         const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
         const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
@@ -307,7 +331,8 @@ static size_t zpass_smem(const GridDev& g, int lb) {
     return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz) * sizeof(C2<float>);
 }
 static size_t deposit_smem(const GridDev& g, int n_cols) {
-    return (size_t)n_cols * (g.Nx / 2 + 1 + g.Ny) * sizeof(C2<float>);
+    const int rows = (g.Nx / 2 + 1 + F32_DEP_SPLIT - 1) / F32_DEP_SPLIT;
+    return (size_t)n_cols * (rows + g.Ny) * sizeof(C2<float>);
 }
 
 // Register-FFT lengths compiled in: elements per lane R = N / W.
@@ -372,7 +397,7 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
                     cudaStream_t s, int mode, int lb) const {
     if (lb != 16 && lb != 32 && lb != 64) fail(WT_ERR_ARG, "z-pass lines per block must be 16, 32 or 64");
     C2<float>* rc = reinterpret_cast<C2<float>*>(rho);
-    dim3 gd(g.Nz, nb);
+    dim3 gd(g.Nz, nb, F32_DEP_SPLIT);
     f32_deposit_kernel<<<gd, 256, deposit_smem(g, n_cols), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
                                                                 reinterpret_cast<const C2<float>*>(phy.p), Zc, rc);
     WT_LAUNCH("f32_deposit");

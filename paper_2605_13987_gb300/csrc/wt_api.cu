@@ -81,6 +81,7 @@ using namespace wt;
 struct wt_ctx {
     int dev = 0;
     cudaStream_t s = nullptr;
+    cudaStream_t s_copy = nullptr;   // device-to-host copies of host-buffer extensions
     wt_grid grid{};
     std::vector<wt_column> cols;
     std::vector<std::vector<double>> rho_prof;   // per column: node resistivities (empty: uniform)
@@ -137,7 +138,7 @@ struct wt_ctx {
     int last_launches = 0;
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
-    int tune_nb = 1, tune_lb = 32, tune_nch = 256;
+    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -705,8 +706,10 @@ void ensure_spectral(wt_ctx* c) {
 // FP32 fast path for a basis of charge vectors Ub [r][ns] and coefficients
 // W32 [nt][32]: column transforms, basis fields (mode 0: the field, 1: its
 // lateral-scale derivative) and the expansion into out [nt][3][npts].
+// host_out != NULL: out is a device staging buffer; the expansion runs in time chunks and each
+// chunk is copied to host_out on the context's copy stream while the next one is computed.
 void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt, float* out, cudaStream_t s, int mode,
-                    int* launches, bool timing) {
+                    int* launches, bool timing, float* host_out = nullptr) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size();
@@ -729,9 +732,36 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
         *launches += 3;
     }
     if (timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
+    if (host_out) {
+        // about 2 GB of H per chunk (whole 32-sample tiles): copies overlap the later chunks' expansion
+        const size_t per_t = 3 * npts * sizeof(float);
+        int tc_n = (int)std::max<size_t>(1, ((size_t)2 << 30) / per_t);
+        tc_n = std::max(32, tc_n / 32 * 32);
+        cudaEvent_t ev;
+        WT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        for (int t0 = 0; t0 < nt; t0 += tc_n) {
+            const int n = std::min(tc_n, nt - t0);
+            float* o = out + (size_t)t0 * 3 * npts;
+            if (tc) {
+                ExpandJob jb{c->E32.p, rp, r, W32 + (size_t)t0 * rp, n, npts, o};
+                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
+            } else {
+                expand_simt(s, c->E32.p, rp, W32 + (size_t)t0 * rp, n, rp, npts, o);
+            }
+            *launches += 1;
+            WT_CUDA(cudaEventRecord(ev, s));
+            WT_CUDA(cudaStreamWaitEvent(c->s_copy, ev, 0));
+            WT_CUDA(cudaMemcpyAsync(host_out + (size_t)t0 * 3 * npts, o, (size_t)n * per_t, cudaMemcpyDeviceToHost,
+                                    c->s_copy));
+        }
+        cudaEventDestroy(ev);
+        if (timing) WT_CUDA(cudaEventRecord(c->ev[3], s));
+        WT_CUDA(cudaStreamSynchronize(c->s_copy));
+        return;
+    }
     if (tc) {
         ExpandJob jb{c->E32.p, rp, r, W32, nt, npts, out};
-        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p);
+        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
     } else {
         expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
     }
@@ -802,10 +832,12 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
             tune_context(c, out);
             if (c->timing) WT_CUDA(cudaEventRecord(c->ev[0], s));
         }
-        extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, out, s, 0, &launches, c->timing);
+        extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, out, s, 0, &launches, c->timing,
+                       dev ? nullptr : static_cast<float*>(H));
     }
     c->last_launches = launches;
     c->ev_recorded = c->timing;
+    if (!dev && prec == WT_FP32) return;     // copied out chunk by chunk above
     if (!dev) {
         const void* src = prec == WT_FP64 ? (const void*)c->stage64.p : (const void*)c->stage32.p;
         WT_CUDA(cudaMemcpyAsync(H, src, need, cudaMemcpyDeviceToHost, s));
@@ -1017,9 +1049,9 @@ void kline_direction(const wt_ctx* c, const double* delta, std::vector<double>& 
             dd[o + j + 1] -= dg;
         }
         const int jt = o + (col.terminal_top ? m - 1 : 0);
-        const double dgt = c->k_k1[jt] * delta[jt];      // k1 = -g_t, d g_t = -g_t delta_t
-        dd[jt] += dgt;
-        dk1[jt] = dgt;
+        const double dgt = c->k_k1[jt] * delta[jt];      // k1 = -g_t, so d g_t = -g_t delta_t = k1 delta_t
+        dd[jt] -= dgt;                                   // K_tt holds -g_t, K 1 at t is -g_t
+        dk1[jt] = -dgt;
     }
 }
 
@@ -1244,7 +1276,7 @@ struct BatchEntry {
 
 struct BatchPlan {
     std::vector<BatchEntry> ents;
-    int nch = 256;
+    int nch = 256, nepi = 8;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long last_use = 0;
@@ -1259,7 +1291,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch;
+    int nb, lb, nch, nepi;
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1329,7 +1361,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, 1e30, 1e30};
     c->tune_nb = 1;
     alloc_fast32(c);
     column_ztransform<float>(s, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
@@ -1347,11 +1379,12 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     spectral_all(c, s);
-    for (int nch : {64, 128, 256}) {
-        ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
-        const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p); });
-        if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; }
-    }
+    for (int nepi : {8, 16})
+        for (int nch : {64, 128, 256}) {
+            ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
+            const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi); });
+            if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; }
+        }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out while tuning");
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[tune_key(c)] = best;
@@ -1363,6 +1396,7 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_nb = t.nb;
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
+    c->tune_nepi = t.nepi;
     c->tuned = true;
     alloc_fast32(c);
 }
@@ -1392,7 +1426,7 @@ void capture_batch(BatchPlan& P, wt_ctx* const* ctxs, int n, float* const* H) {
         }
         const int mj = expand_tc_max_jobs();
         for (int j0 = 0; j0 < n; j0 += mj)
-            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p);
+            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi);
     } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
@@ -1435,28 +1469,31 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_nb = t.nb;
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
+        c->tune_nepi = t.nepi;
         c->tuned = true;
         alloc_fast32(c);
     }
-    // one time chunk for the shared expansion launch: the one most of the units asked for
-    std::map<int, double> votes;
+    // one (time chunk, epilogue warps) pair for the shared expansion launch: the one most of the
+    // grid points asked for
+    std::map<std::pair<int, int>, double> votes;
     for (int i = 0; i < n; ++i) {
         const wt_grid& g = ctxs[i]->grid;
-        votes[ctxs[i]->tune_nch] += (double)g.Nx * g.Ny * g.Nz;
+        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi}] += (double)g.Nx * g.Ny * g.Nz;
     }
-    int nch = 256;
+    int nch = 256, nepi = 8;
     double top = -1;
     for (auto& v : votes)
-        if (v.second > top) { top = v.second; nch = v.first; }
+        if (v.second > top) { top = v.second; nch = v.first.first; nepi = v.first.second; }
     std::vector<BatchEntry> want;
     for (int i = 0; i < n; ++i) want.push_back(entry_of(ctxs[i], H[i]));
     BatchPlan* plan = nullptr;
     for (auto& p : c0->plans)
-        if (p->nch == nch && p->ents == want) plan = p.get();
+        if (p->nch == nch && p->nepi == nepi && p->ents == want) plan = p.get();
     if (!plan) {
         auto P = std::make_unique<BatchPlan>();
         P->ents = want;
         P->nch = nch;
+        P->nepi = nepi;
         capture_batch(*P, ctxs, n, reinterpret_cast<float* const*>(H));
         if (c0->plans.size() >= 4) {         // keep the four most recently used graphs
             auto old = std::min_element(c0->plans.begin(), c0->plans.end(),
@@ -1506,11 +1543,13 @@ wt_status wt_create(wt_ctx** out, const wt_grid* grid, int cuda_device) {
         c->grid = g;
         try {
             WT_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+            WT_CUDA(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
             c->d_err.alloc(16);
             c->d_err.zero(c->s);
             c->d_scr.alloc(16);
         } catch (...) {
             if (c->s) cudaStreamDestroy(c->s);
+            if (c->s_copy) cudaStreamDestroy(c->s_copy);
             delete c;
             throw;
         }
@@ -1634,13 +1673,14 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
     });
 }
 
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape3) {
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape4) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_get_tuning", [&] {
-        if (!shape3) fail(WT_ERR_ARG, "NULL output");
-        shape3[0] = ctx->tune_nb;
-        shape3[1] = ctx->tune_lb;
-        shape3[2] = ctx->tune_nch;
+        if (!shape4) fail(WT_ERR_ARG, "NULL output");
+        shape4[0] = ctx->tune_nb;
+        shape4[1] = ctx->tune_lb;
+        shape4[2] = ctx->tune_nch;
+        shape4[3] = ctx->tune_nepi;
     });
 }
 
@@ -1737,11 +1777,13 @@ void wt_destroy(wt_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->dev);
     if (ctx->s) cudaStreamSynchronize(ctx->s);
-    cudaStream_t s = ctx->s;
+    cudaStream_t s = ctx->s, s2 = ctx->s_copy;
+    if (s2) cudaStreamSynchronize(s2);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
     if (s) cudaStreamDestroy(s);
+    if (s2) cudaStreamDestroy(s2);
 }
 
 }  // extern "C"

@@ -83,7 +83,7 @@ class Sensor:
         return B.wt_eq1_loss_grad_profile(self.ctx, tracks, delta)
 
     def tuning(self):
-        """Launch shapes of the FP32 path (nb, lb, nch), set by the batch autotuner."""
+        """Launch shapes of the FP32 path (nb, lb, nch, nepi), set by the autotuner."""
         return B.wt_get_tuning(self.ctx)
 
     def charges(self):
