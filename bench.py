@@ -365,16 +365,37 @@ def run_ours(args):
         sen.set_timing(False)
         sen.extend("fp32", out=Hh)
         barrier(world)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
         k2 = max(1, min(3, args.steps))
-        for _ in range(k2):
+        per_call = []
+        for _ in range(k2):             # each call is one whole end-to-end step; the median is reported
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             sen.extend("fp32", out=Hh)
-        torch.cuda.synchronize()
-        el = max_over_ranks((time.perf_counter() - t1) / k2, world)
+            torch.cuda.synchronize()
+            per_call.append(time.perf_counter() - t1)
+        el = max_over_ranks(statistics.median(per_call), world)
         e2e = {"value": world * ps_step / el, "unit": "point-samples/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": int(Hh.numel() * 4)}
+               "d2h_bytes_per_step": int(Hh.numel() * 4), "ms_per_call": [1e3 * t for t in per_call]}
         del Hh
+
+    # the comparison path of the metric: the FP64 plain extension (one FP64 spectral transform per
+    # time sample), timed once after one untimed call, into its own device buffer
+    fp64 = None
+    if not args.no_fp64 and not args.profile:
+        H64 = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float64, device=dev)
+        sen.set_timing(False)
+        sen.extend("fp64", out=H64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sen.extend("fp64", out=H64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": ps_step / (ms64 / 1e3), "unit": "point-samples/s", "ms_per_step": ms64,
+                "dtype": "f64", "fp32_speedup": ms64 / ms_max}
+        del H64
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
@@ -408,7 +429,7 @@ def run_ours(args):
                          "spectral_passes": sum(s[1] for s in stage_ms) / len(stage_ms),
                          "expansion": exp_ms},
             "step_frac_of_hbm_roof": (alg_bytes / (ms_max / 1e3) / 1e9) / peak,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64_plain": fp64,
             "clocks": clk.summary(local),
             "setup_s": setup,
             "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond,
@@ -430,6 +451,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 plain path")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--arena-gb", type=float, default=96.0, help="c3: device memory for one wave's H")
     ap.add_argument("--profile", action="store_true",

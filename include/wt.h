@@ -271,6 +271,51 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
  * expansion accumulator chunk, shape4[3] expansion epilogue warps. */
 wt_status wt_get_tuning(wt_ctx* ctx, int* shape4);
 
+/* Static field of the electrodes held at fixed potentials (the paper's
+ * static drift field, Fig. 2; the sigma -> infinity limit of the
+ * relaxation): every node of column k at phi_cols[k] volts (host array of
+ * n_columns values), node charges q = C_n phi, and their field
+ * E[c][x][y][z] = -grad(potential) on the grid (V/m) by the extension's
+ * spectral path (WT_FP32: float, WT_FP64: double).  E: device buffer of
+ * at least 3 Nx Ny Nz elements.  Equal potentials on all electrodes give
+ * no field.  Needs wt_fit; ordered after the caller's pending work on
+ * cuda_stream, returns when E is written. */
+wt_status wt_static_field(wt_ctx* ctx, const double* phi_cols, wt_precision prec, void* E, size_t E_bytes,
+                          void* cuda_stream);
+
+/* Carrier drift in a static field (the paper uses Garfield++ for the
+ * transport; this is a constant-mobility drift that produces tracks for
+ * wt_eq1): dx/dt = smu[a] E(x) (smu = signed mobility [m^2/(V s)], + for
+ * holes, - for electrons), explicit midpoint steps of dt in FP64 on the
+ * trilinear interpolation of E (FP32 [3][Nx][Ny][Nz], device; grid points
+ * at (i hx, j hy, (k + 1/2) hz), x and y periodic, z clamped as in Eq. 1).
+ * Step m of carrier a records its midpoint and velocity in
+ * x..vz[a][m] (device FP32 arrays [n][n_steps], the wt_tracks layout); a
+ * carrier stops after the step that ends inside a column or outside
+ * 0 <= z <= Lz, and its later steps repeat its last position with zero
+ * velocity.  x0: device [n][3] start positions (FP64).  Synchronous. */
+wt_status wt_drift(wt_ctx* ctx, const float* E, const double* x0, const double* smu, int n, int n_steps, double dt,
+                   float* x, float* y, float* z, float* vx, float* vy, float* vz, void* cuda_stream);
+
+/* Front-end shaping of Eq. 1 currents.  The paper names the readout
+ * electronics as the next step of the signal chain without giving a
+ * transfer function; this is the common CR-(RC)^n shaper of unit area,
+ *   h(t) = (t / tau)^n e^(-t / tau) / (n! tau),  peak at t = n tau,
+ * applied on the output grid of wt_eq1 by the rectangle rule,
+ *   v[tr][m] = gain * sum_k h(k dt) dt i[tr][m - k]  +  noise_rms * noise[tr][m],
+ * with FP64 accumulation (taps beyond (n + 60) tau dropped).  i, noise (may
+ * be NULL) and v: device arrays [n_tracks][n_out] (FP32); the noise samples
+ * are drawn by the caller.  Asynchronous on cuda_stream.  n_out is limited
+ * by one block's shared memory (12 bytes per sample, 200 KB). */
+typedef struct {
+    double tau;        /* shaping time constant [s] */
+    int order;         /* n, 0..20 */
+    double gain;       /* output per unit current */
+    double noise_rms;  /* scale of the caller's noise samples */
+} wt_shaper;
+wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double dt, const wt_shaper* shaper,
+                   const float* noise, float* v, void* cuda_stream);
+
 /* Copy intermediate results to host memory (for checks and diagnostics):
  * q: [n_t][n_sources] node charges (after wt_relax);
  * cn: [n_sources][n_sources] capacitance (after wt_fit);

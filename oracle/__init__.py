@@ -27,6 +27,8 @@ listed in the module docstrings:
                at each time sample (Abstract; Sec. 1: discrete Fourier
                transforms).
 * ``eq1``      the Ramo-Shockley-Riegler convolution, Eq. 1.
+* ``electronics`` CR-(RC)^n shaping of the currents (parameterised; the paper
+               gives no transfer function).
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 except the brute-force finite-difference model (``bruteforce``), which is a

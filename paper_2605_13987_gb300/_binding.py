@@ -48,6 +48,10 @@ class wt_tracks(C.Structure):
                 ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("q", C.c_void_p)]
 
 
+class wt_shaper(C.Structure):
+    _fields_ = [("tau", C.c_double), ("order", C.c_int), ("gain", C.c_double), ("noise_rms", C.c_double)]
+
+
 class wt_info(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("n_sources", C.c_int), ("n_colloc", C.c_int), ("n_t", C.c_int),
                 ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
@@ -73,6 +77,11 @@ SIGNATURES = {
     "wt_set_resistivity_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
     "wt_eq1_loss_grad_profile": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.POINTER(C.c_double),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "wt_static_field": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "wt_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double]
+                 + [C.c_void_p] * 7),
+    "wt_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.POINTER(wt_shaper),
+                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
     "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -246,6 +255,38 @@ def wt_eq1_loss_grad_profile(ctx, tracks, delta):
     g = C.c_double(0.0)
     _check(lib.wt_eq1_loss_grad_profile(ctx, C.byref(tr), _dptr(d), C.byref(out), C.byref(g)), ctx)
     return out.value, g.value
+
+
+def wt_static_field(ctx, phi_cols, precision, E, stream=None):
+    """Static field of the electrodes at phi_cols volts into the device tensor E [3, Nx, Ny, Nz]."""
+    lib = load_library()
+    p = np.ascontiguousarray(phi_cols, dtype=np.float64)
+    _check(lib.wt_static_field(ctx, _dptr(p), int(precision), _ptr(E), E.numel() * E.element_size(),
+                               _stream_handle(stream)), ctx)
+    return E
+
+
+def wt_drift(ctx, E, x0, smu, n_steps, dt, stream=None):
+    """Drift tracks (dict of device tensors x, y, z, vx, vy, vz [n, n_steps])."""
+    import torch
+    lib = load_library()
+    n = int(x0.shape[0])
+    out = {k: torch.empty((n, n_steps), dtype=torch.float32, device=E.device) for k in ("x", "y", "z", "vx", "vy", "vz")}
+    _check(lib.wt_drift(ctx, _ptr(E), _ptr(x0), _ptr(smu), n, int(n_steps), float(dt),
+                        *[_ptr(out[k]) for k in ("x", "y", "z", "vx", "vy", "vz")], _stream_handle(stream)), ctx)
+    return out
+
+
+def wt_shape(ctx, i, dt, tau, order, gain=1.0, noise=None, noise_rms=0.0, out=None, stream=None):
+    """CR-(RC)^n shaping of device currents i [n_tracks, n_out] (torch, FP32)."""
+    import torch
+    lib = load_library()
+    if out is None:
+        out = torch.empty_like(i)
+    sh = wt_shaper(float(tau), int(order), float(gain), float(noise_rms))
+    _check(lib.wt_shape(ctx, _ptr(i), int(i.shape[0]), int(i.shape[1]), float(dt), C.byref(sh), _ptr(noise),
+                        _ptr(out), _stream_handle(stream)), ctx)
+    return out
 
 
 def wt_batch_run(ctxs, precision, H_list, stream=None):

@@ -61,6 +61,9 @@ void eq1_pack_lag(void*, int, float, float);
 size_t eq1_lag64_size();
 void eq1_pack_lag64(void*, int, double, double);
 double dot_f64(cudaStream_t, const double*, const double*, size_t, double*);
+void shape_launch(cudaStream_t, const float*, int, int, double, double, int, double, double, const float*, float*);
+void drift_launch(cudaStream_t, const float*, int, int, int, double, double, double, const std::vector<double>&,
+                  const double*, const double*, int, int, double, float*, float*, float*, float*, float*, float*);
 
 void fail(wt_status code, const std::string& msg) { throw Error{code, msg}; }
 
@@ -1708,6 +1711,96 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
         for (int j = 0; j < ctx->ns; ++j)
             if (!std::isfinite(delta[j])) fail(WT_ERR_ARG, "non-finite direction");
         do_loss_grad(ctx, tracks, loss, dL, delta);
+    });
+}
+
+wt_status wt_static_field(wt_ctx* ctx, const double* phi_cols, wt_precision prec, void* E, size_t E_bytes,
+                          void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_static_field", [&] {
+        if (ctx->stage < 1) fail(WT_ERR_STATE, "wt_static_field needs wt_fit first");
+        if (!phi_cols || !E) fail(WT_ERR_ARG, "NULL argument");
+        if (prec != WT_FP32 && prec != WT_FP64) fail(WT_ERR_ARG, "bad precision");
+        const wt_grid& g = ctx->grid;
+        const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+        const size_t need = 3 * npts * (prec == WT_FP64 ? 8 : 4);
+        if (E_bytes < need) fail(WT_ERR_ARG, "E_bytes too small: need " + std::to_string(need));
+        if (!is_device_ptr(E)) fail(WT_ERR_ARG, "E must be device memory");
+        ensure_spectral(ctx);
+        cudaStream_t s = ctx->s;
+        const int ns = ctx->ns, ncol = (int)ctx->cols.size();
+        // every node of a column at its electrode's potential; q = C_n phi
+        std::vector<double> phi(ns);
+        for (int k = 0; k < ncol; ++k) {
+            if (!std::isfinite(phi_cols[k])) fail(WT_ERR_ARG, "non-finite potential");
+            for (int j = ctx->col_off[k]; j < ctx->col_off[k + 1]; ++j) phi[j] = phi_cols[k];
+        }
+        DBuf<double> dphi, q;
+        dphi.upload(phi.data(), ns, s);
+        q.alloc(ns);
+        dgemv(s, false, ns, ns, 1.0, ctx->Cn.p, ns, dphi.p, 0.0, q.p);
+        // order after the caller's pending work on its stream, then back
+        cudaEvent_t ev;
+        WT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        WT_CUDA(cudaEventRecord(ev, static_cast<cudaStream_t>(stream)));
+        WT_CUDA(cudaStreamWaitEvent(s, ev, 0));
+        if (prec == WT_FP64) {
+            ctx->Zc64.alloc((size_t)4 * ncol * g.Nz);
+            ctx->G64.alloc(ctx->sp64.scratch_elems(4));
+            column_ztransform<double>(s, q.p, 1, ns, ns, ctx->zcos.p, ctx->d_col_off.p, ncol, g.Nz, ctx->Zc64.p);
+            ctx->sp64.fields(ctx->Zc64.p, 1, ctx->G64.p, static_cast<double*>(E), 0, npts, s);
+        } else {
+            ctx->Zc32.alloc((size_t)32 * ncol * g.Nz);
+            ctx->rho32.alloc(ctx->sp32.rho_elems(ctx->tune_nb));
+            ctx->R32.alloc(ctx->sp32.r_elems(ctx->tune_nb));
+            column_ztransform<float>(s, q.p, 1, ns, ns, ctx->zcos.p, ctx->d_col_off.p, ncol, g.Nz, ctx->Zc32.p);
+            ctx->sp32.fields(ctx->Zc32.p, 1, ctx->rho32.p, ctx->R32.p, static_cast<float*>(E), 0, npts, s, 0,
+                             ctx->tune_lb);
+        }
+        WT_CUDA(cudaEventRecord(ev, s));
+        WT_CUDA(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), ev, 0));
+        WT_CUDA(cudaStreamSynchronize(s));
+        cudaEventDestroy(ev);
+    });
+}
+
+wt_status wt_drift(wt_ctx* ctx, const float* E, const double* x0, const double* smu, int n, int n_steps, double dt,
+                   float* x, float* y, float* z, float* vx, float* vy, float* vz, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_drift", [&] {
+        if (n < 0 || n_steps < 1 || !(dt > 0.0)) fail(WT_ERR_ARG, "bad sizes or dt");
+        if (n == 0) return;
+        const void* ptrs[10] = {E, x0, smu, x, y, z, vx, vy, vz, nullptr};
+        for (int k = 0; k < 9; ++k)
+            if (!ptrs[k] || !is_device_ptr(ptrs[k])) fail(WT_ERR_ARG, "every array of wt_drift must be device memory");
+        std::vector<double> cs;
+        for (const wt_column& c : ctx->cols) {
+            cs.push_back(c.x);
+            cs.push_back(c.y);
+            cs.push_back(c.radius * c.radius);
+            cs.push_back(c.z0);
+            cs.push_back(c.z1);
+        }
+        const wt_grid& g = ctx->grid;
+        drift_launch(static_cast<cudaStream_t>(stream), E, g.Nx, g.Ny, g.Nz, g.Lx, g.Ly, g.Lz, cs, x0, smu, n, n_steps,
+                     dt, x, y, z, vx, vy, vz);
+    });
+}
+
+wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double dt, const wt_shaper* sh,
+                   const float* noise, float* v, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_shape", [&] {
+        if (!sh || n_tracks < 0 || n_out < 1 || !(dt > 0.0)) fail(WT_ERR_ARG, "bad sizes or dt");
+        if (!(sh->tau > 0.0) || sh->order < 0 || sh->order > 20 || !std::isfinite(sh->gain) ||
+            !std::isfinite(sh->noise_rms))
+            fail(WT_ERR_ARG, "bad shaper parameters (tau > 0, 0 <= order <= 20)");
+        if (n_tracks == 0) return;
+        if (!i || !v || !is_device_ptr(i) || !is_device_ptr(v) || (noise && !is_device_ptr(noise)))
+            fail(WT_ERR_ARG, "currents, noise and output must be device memory");
+        if ((size_t)n_out * 12 > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "n_out too large for one block's shared memory");
+        shape_launch(static_cast<cudaStream_t>(stream), i, n_tracks, n_out, dt, sh->tau, sh->order, sh->gain,
+                     sh->noise_rms, noise, v);
     });
 }
 

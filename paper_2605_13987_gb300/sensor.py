@@ -82,6 +82,27 @@ class Sensor:
         """(loss, dL/deps) along rho_j -> rho_j (1 + eps delta_j)."""
         return B.wt_eq1_loss_grad_profile(self.ctx, tracks, delta)
 
+    def static_field(self, phi_cols, precision="fp32"):
+        """Static field [3, Nx, Ny, Nz] of the electrodes held at phi_cols volts."""
+        import torch
+        prec = B.WT_FP64 if precision in ("fp64", B.WT_FP64) else B.WT_FP32
+        g = self.grid
+        E = torch.empty((3, g.Nx, g.Ny, g.Nz), dtype=torch.float64 if prec == B.WT_FP64 else torch.float32,
+                        device=f"cuda:{self.device}")
+        return B.wt_static_field(self.ctx, phi_cols, prec, E)
+
+    def drift(self, E, x0, smu, n_steps, dt, charge=None):
+        """Carrier tracks in the static field E (FP32): a track dict for eq1()."""
+        import torch
+        out = B.wt_drift(self.ctx, E, x0, smu, n_steps, dt)
+        out.update(n_tracks=int(x0.shape[0]), n_steps=int(n_steps), n_out=2 * int(n_steps), dt=float(dt),
+                   charge=1.0, q=charge)
+        return out
+
+    def shape(self, i, dt, tau, order, gain=1.0, noise=None, noise_rms=0.0, out=None, stream=None):
+        """CR-(RC)^n front-end shaping of Eq. 1 currents (device tensors)."""
+        return B.wt_shape(self.ctx, i, dt, tau, order, gain, noise, noise_rms, out, stream)
+
     def tuning(self):
         """Launch shapes of the FP32 path (nb, lb, nch, nepi), set by the autotuner."""
         return B.wt_get_tuning(self.ctx)
