@@ -51,10 +51,13 @@ namespace wt {
 struct Fast32 {
     GridDev g{};
     int n_cols = 0;
-    int rxy = 0, rz = 0;           // register-FFT elements per lane (lateral, z)
+    int rxy = 0, rz = 0;           // register-FFT elements per lane (lateral, z); lanes per line = N / R
     DBuf<float> tw_y, tw_x, tw_z;
     DBuf<float> phx, phy, zsh;     // complex tables
     void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);
+    // register-FFT shapes: the elements per lane that give a power-of-two lane count 4..32
+    static std::vector<int> radix_options(int N);
+    void set_radix(int r_xy, int r_z);
     // rho scratch: nb * Nz * (Nx/2+1) * Ny complex; R scratch: nb * 3 * Nz * Nx * Ny real.
     size_t rho_elems(int nb) const { return (size_t)nb * g.Nz * (g.Nx / 2 + 1) * g.Ny * 2; }
     size_t r_elems(int nb) const { return (size_t)nb * 3 * g.Nz * g.Nx * g.Ny; }

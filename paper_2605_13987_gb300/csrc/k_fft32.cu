@@ -324,9 +324,7 @@ static size_t plane_smem(const GridDev& g) {
     (void)W;
     return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>);
 }
-static size_t zpass_smem(const GridDev& g, int lb) {
-    int W, R;
-    warp_fft_shape(g.Nz, &W, &R);
+static size_t zpass_smem(const GridDev& g, int lb, int R) {
     const size_t S = (size_t)zpass_pitch(g.Nz, R);
     return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz) * sizeof(C2<float>);
 }
@@ -373,15 +371,34 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
     f32_twiddle_kernel<<<(g.Nx + 127) / 128, 128, 0, s>>>(tw_x.p, g.Nx);
     f32_twiddle_kernel<<<(g.Nz + 127) / 128, 128, 0, s>>>(tw_z.p, g.Nz);
     WT_LAUNCH("fast32 tables");
-    const size_t sp = plane_smem(g), sz = zpass_smem(g, 64), sd = deposit_smem(g, n_cols);
-    if (sp > 227 * 1024 || sz > 227 * 1024 || sd > 227 * 1024)
-        fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
-    switch (rxy) {
+    const size_t sd = deposit_smem(g, n_cols);
+    if (sd > 227 * 1024) fail(WT_ERR_UNSUPPORTED, "too many columns for the FP32 deposit kernel");
+    allow_dyn_smem(f32_deposit_kernel, sd);
+    set_radix(rxy, rz);
+    WT_CUDA(cudaStreamSynchronize(s));
+}
+
+std::vector<int> Fast32::radix_options(int N) {
+    std::vector<int> out;
+    for (int w = 32; w >= 4; w >>= 1)
+        if (N % w == 0 && supported_r(N / w)) out.push_back(N / w);
+    return out;
+}
+
+void Fast32::set_radix(int r_xy, int r_z) {
+    if (g.Nx % r_xy || g.Nz % r_z || !supported_r(r_xy) || !supported_r(r_z))
+        fail(WT_ERR_ARG, "register-FFT length does not divide the grid");
+    int w = g.Nx / r_xy, wz = g.Nz / r_z;
+    if ((w & (w - 1)) || w > 32 || (wz & (wz - 1)) || wz > 32)
+        fail(WT_ERR_ARG, "lanes per FFT line must be a power of two up to 32");
+    const size_t sp = plane_smem(g), sz = zpass_smem(g, 64, r_z);
+    if (sp > 227 * 1024 || sz > 227 * 1024) fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
+    switch (r_xy) {
 #define WT_CASE(R) case R: { allow_dyn_smem(f32_plane_kernel<R, R>, sp); break; }
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }
-    switch (rz) {
+    switch (r_z) {
 #define WT_CASE(R) case R: { \
         allow_dyn_smem(f32_zpass_kernel<R, 16>, sz); \
         allow_dyn_smem(f32_zpass_kernel<R, 32>, sz); \
@@ -389,8 +406,8 @@ void Fast32::init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE
     }
-    allow_dyn_smem(f32_deposit_kernel, sd);
-    WT_CUDA(cudaStreamSynchronize(s));
+    rxy = r_xy;
+    rz = r_z;
 }
 
 void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
@@ -416,9 +433,9 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
     switch (rz) {
 #define WT_CASE(RR) case RR: \
-        if (lb == 16) f32_zpass_kernel<RR, 16><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else if (lb == 32) f32_zpass_kernel<RR, 32><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else f32_zpass_kernel<RR, 64><<<gz, 256, zpass_smem(g, lb), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        if (lb == 16) f32_zpass_kernel<RR, 16><<<gz, 256, zpass_smem(g, lb, RR), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else if (lb == 32) f32_zpass_kernel<RR, 32><<<gz, 256, zpass_smem(g, lb, RR), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else f32_zpass_kernel<RR, 64><<<gz, 256, zpass_smem(g, lb, RR), s>>>(g, R, tz, zz, out, out_sb, out_sc); \
         break;
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE

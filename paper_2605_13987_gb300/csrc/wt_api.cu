@@ -1270,10 +1270,11 @@ struct BatchEntry {
     unsigned long long uid, version;
     const void* H;
     const void *E, *Zc, *rho, *R, *Ub, *W;
-    int nb, lb;
+    int nb, lb, rxy, rz;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
-               rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb;
+               rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb && rxy == o.rxy &&
+               rz == o.rz;
     }
 };
 
@@ -1294,7 +1295,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi;
+    int nb, lb, nch, nepi, rxy, rz;
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1364,10 +1365,22 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 1e30, 1e30};
     c->tune_nb = 1;
+    c->tune_lb = 32;
     alloc_fast32(c);
     column_ztransform<float>(s, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
+    // register-FFT shapes (lanes per line) of the plane and z passes
+    {
+        double best_ms = 1e30;
+        for (int rxy : Fast32::radix_options(g.Nx))
+            for (int rz : Fast32::radix_options(g.Nz)) {
+                c->sp32.set_radix(rxy, rz);
+                const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
+                if (ms < best_ms) { best_ms = ms; best.rxy = rxy; best.rz = rz; }
+            }
+        c->sp32.set_radix(best.rxy, best.rz);
+    }
     for (int nb : {1, 2, 4}) {
         if (nb > 1 && nb > c->rank) break;
         c->tune_nb = nb;
@@ -1400,13 +1413,14 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
+    c->sp32.set_radix(t.rxy, t.rz);
     c->tuned = true;
     alloc_fast32(c);
 }
 
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
-                      c->tune_nb, c->tune_lb};
+                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1473,6 +1487,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
+        c->sp32.set_radix(t.rxy, t.rz);
         c->tuned = true;
         alloc_fast32(c);
     }
@@ -1676,14 +1691,16 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
     });
 }
 
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape4) {
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape6) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_get_tuning", [&] {
-        if (!shape4) fail(WT_ERR_ARG, "NULL output");
-        shape4[0] = ctx->tune_nb;
-        shape4[1] = ctx->tune_lb;
-        shape4[2] = ctx->tune_nch;
-        shape4[3] = ctx->tune_nepi;
+        if (!shape6) fail(WT_ERR_ARG, "NULL output");
+        shape6[0] = ctx->tune_nb;
+        shape6[1] = ctx->tune_lb;
+        shape6[2] = ctx->tune_nch;
+        shape6[3] = ctx->tune_nepi;
+        shape6[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
+        shape6[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
     });
 }
 
