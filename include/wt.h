@@ -266,12 +266,13 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
 /* Launch shapes the FP32 path of this context uses (set by the autotuner;
- * defaults 1, 32, 256, 8 and the widest register FFTs): shape6[0] charge
- * vectors per spectral launch, shape6[1] (x, y) lines per z-pass block,
- * shape6[2] time samples per expansion accumulator chunk, shape6[3]
- * expansion epilogue warps, shape6[4] and shape6[5] elements per lane of
- * the lateral and z register FFTs (0 before the first extension). */
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape6);
+ * defaults 1, 32, 256, 8, the widest register FFTs, 0): shape7[0] charge
+ * vectors per spectral launch, shape7[1] (x, y) lines per z-pass block,
+ * shape7[2] time samples per expansion accumulator chunk, shape7[3]
+ * expansion epilogue warps, shape7[4] and shape7[5] elements per lane of
+ * the lateral and z register FFTs (0 before the first extension),
+ * shape7[6] 1 if H is stored with an L2 evict-first policy. */
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape7);
 
 /* Static field of the electrodes held at fixed potentials (the paper's
  * static drift field, Fig. 2; the sigma -> infinity limit of the

@@ -143,13 +143,15 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
         // ends with Y[k + RY bitrev(gl)] and writes it back at row position gl + Wy k (consecutive
         // lanes, no bank conflicts): Y[y] sits at column sigma(y) = bitrev(y / RY) + Wy (y % RY).
         const int W = Wy, G = 32 / W, grp = lane / W, gl = lane % W;
+        LaneTw<RY> lt;
+        lane_twiddles<RY>(ty, gl, W, true, lt);
         for (int base = warp * G; base < nxh; base += 8 * G) {
             const int mx = base + grp;
             const bool act = mx < nxh;
             C2<float> v[RY];
 #pragma unroll
             for (int j = 0; j < RY; ++j) v[j] = act ? P[mx * ldp + gl + W * j] : C2<float>{0.f, 0.f};
-            warp_fft_dit<RY>(v, gl, W, ty, ny);
+            warp_fft_dit_t<RY>(v, gl, W, lt, ty);
             if (act)
 #pragma unroll
                 for (int k = 0; k < RY; ++k) P[mx * ldp + gl + W * k] = v[k];
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
         const int W = nx / RX, G = 32 / W, grp = lane / W, gl = lane % W;
         const int k2 = warp_fft_k2(gl, W);
         const int nxq = nx / 2;
+        LaneTw<RX> lt;
+        lane_twiddles<RX>(tx, gl, W, true, lt);
         for (int base = warp * G; base < ny / 2; base += 8 * G) {
             const int pp = base + grp;
             const bool act = pp < ny / 2;
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
                 }
                 v[j] = z;
             }
-            warp_fft_dit<RX>(v, gl, W, tx, nx);
+            warp_fft_dit_t<RX>(v, gl, W, lt, tx);
             // the pair's own two columns of P (read only by this lane group, now consumed) hold the
             // two output lines: x -> float (x & 1) of P[x / 2][y]
             __syncwarp();
@@ -267,6 +271,8 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
     const int W = nz / RZ, G = 32 / W, grp = lane / W, gl = lane % W;
     const int k2 = warp_fft_k2(gl, W);
     const bool sine = comp == 2;
+    LaneTw<RZ> lt;
+    lane_twiddles<RZ>(tw, gl, W, false, lt);
     float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
     for (int base = warp * G; base < LB / 2; base += 8 * G) {
         const int f = base + grp;                 // lines 2f, 2f+1 of this block
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
             const C2<float> p = sine ? cr : cm, q = sine ? cm : cr;     // Y = (p - i q) e^{i pi m / 2N}
             v[j1] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
         }
-        warp_fft<RZ>(v, gl, W, tw, nz);
+        warp_fft_t<RZ>(v, gl, W, lt, tw);
         __syncwarp();                             // every lane of the group has read its inputs
         if (act)
 #pragma unroll

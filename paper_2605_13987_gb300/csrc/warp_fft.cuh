@@ -118,6 +118,69 @@ __device__ __forceinline__ void warp_fft_dit(C2<float> (&v)[R], int gl, int W, c
     }
 }
 
+// Per-lane twiddles of a W x R warp FFT, computed once per kernel: the
+// cross-lane stage factors (stage s pairs lanes gl, gl ^ h with h = W >> (s+1);
+// bottom lanes multiply b - a by w_{2h}^{gl mod h}, top lanes keep a + b, written
+// as t = b + sg a, v = t st with st = 1 and sg = +1 on top lanes, sg = -1 below)
+// and the twiddles between the register and cross-lane parts.
+template <int R>
+struct LaneTw {
+    C2<float> st[5];
+    C2<float> in[R];
+};
+
+// dit: inter twiddles w_N^{gl k} (decimation in time); else w_N^{j k2} (in frequency).
+template <int R>
+__device__ __forceinline__ void lane_twiddles(const C2<float>* __restrict__ tw, int gl, int W, bool dit,
+                                              LaneTw<R>& t) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = W >> (s + 1);
+        t.st[s] = {1.f, 0.f};
+        if (h >= 1 && (gl & h)) t.st[s] = tw[(gl & (h - 1)) * R * (W / (2 * h))];
+    }
+    const int lw = 31 - __clz(W);
+    const int k2 = lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) t.in[k] = tw[(dit ? gl : k2) * k];
+}
+
+// Cross-lane stages with precomputed factors (h = W/2 .. 1).
+template <int R>
+__device__ __forceinline__ void lane_stages(C2<float> (&v)[R], int gl, int W, const LaneTw<R>& t) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = W >> (s + 1);
+        if (h < 1) break;
+        const C2<float> w = t.st[s];
+        const float sg = (gl & h) ? -1.f : 1.f;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const C2<float> a = v[j];
+            const C2<float> b = {__shfl_xor_sync(0xffffffffu, a.x, h), __shfl_xor_sync(0xffffffffu, a.y, h)};
+            v[j] = cmul(C2<float>{fmaf(sg, a.x, b.x), fmaf(sg, a.y, b.y)}, w);
+        }
+    }
+}
+
+// warp_fft / warp_fft_dit with per-lane twiddles (same input and output orders).
+template <int R>
+__device__ __forceinline__ void warp_fft_t(C2<float> (&v)[R], int gl, int W, const LaneTw<R>& t,
+                                           const C2<float>* __restrict__ tw) {
+    lane_stages<R>(v, gl, W, t);
+#pragma unroll
+    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], t.in[j]);
+    reg_dft<R>(v, tw, W);
+}
+template <int R>
+__device__ __forceinline__ void warp_fft_dit_t(C2<float> (&v)[R], int gl, int W, const LaneTw<R>& t,
+                                               const C2<float>* __restrict__ tw) {
+    reg_dft<R>(v, tw, W);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t.in[k]);
+    lane_stages<R>(v, gl, W, t);
+}
+
 __device__ __forceinline__ int warp_fft_k2(int gl, int W) {
     const int lw = 31 - __clz(W);
     return lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;

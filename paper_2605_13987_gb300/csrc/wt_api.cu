@@ -141,7 +141,7 @@ struct wt_ctx {
     int last_launches = 0;
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
-    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8;
+    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_ef = 0;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -747,7 +747,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
             float* o = out + (size_t)t0 * 3 * npts;
             if (tc) {
                 ExpandJob jb{c->E32.p, rp, r, W32 + (size_t)t0 * rp, n, npts, o};
-                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
+                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_ef);
             } else {
                 expand_simt(s, c->E32.p, rp, W32 + (size_t)t0 * rp, n, rp, npts, o);
             }
@@ -764,7 +764,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
     }
     if (tc) {
         ExpandJob jb{c->E32.p, rp, r, W32, nt, npts, out};
-        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
+        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_ef);
     } else {
         expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
     }
@@ -1280,7 +1280,7 @@ struct BatchEntry {
 
 struct BatchPlan {
     std::vector<BatchEntry> ents;
-    int nch = 256, nepi = 8;
+    int nch = 256, nepi = 8, ef = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long last_use = 0;
@@ -1295,7 +1295,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi, rxy, rz;
+    int nb, lb, nch, nepi, ef, rxy, rz;
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1365,7 +1365,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, 0, c->sp32.rxy, c->sp32.rz, 1e30, 1e30};
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
@@ -1395,12 +1395,13 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     spectral_all(c, s);
-    for (int nepi : {8, 16})
-        for (int nch : {64, 128, 256}) {
-            ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
-            const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi); });
-            if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; }
-        }
+    for (int ef : {0, 1})
+        for (int nepi : {8, 16})
+            for (int nch : {64, 128, 256}) {
+                ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
+                const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi, ef); });
+                if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; best.ef = ef; }
+            }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out while tuning");
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[tune_key(c)] = best;
@@ -1413,6 +1414,7 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
+    c->tune_ef = t.ef;
     c->sp32.set_radix(t.rxy, t.rz);
     c->tuned = true;
     alloc_fast32(c);
@@ -1443,7 +1445,7 @@ void capture_batch(BatchPlan& P, wt_ctx* const* ctxs, int n, float* const* H) {
         }
         const int mj = expand_tc_max_jobs();
         for (int j0 = 0; j0 < n; j0 += mj)
-            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi);
+            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi, P.ef);
     } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
@@ -1487,31 +1489,36 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
+        c->tune_ef = t.ef;
         c->sp32.set_radix(t.rxy, t.rz);
         c->tuned = true;
         alloc_fast32(c);
     }
     // one (time chunk, epilogue warps) pair for the shared expansion launch: the one most of the
     // grid points asked for
-    std::map<std::pair<int, int>, double> votes;
+    std::map<std::tuple<int, int, int>, double> votes;
     for (int i = 0; i < n; ++i) {
         const wt_grid& g = ctxs[i]->grid;
-        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi}] += (double)g.Nx * g.Ny * g.Nz;
+        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi, ctxs[i]->tune_ef}] += (double)g.Nx * g.Ny * g.Nz;
     }
-    int nch = 256, nepi = 8;
+    int nch = 256, nepi = 8, ef = 0;
     double top = -1;
     for (auto& v : votes)
-        if (v.second > top) { top = v.second; nch = v.first.first; nepi = v.first.second; }
+        if (v.second > top) {
+            top = v.second;
+            std::tie(nch, nepi, ef) = v.first;
+        }
     std::vector<BatchEntry> want;
     for (int i = 0; i < n; ++i) want.push_back(entry_of(ctxs[i], H[i]));
     BatchPlan* plan = nullptr;
     for (auto& p : c0->plans)
-        if (p->nch == nch && p->nepi == nepi && p->ents == want) plan = p.get();
+        if (p->nch == nch && p->nepi == nepi && p->ef == ef && p->ents == want) plan = p.get();
     if (!plan) {
         auto P = std::make_unique<BatchPlan>();
         P->ents = want;
         P->nch = nch;
         P->nepi = nepi;
+        P->ef = ef;
         capture_batch(*P, ctxs, n, reinterpret_cast<float* const*>(H));
         if (c0->plans.size() >= 4) {         // keep the four most recently used graphs
             auto old = std::min_element(c0->plans.begin(), c0->plans.end(),
@@ -1691,16 +1698,17 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
     });
 }
 
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape6) {
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape7) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_get_tuning", [&] {
-        if (!shape6) fail(WT_ERR_ARG, "NULL output");
-        shape6[0] = ctx->tune_nb;
-        shape6[1] = ctx->tune_lb;
-        shape6[2] = ctx->tune_nch;
-        shape6[3] = ctx->tune_nepi;
-        shape6[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
-        shape6[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
+        if (!shape7) fail(WT_ERR_ARG, "NULL output");
+        shape7[0] = ctx->tune_nb;
+        shape7[1] = ctx->tune_lb;
+        shape7[2] = ctx->tune_nch;
+        shape7[3] = ctx->tune_nepi;
+        shape7[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
+        shape7[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
+        shape7[6] = ctx->tune_ef;
     });
 }
 
