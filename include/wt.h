@@ -271,7 +271,7 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
  * shape7[2] time samples per expansion accumulator chunk, shape7[3]
  * expansion epilogue warps, shape7[4] and shape7[5] elements per lane of
  * the lateral and z register FFTs (0 before the first extension),
- * shape7[6] 1 if H is stored with an L2 evict-first policy. */
+ * shape7[6] 1 if the x transforms store from registers (else staged). */
 wt_status wt_get_tuning(wt_ctx* ctx, int* shape7);
 
 /* Static field of the electrodes held at fixed potentials (the paper's

@@ -302,7 +302,7 @@ def wt_get_tuning(ctx):
     lib = load_library()
     out = (C.c_int * 7)()
     _check(lib.wt_get_tuning(ctx, out), ctx)
-    return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], evict_first=out[6])
+    return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6])
 
 
 def wt_get_charges(ctx, n_t, n_sources):

@@ -160,12 +160,6 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
 
 constexpr int RAW_BYTES = KR * BM * 4;   // one raw FP32 slice [32 basis][128 points]
 
-__device__ __forceinline__ void st_stream_v4(float* p, float a, float b, float c, float d, unsigned long long pol) {
-    asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a),
-                 "f"(b), "f"(c), "f"(d), "l"(pol)
-                 : "memory");
-}
-
 // 4 x 4 transposes within lane quads: on entry lane 4g + i holds v[4b + j] =
 // D[point 4g + i][time 4b + j]; on return v[4b + j] = D[point 4g + j][time 4b + i],
 // so that each lane can store 4 consecutive points of one time sample.
@@ -229,8 +223,7 @@ __device__ __forceinline__ void load_coeffs(const float* __restrict__ W, int nt,
 
 template <int NEPI>
 __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
-    expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int evict_first,
-                     int* __restrict__ d_err) {
+    expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // align the tile region to 1024 bytes
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -386,10 +379,6 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         // ---------------- epilogue: TMEM -> H; warps 2..9, quadrant warp & 3, column slice (warp - 2) / 4
         const int q = warp & 3;
         const int slice = (warp - 2) >> 2;
-        // H is written once and never read here: optionally stream it past L1 with an
-        // evict-first L2 policy so that it does not displace the basis fields
-        unsigned long long policy = 0;
-        if (evict_first) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
         constexpr int NSL = NEPI / 4;
         int g = 0, cur = job0;
         bool ok = true;
@@ -417,14 +406,9 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                     if (in) {
 #pragma unroll
                         for (int bb = 0; bb < 8; ++bb)
-                            if (t0 + 4 * bb < nt) {
-                                float* dst = hp + (size_t)(t0 + 4 * bb) * 3 * npts;
-                                if (evict_first)
-                                    st_stream_v4(dst, v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3], policy);
-                                else
-                                    *reinterpret_cast<float4*>(dst) =
-                                        make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
-                            }
+                            if (t0 + 4 * bb < nt)
+                                *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
+                                    make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
                     }
                 }
                 tc_fence_before();
@@ -476,8 +460,7 @@ int expand_tc_max_jobs() { return tc::MAX_JOBS; }
 
 // jobs[j]: E [3][32][npts] FP32, W [nt][32] FP32, H [nt][3][npts] FP32; all
 // expansions in one persistent launch of at most `max_ctas` CTAs (0: one per SM).
-void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err, int nepi,
-                    int evict_first) {
+void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err, int nepi) {
     if (n_jobs < 1) return;
     if (nch != 64 && nch != 128 && nch != 256) fail(WT_ERR_ARG, "expansion time chunk must be 64, 128 or 256");
     if (n_jobs > tc::MAX_JOBS) fail(WT_ERR_UNSUPPORTED, "too many expansion jobs for one launch");
@@ -516,9 +499,8 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     else allow_dyn_smem(tc::expand_tc_kernel<16>, sh);
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
-    const int ef = evict_first ? 1 : 0;
-    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, ef, d_err);
-    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, ef, d_err);
+    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, d_err);
+    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, d_err);
     WT_LAUNCH("expand_tc");
 }
 

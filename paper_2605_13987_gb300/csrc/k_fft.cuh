@@ -52,6 +52,7 @@ struct Fast32 {
     GridDev g{};
     int n_cols = 0;
     int rxy = 0, rz = 0;           // register-FFT elements per lane (lateral, z); lanes per line = N / R
+    bool xdirect = false;          // x transforms store from registers (else staged for coalescing)
     DBuf<float> tw_y, tw_x, tw_z;
     DBuf<float> phx, phy, zsh;     // complex tables
     void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);

@@ -1,0 +1,37 @@
+// Shared pieces of the FP32 spectral kernels (plane and z passes live in
+// their own translation units so that their many register-FFT instances
+// compile in parallel).
+#pragma once
+#include "k_fft.cuh"
+#include "fft_core.cuh"
+#include "warp_fft.cuh"
+
+namespace wt {
+
+// Register-FFT lengths compiled in: elements per lane R = N / W.
+#define WT_FOR_EACH_R(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(24)
+
+inline int plane_ldp(const GridDev& g) { return (g.Ny + 1) | 1; }     // odd row pitch (complex units)
+inline size_t plane_smem(const GridDev& g) {
+    const int nxh = g.Nx / 2 + 1;
+    return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>);
+}
+// Row pitch of a staged z line pair: room for the skewed inputs and the skewed outputs.
+__host__ __device__ __forceinline__ int zpass_pitch(int nz, int R) {
+    const int a = (nz - 1) + (nz - 1) / R + 1, b = (nz - 1) + ((nz - 1) >> 4) + 1;
+    return (a > b ? a : b) | 1;
+}
+inline size_t zpass_smem(const GridDev& g, int lb, int R) {
+    const size_t S = (size_t)zpass_pitch(g.Nz, R);
+    return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz) * sizeof(C2<float>);
+}
+
+// Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.
+void plane_allow(int r, size_t smem);
+void plane_launch(int r, bool xdirect, dim3 grid, cudaStream_t s, const GridDev& g, const C2<float>* rho,
+                  const C2<float>* twy, const C2<float>* twx, float* R, int mode);
+void zpass_allow(int r, size_t smem);
+void zpass_launch(int r, int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
+                  const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc);
+
+}  // namespace wt

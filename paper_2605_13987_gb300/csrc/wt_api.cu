@@ -141,7 +141,7 @@ struct wt_ctx {
     int last_launches = 0;
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
-    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_ef = 0;
+    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -747,7 +747,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
             float* o = out + (size_t)t0 * 3 * npts;
             if (tc) {
                 ExpandJob jb{c->E32.p, rp, r, W32 + (size_t)t0 * rp, n, npts, o};
-                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_ef);
+                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
             } else {
                 expand_simt(s, c->E32.p, rp, W32 + (size_t)t0 * rp, n, rp, npts, o);
             }
@@ -764,7 +764,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
     }
     if (tc) {
         ExpandJob jb{c->E32.p, rp, r, W32, nt, npts, out};
-        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_ef);
+        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
     } else {
         expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
     }
@@ -1270,17 +1270,17 @@ struct BatchEntry {
     unsigned long long uid, version;
     const void* H;
     const void *E, *Zc, *rho, *R, *Ub, *W;
-    int nb, lb, rxy, rz;
+    int nb, lb, rxy, rz, xd;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
                rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb && rxy == o.rxy &&
-               rz == o.rz;
+               rz == o.rz && xd == o.xd;
     }
 };
 
 struct BatchPlan {
     std::vector<BatchEntry> ents;
-    int nch = 256, nepi = 8, ef = 0;
+    int nch = 256, nepi = 8;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long last_use = 0;
@@ -1295,7 +1295,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi, ef, rxy, rz;
+    int nb, lb, nch, nepi, rxy, rz, xd;
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1365,7 +1365,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, 0, c->sp32.rxy, c->sp32.rz, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 1e30, 1e30};
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
@@ -1373,13 +1373,16 @@ TuneResult autotune(wt_ctx* c, float* H) {
     // register-FFT shapes (lanes per line) of the plane and z passes
     {
         double best_ms = 1e30;
-        for (int rxy : Fast32::radix_options(g.Nx))
-            for (int rz : Fast32::radix_options(g.Nz)) {
-                c->sp32.set_radix(rxy, rz);
-                const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
-                if (ms < best_ms) { best_ms = ms; best.rxy = rxy; best.rz = rz; }
-            }
+        for (int xd : {0, 1})
+            for (int rxy : Fast32::radix_options(g.Nx))
+                for (int rz : Fast32::radix_options(g.Nz)) {
+                    c->sp32.set_radix(rxy, rz);
+                    c->sp32.xdirect = xd;
+                    const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
+                    if (ms < best_ms) { best_ms = ms; best.rxy = rxy; best.rz = rz; best.xd = xd; }
+                }
         c->sp32.set_radix(best.rxy, best.rz);
+        c->sp32.xdirect = best.xd;
     }
     for (int nb : {1, 2, 4}) {
         if (nb > 1 && nb > c->rank) break;
@@ -1395,13 +1398,12 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     spectral_all(c, s);
-    for (int ef : {0, 1})
-        for (int nepi : {8, 16})
-            for (int nch : {64, 128, 256}) {
-                ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
-                const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi, ef); });
-                if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; best.ef = ef; }
-            }
+    for (int nepi : {8, 16})
+        for (int nch : {64, 128, 256}) {
+            ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
+            const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi); });
+            if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; }
+        }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out while tuning");
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[tune_key(c)] = best;
@@ -1414,15 +1416,15 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
-    c->tune_ef = t.ef;
     c->sp32.set_radix(t.rxy, t.rz);
+    c->sp32.xdirect = t.xd;
     c->tuned = true;
     alloc_fast32(c);
 }
 
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
-                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz};
+                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1445,7 +1447,7 @@ void capture_batch(BatchPlan& P, wt_ctx* const* ctxs, int n, float* const* H) {
         }
         const int mj = expand_tc_max_jobs();
         for (int j0 = 0; j0 < n; j0 += mj)
-            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi, P.ef);
+            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi);
     } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
@@ -1489,36 +1491,36 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
-        c->tune_ef = t.ef;
         c->sp32.set_radix(t.rxy, t.rz);
+        c->sp32.xdirect = t.xd;
         c->tuned = true;
         alloc_fast32(c);
     }
     // one (time chunk, epilogue warps) pair for the shared expansion launch: the one most of the
     // grid points asked for
-    std::map<std::tuple<int, int, int>, double> votes;
+    std::map<std::pair<int, int>, double> votes;
     for (int i = 0; i < n; ++i) {
         const wt_grid& g = ctxs[i]->grid;
-        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi, ctxs[i]->tune_ef}] += (double)g.Nx * g.Ny * g.Nz;
+        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi}] += (double)g.Nx * g.Ny * g.Nz;
     }
-    int nch = 256, nepi = 8, ef = 0;
+    int nch = 256, nepi = 8;
     double top = -1;
     for (auto& v : votes)
         if (v.second > top) {
             top = v.second;
-            std::tie(nch, nepi, ef) = v.first;
+            nch = v.first.first;
+            nepi = v.first.second;
         }
     std::vector<BatchEntry> want;
     for (int i = 0; i < n; ++i) want.push_back(entry_of(ctxs[i], H[i]));
     BatchPlan* plan = nullptr;
     for (auto& p : c0->plans)
-        if (p->nch == nch && p->nepi == nepi && p->ef == ef && p->ents == want) plan = p.get();
+        if (p->nch == nch && p->nepi == nepi && p->ents == want) plan = p.get();
     if (!plan) {
         auto P = std::make_unique<BatchPlan>();
         P->ents = want;
         P->nch = nch;
         P->nepi = nepi;
-        P->ef = ef;
         capture_batch(*P, ctxs, n, reinterpret_cast<float* const*>(H));
         if (c0->plans.size() >= 4) {         // keep the four most recently used graphs
             auto old = std::min_element(c0->plans.begin(), c0->plans.end(),
@@ -1708,7 +1710,7 @@ wt_status wt_get_tuning(wt_ctx* ctx, int* shape7) {
         shape7[3] = ctx->tune_nepi;
         shape7[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
         shape7[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
-        shape7[6] = ctx->tune_ef;
+        shape7[6] = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
     });
 }
 

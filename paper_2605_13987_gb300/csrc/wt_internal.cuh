@@ -153,8 +153,8 @@ void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W,
                int* d_err);
 // Several expansions in one persistent launch (at most max_ctas CTAs, 0 = one
 // per SM; nch = time samples per accumulator chunk: 64, 128 or 256; nepi =
-// epilogue warps: 8 or 16; evict_first: H stores with an L2 evict-first policy).
+// epilogue warps: 8 or 16).
 void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err,
-                    int nepi = 8, int evict_first = 0);
+                    int nepi = 8);
 
 }  // namespace wt
