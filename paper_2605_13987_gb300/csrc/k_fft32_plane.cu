@@ -35,48 +35,43 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
     const float pref = (float)g.pref;
     const C2<float>* rp = rho + ((size_t)b * nz + mz) * nxh * ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // warps over m_x rows, lanes over m_y (no index division); FP32 fast division: the path's
-    // tolerance is far above its 2-ulp error
-    for (int mx = warp; mx < nxh; mx += 8) {
-        const float kx = ckx * mx;
-        const float fold = mx ? 2.f : 1.f;                        // x half-spectrum fold
-        const C2<float>* rrow = rp + (size_t)mx * ny;
-        C2<float>* prow = P + (size_t)mx * ldp;
-#pragma unroll 4
-        for (int my = lane; my < ny; my += 32) {
-            const int mys = my < ny / 2 ? my : my - ny;
-            C2<float> v = {0.f, 0.f};
-            if (mx != nx / 2 && my != ny / 2) {
-                const float ky = cky * mys;
-                const float kp2 = kx * kx + ky * ky;
-                const float k2 = kp2 + kz * kz;
-                if (k2 > 0.f) {
-                    const C2<float> r = rrow[my];
-                    float gk = __fdividef(pref * fold, k2);
-                    if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + __fdividef(2.f * kp2, k2);
-                    // the z pass's cosine series carries the factor 2 of the +-k_z pair itself
-                    if (comp == 0) { const float f = kx * gk; v = {r.y * f, -r.x * f}; }
-                    else if (comp == 1) { const float f = ky * gk; v = {r.y * f, -r.x * f}; }
-                    else { const float f = 2.f * kz * gk; v = {r.x * f, r.y * f}; }
-                }
-            }
-            prow[my] = v;
-        }
-    }
-    __syncthreads();
     const int Wy = ny / RY;
-    {   // y: nxh lines of length ny (decimation in time: lanes read consecutive elements).  Lane gl
-        // ends with Y[k + RY bitrev(gl)] and writes it back at row position gl + Wy k (consecutive
-        // lanes, no bank conflicts): Y[y] sits at column sigma(y) = bitrev(y / RY) + Wy (y % RY).
+    __syncthreads();                                           // twiddle tables
+    {   // multiplier and y transform, row by row from global memory: nxh lines of length ny
+        // (decimation in time: lanes read consecutive elements).  Lane gl ends with
+        // Y[k + RY bitrev(gl)] and writes it at row position gl + Wy k (consecutive lanes, no
+        // bank conflicts): Y[y] sits at column sigma(y) = bitrev(y / RY) + Wy (y % RY).
+        // FP32 fast division: the path's tolerance is far above its 2-ulp error.
         const int W = Wy, G = 32 / W, grp = lane / W, gl = lane % W;
         LaneTw<RY> lt;
         lane_twiddles<RY>(ty, gl, W, true, lt);
         for (int base = warp * G; base < nxh; base += 8 * G) {
             const int mx = base + grp;
             const bool act = mx < nxh;
+            const bool live = act && mx != nx / 2;                 // the x Nyquist row stays zero
+            const float kx = ckx * mx;
+            const float fold = mx ? 2.f : 1.f;                     // x half-spectrum fold
+            const C2<float>* rrow = rp + (size_t)(live ? mx : 0) * ny;
             C2<float> v[RY];
 #pragma unroll
-            for (int j = 0; j < RY; ++j) v[j] = act ? P[mx * ldp + gl + W * j] : C2<float>{0.f, 0.f};
+            for (int j = 0; j < RY; ++j) {
+                const int my = gl + W * j;
+                const int mys = my < ny / 2 ? my : my - ny;
+                const float ky = cky * mys;
+                const float kp2 = kx * kx + ky * ky;
+                const float k2 = kp2 + kz * kz;
+                C2<float> e = {0.f, 0.f};
+                if (live && my != ny / 2 && k2 > 0.f) {
+                    const C2<float> r = rrow[my];
+                    float gk = __fdividef(pref * fold, k2);
+                    if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + __fdividef(2.f * kp2, k2);
+                    // the z pass's cosine series carries the factor 2 of the +-k_z pair itself
+                    if (comp == 0) { const float f = kx * gk; e = {r.y * f, -r.x * f}; }
+                    else if (comp == 1) { const float f = ky * gk; e = {r.y * f, -r.x * f}; }
+                    else { const float f = 2.f * kz * gk; e = {r.x * f, r.y * f}; }
+                }
+                v[j] = e;
+            }
             warp_fft_dit_t<RY>(v, gl, W, lt, ty);
             if (act)
 #pragma unroll
