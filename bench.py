@@ -42,6 +42,8 @@ WORKLOADS = {
              "(profiling case: H = 1.6 GB > L2)",
     "prof": "prof: c2's geometry and grid (128x128x256, 18 columns) with 16 time samples "
             "(profiling case: the spectral kernels at c2 sizes, about 2.5 GB on the device)",
+    "c4": "c4: 3x3 pixel cell at grid 96x96x192, radius 5 um, 256 time samples, 1e4 straight tracks of 100 "
+          "steps; the Eq. 1 loss and its gradient (resistivities, radius, pitch)",
     "c3": "c3: 64 single cells, pitch 40-110 um, thickness 300-500 um, radius 4-10 um, grids 64^2x128 to "
           "128^2x256 (uneven), 256 time samples each; batched in waves through an H arena",
 }
@@ -283,6 +285,65 @@ def run_batch(args):
     return 0
 
 
+def run_adjoint(args):
+    """c4: L = mean i^2 of Eq. 1 currents over 1e4 tracks and its gradient with
+    respect to the readout/bias resistivity scales, radius and lateral scale
+    (wt_eq1_loss_grad: four tangent sweeps of the FP32 extension and Eq. 1).
+    A step = one loss-and-gradient evaluation; the loss alone is timed too."""
+    import numpy as np
+    import torch
+    import paper_2605_13987_gb300 as P
+    import workloads as W
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    P.load_library()
+    w = W.workload("c4")
+    tr = w.tracks
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=f"cuda:{local}")
+    t = dict(n_tracks=tr.n_tracks, n_steps=tr.n_steps, n_out=tr.n_out, dt=tr.dt, charge=1.0,
+             x=dev(tr.x), y=dev(tr.y), z=dev(tr.z), vx=dev(tr.vx), vy=dev(tr.vy), vz=dev(tr.vz), q=dev(tr.charge))
+    t0 = time.perf_counter()
+    sen = P.Sensor(w.grid, w.columns, device=local)
+    sen.fit()
+    sen.relax(w.times)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    H = sen.extend("fp32")           # tunes the launch shapes
+    torch.cuda.synchronize()
+    del H
+    for _ in range(args.warmup):
+        sen.loss_grad(t)
+    per = []
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+        barrier(world)
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            L, g = sen.loss_grad(t)
+            torch.cuda.synchronize()
+            per.append(time.perf_counter() - a)
+        barrier(world)
+        a = time.perf_counter()
+        L32 = sen.loss(t, "fp32")
+        torch.cuda.synchronize()
+        loss_s = time.perf_counter() - a
+    s = max_over_ranks(statistics.median(per), world)
+    if rank == 0:
+        line = {"metric": "Eq. 1 loss + 4-parameter gradient evaluations/sec", "value": world / s,
+                "unit": "evaluations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["c4"], "tracks": tr.n_tracks, "steps_per_track": tr.n_steps,
+                           "grid_points": w.grid.Nx * w.grid.Ny * w.grid.Nz, "time_samples": len(w.times)},
+                "loss": L, "gradient": list(map(float, g)), "loss_only_ms": 1e3 * loss_s,
+                "grad_trunc_rel": sen.info()["grad_trunc_rel"], "clocks": clk.summary(local), "setup_s": setup,
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    sen.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -463,6 +524,8 @@ def main():
         return run_reference(args)
     if args.workload == "c3":
         return run_batch(args)
+    if args.workload == "c4":
+        return run_adjoint(args)
     return run_ours(args)
 
 

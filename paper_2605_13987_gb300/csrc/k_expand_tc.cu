@@ -143,6 +143,17 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
+// Issue a 32-column TMEM load without waiting (tcgen05.wait::ld before the values are read).
+__device__ __forceinline__ void tmem_ld32_nowait(unsigned taddr, unsigned (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
     unsigned r[32];
     asm volatile(
@@ -398,17 +409,29 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 if (!mbar_wait(&S->acc_full[b], (g >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
                 const int n = min(nch, nt_pad - ch * nch);
-                for (int j = slice * 32; j < n; j += 32 * NSL) {
-                    float v[32];
-                    tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), v);
-                    quad_transpose(v, lane);
-                    const int t0 = ch * nch + j + (lane & 3);
-                    if (in) {
+                // two 32-column slices per round: both TMEM loads in flight before one wait
+                for (int j = slice * 32; j < n; j += 64 * NSL) {
+                    const int j2 = j + 32 * NSL;
+                    const bool two = j2 < n;
+                    unsigned ra[32], rb[32];
+                    tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), ra);
+                    if (two) tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j2), rb);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int bb = 0; bb < 8; ++bb)
-                            if (t0 + 4 * bb < nt)
-                                *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
-                                    make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !two) break;
+                        float v[32];
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(h ? rb[e] : ra[e]);
+                        quad_transpose(v, lane);
+                        const int t0 = ch * nch + (h ? j2 : j) + (lane & 3);
+                        if (in) {
+#pragma unroll
+                            for (int bb = 0; bb < 8; ++bb)
+                                if (t0 + 4 * bb < nt)
+                                    *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
+                                        make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
+                        }
                     }
                 }
                 tc_fence_before();
