@@ -158,7 +158,9 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * H_bytes must be >= n_t * 3 * Nx*Ny*Nz * sizeof(element), else WT_ERR_ARG.
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
- * and returns only after that tuning; later calls reuse the choice. */
+ * and returns only after that tuning; later calls reuse the choice.  The
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct"
+ * (the values of wt_get_tuning) fixes the shapes without tuning. */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
 /* Exact FP64 point evaluation of H (the band-limited spectral sum, no grid

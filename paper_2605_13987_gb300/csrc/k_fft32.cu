@@ -37,9 +37,9 @@ __global__ void f32_tables_kernel(const double* __restrict__ xy, int n_cols, int
 }
 
 // rho^ planes; grid (Nz, nb, F32_DEP_SPLIT): each block takes a slice of the
-// m_x rows of one plane (warps over rows, lanes over m_y).  Shared tables:
+// m_x rows of one plane (warps over 2-row x 64-column tiles, lanes over m_y).  Shared tables:
 // px[c][mx] = e^{-i kx x_c} (the block's rows), qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
-constexpr int F32_DEP_SPLIT = 4;
+constexpr int F32_DEP_SPLIT = 5;
 __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __restrict__ phx,
                                    const C2<float>* __restrict__ phy, const float* __restrict__ Zc,
                                    C2<float>* __restrict__ rho) {
@@ -64,16 +64,33 @@ __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __res
     __syncthreads();
     C2<float>* out = rho + ((size_t)b * g.Nz + mz) * nxh * ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = warp; r < nr; r += nw)
-        for (int my = lane; my < ny; my += 32) {
-            C2<float> acc = {0.f, 0.f};
-            for (int c = 0; c < n_cols; ++c) {
-                const C2<float> a = px[c * rows + r], q = qy[c * ny + my];
-                acc.x = fmaf(a.x, q.x, fmaf(-a.y, q.y, acc.x));
-                acc.y = fmaf(a.x, q.y, fmaf(a.y, q.x, acc.y));
-            }
-            out[(size_t)(mx0 + r) * ny + my] = acc;
+    // register tiles of 2 rows x 2 columns per lane (64-column chunks): per column 2 broadcast
+    // loads of px and 2 loads of qy feed 4 complex multiply-adds
+    const int n_rp = (nr + 1) / 2, n_ch = (ny + 63) / 64;
+    for (int item = warp; item < n_rp * n_ch; item += nw) {
+        const int r = 2 * (item / n_ch), my = (item % n_ch) * 64 + lane;
+        const bool r1 = r + 1 < nr, c0 = my < ny, c1 = my + 32 < ny;
+        C2<float> a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
+        const C2<float>* pr = px + r;
+        const C2<float>* qm = qy + my;
+#pragma unroll 6
+        for (int c = 0; c < n_cols; ++c) {
+            const C2<float> p0 = pr[c * rows], p1 = r1 ? pr[c * rows + 1] : C2<float>{0.f, 0.f};
+            const C2<float> q0 = c0 ? qm[c * ny] : C2<float>{0.f, 0.f};
+            const C2<float> q1 = c1 ? qm[c * ny + 32] : C2<float>{0.f, 0.f};
+            a00 = {fmaf(p0.x, q0.x, fmaf(-p0.y, q0.y, a00.x)), fmaf(p0.x, q0.y, fmaf(p0.y, q0.x, a00.y))};
+            a01 = {fmaf(p0.x, q1.x, fmaf(-p0.y, q1.y, a01.x)), fmaf(p0.x, q1.y, fmaf(p0.y, q1.x, a01.y))};
+            a10 = {fmaf(p1.x, q0.x, fmaf(-p1.y, q0.y, a10.x)), fmaf(p1.x, q0.y, fmaf(p1.y, q0.x, a10.y))};
+            a11 = {fmaf(p1.x, q1.x, fmaf(-p1.y, q1.y, a11.x)), fmaf(p1.x, q1.y, fmaf(p1.y, q1.x, a11.y))};
         }
+        C2<float>* o0 = out + (size_t)(mx0 + r) * ny + my;
+        if (c0) o0[0] = a00;
+        if (c1) o0[32] = a01;
+        if (r1) {
+            if (c0) o0[ny] = a10;
+            if (c1) o0[ny + 32] = a11;
+        }
+    }
 }
 
 __global__ void f32_twiddle_kernel(float* tw, int N) {

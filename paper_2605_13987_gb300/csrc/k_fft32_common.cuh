@@ -23,7 +23,8 @@ __host__ __device__ __forceinline__ int zpass_pitch(int nz, int R) {
 }
 inline size_t zpass_smem(const GridDev& g, int lb, int R) {
     const size_t S = (size_t)zpass_pitch(g.Nz, R);
-    return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz) * sizeof(C2<float>);
+    // staged pairs, the twiddle table (nz) and the skewed phase table (nz + nz / R)
+    return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz + (size_t)g.Nz / R + 1) * sizeof(C2<float>);
 }
 
 // Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.

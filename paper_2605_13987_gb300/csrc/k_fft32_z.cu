@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
     const int S = zpass_pitch(nz, RZ);                                      // odd pair pitch
     C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [LB/2][S]
     C2<float>* tw = cs + (size_t)(LB / 2) * S;                              // [nz]
-    C2<float>* zs = tw + nz;                                                // [nz]
+    C2<float>* zs = tw + nz;                                                // [zskew(nz-1)+1], skewed
     for (int e = threadIdx.x; e < nz; e += blockDim.x) {
         tw[e] = twz[e];
-        zs[e] = zsh[e];
+        zs[zskew(e, RZ)] = zsh[e];          // read at m = j1 + RZ gl: the skew spreads the banks
     }
     {   // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
         constexpr int MS = 256 / LB;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
             const C2<float> cm = act ? cf[zskew(m, RZ)] : C2<float>{0.f, 0.f};
             const C2<float> cr = (act && m) ? cf[zskew(nz - m, RZ)] : C2<float>{0.f, 0.f};
             const C2<float> p = sine ? cr : cm, q = sine ? cm : cr;     // Y = (p - i q) e^{i pi m / 2N}
-            v[j1] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
+            v[j1] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[zskew(m, RZ)]);
         }
         warp_fft_t<RZ>(v, gl, W, lt, tw);
         __syncwarp();                             // every lane of the group has read its inputs

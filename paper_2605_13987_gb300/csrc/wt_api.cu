@@ -12,6 +12,7 @@
 #include <mutex>
 #include <tuple>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -1360,6 +1361,19 @@ TuneResult autotune(wt_ctx* c, float* H) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(tune_key(c));
         if (it != g_tune.end()) return it->second;
+    }
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct" fixes the shapes without timing
+    // (reproducible profiling runs); the values are checked like tuned ones
+    if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
+        TuneResult t{};
+        if (std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy, &t.rz, &t.xd) != 7 ||
+            (t.nb != 1 && t.nb != 2 && t.nb != 4) || (t.lb != 16 && t.lb != 32 && t.lb != 64) ||
+            (t.nch != 64 && t.nch != 128 && t.nch != 256) || (t.nepi != 8 && t.nepi != 16))
+            fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct with valid values");
+        c->sp32.set_radix(t.rxy, t.rz);       // checks the register-FFT lengths
+        t.xd = t.xd ? 1 : 0;
+        t.spectral_ms = t.expand_ms = 0.0;
+        return t;
     }
     cudaStream_t s = c->s;
     const wt_grid& g = c->grid;
