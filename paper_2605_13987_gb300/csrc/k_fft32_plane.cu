@@ -45,13 +45,22 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
         const int W = Wy, G = 32 / W, grp = lane / W, gl = lane % W;
         LaneTw<RY> lt;
         lane_twiddles<RY>(ty, gl, W, true, lt);
+        // the next row's rho^ values are loaded while the current row is transformed
+        C2<float> raw[RY];
+        auto load_row = [&](int base_) {
+            const int mx_ = base_ + grp;
+            const bool live_ = mx_ < nxh && mx_ != nx / 2;
+            const C2<float>* rrow = rp + (size_t)(live_ ? mx_ : 0) * ny;
+#pragma unroll
+            for (int j = 0; j < RY; ++j) raw[j] = live_ ? rrow[gl + W * j] : C2<float>{0.f, 0.f};
+        };
+        if (warp * G < nxh) load_row(warp * G);
         for (int base = warp * G; base < nxh; base += 8 * G) {
             const int mx = base + grp;
             const bool act = mx < nxh;
             const bool live = act && mx != nx / 2;                 // the x Nyquist row stays zero
             const float kx = ckx * mx;
             const float fold = mx ? 2.f : 1.f;                     // x half-spectrum fold
-            const C2<float>* rrow = rp + (size_t)(live ? mx : 0) * ny;
             C2<float> v[RY];
 #pragma unroll
             for (int j = 0; j < RY; ++j) {
@@ -62,7 +71,7 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
                 const float k2 = kp2 + kz * kz;
                 C2<float> e = {0.f, 0.f};
                 if (live && my != ny / 2 && k2 > 0.f) {
-                    const C2<float> r = rrow[my];
+                    const C2<float> r = raw[j];
                     float gk = __fdividef(pref * fold, k2);
                     if (mode == 1) gk *= (comp < 2 ? -3.f : -2.f) + __fdividef(2.f * kp2, k2);
                     // the z pass's cosine series carries the factor 2 of the +-k_z pair itself
@@ -72,6 +81,7 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
                 }
                 v[j] = e;
             }
+            if (base + 8 * G < nxh) load_row(base + 8 * G);
             warp_fft_dit_t<RY>(v, gl, W, lt, ty);
             if (act)
 #pragma unroll

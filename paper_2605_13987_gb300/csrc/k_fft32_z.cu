@@ -89,10 +89,15 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
         const size_t La = L0 + 2 * f, Lb = La + 1;
         const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
         const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
-        if (La < nxy)
+        if (Lb < nxy) {
+            for (int z = gl; z < nz; z += W) {      // one 64-bit read per lane feeds both lines
+                const C2<float> y = cf[z + (z >> 4)];
+                ob[pa + z] = y.x;
+                ob[pb + z] = y.y;
+            }
+        } else if (La < nxy) {
             for (int z = gl; z < nz; z += W) ob[pa + z] = cf[z + (z >> 4)].x;
-        if (Lb < nxy)
-            for (int z = gl; z < nz; z += W) ob[pb + z] = cf[z + (z >> 4)].y;
+        }
     }
 }
 
