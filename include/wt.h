@@ -321,6 +321,20 @@ typedef struct {
 wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double dt, const wt_shaper* shaper,
                    const float* noise, float* v, void* cuda_stream);
 
+/* Wait for the context's work and for cuda_stream, and report a device-side
+ * failure of earlier asynchronous calls (wt_extend / wt_batch_run into
+ * device buffers, wt_eq1): WT_ERR_TIMEOUT if a bounded wait in a kernel gave
+ * up (the kernel unwound and freed its resources; the context stays
+ * usable), WT_ERR_NAN for a non-finite result.  The error word is cleared.
+ *
+ * Failure injection for tests: the environment variable WT_FAULT, a comma
+ * separated list of fit_singular (wt_fit reports WT_ERR_NOT_SPD),
+ * alloc (every device allocation fails with WT_ERR_OOM), nan_q (wt_relax
+ * meets a non-finite charge: WT_ERR_NAN) and queue_stall (the tensor-core
+ * expansion withholds its accumulator signals, its bounded waits run out
+ * after about 2 s and the call reports WT_ERR_TIMEOUT). */
+wt_status wt_sync(wt_ctx* ctx, void* cuda_stream);
+
 /* Copy intermediate results to host memory (for checks and diagnostics):
  * q: [n_t][n_sources] node charges (after wt_relax);
  * cn: [n_sources][n_sources] capacitance (after wt_fit);

@@ -84,6 +84,7 @@ SIGNATURES = {
                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
     "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "wt_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_capacitance": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_modes": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -303,6 +304,11 @@ def wt_get_tuning(ctx):
     out = (C.c_int * 7)()
     _check(lib.wt_get_tuning(ctx, out), ctx)
     return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6])
+
+
+def wt_sync(ctx, stream=None):
+    """Wait for the context's work and report device-side failures of earlier asynchronous calls."""
+    _check(load_library().wt_sync(ctx, _stream_handle(stream)), ctx)
 
 
 def wt_get_charges(ctx, n_t, n_sources):

@@ -73,19 +73,25 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity)
     return ok != 0;
 }
 // Bounded wait: false on timeout (and the abort flag is raised).
+// Every caller is a whole warp: the lanes vote, so that a warp either proceeds or unwinds as
+// one (a lane that saw the phase complete while another saw the abort flag takes the abort),
+// and no warp-collective instruction after the wait sees a divided warp.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, volatile int* abort_flag,
                                           int* d_err) {
-    if (mbar_try(b, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        if (mbar_try(b, parity)) return true;
-        if (*abort_flag) return false;
-        if (globaltimer() - t0 > TIMEOUT_NS) {
-            *abort_flag = 1;
-            atomicMax(d_err, (int)DERR_TIMEOUT);
-            return false;
+    bool ok = mbar_try(b, parity);
+    if (!ok) {
+        const unsigned long long t0 = globaltimer();
+        while (true) {
+            if (mbar_try(b, parity)) { ok = true; break; }
+            if (*abort_flag) break;
+            if (globaltimer() - t0 > TIMEOUT_NS) {
+                *abort_flag = 1;
+                atomicMax(d_err, (int)DERR_TIMEOUT);
+                break;
+            }
         }
     }
+    return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
@@ -234,7 +240,8 @@ __device__ __forceinline__ void load_coeffs(const float* __restrict__ W, int nt,
 
 template <int NEPI>
 __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
-    expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int* __restrict__ d_err) {
+    expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int stall,
+                     int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // align the tile region to 1024 bytes
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                         mma_tf32(d, sdesc(a_hi + off), sdesc(bl + off), idesc, 1);
                         mma_tf32(d, sdesc(a_hi + off), sdesc(bh + off), idesc, 1);
                     }
-                    mma_commit(&S->acc_full[b]);
+                    if (!stall) mma_commit(&S->acc_full[b]);     // stall: injected fault (WT_FAULT=queue_stall)
                 }
                 __syncwarp();
             }
@@ -522,8 +529,11 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     else allow_dyn_smem(tc::expand_tc_kernel<16>, sh);
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
-    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, d_err);
-    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, d_err);
+    // WT_FAULT=queue_stall: the MMA warp withholds its accumulator-ready signals, so the epilogue's
+    // bounded waits run out and the kernel unwinds with DERR_TIMEOUT (tests of the failure path)
+    const int stall = fault_enabled("queue_stall") ? 1 : 0;
+    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     WT_LAUNCH("expand_tc");
 }
 

@@ -415,6 +415,10 @@ void do_fit(wt_ctx* c) {
     transpose(s, Y.p, ns, ns, R.p);
     // --- S4: Cholesky and solves, one step of corrected semi-normal equations
     cholesky(s, G.p, ns, ns, c->d_err.p);
+    if (fault_enabled("fit_singular")) {      // injected: as if the factorisation met a non-positive pivot
+        const int v = DERR_NOT_SPD;
+        WT_CUDA(cudaMemcpyAsync(c->d_err.p, &v, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     if (read_err(c)) fail(WT_ERR_NOT_SPD, "normal matrix of the fit is not positive definite (rank-deficient fit)");
     copy_block(s, R.p, ns, Y.p, ns, ns, ns);
     trsm_lower(s, G.p, ns, ns, Y.p, ns, ns);
@@ -681,6 +685,7 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
     charges_at(c, c->d_times.p, nt, Q.p);
     c->Qt.alloc((size_t)nt * ns);
     transpose(s, Q.p, ns, nt, c->Qt.p);
+    if (fault_enabled("nan_q")) fill(s, c->Qt.p, 1, std::nan(""));     // injected non-finite charge
     check_finite(s, c->Qt.p, (size_t)nt * ns, c->d_err.p);
     if (read_err(c)) fail(WT_ERR_NAN, "non-finite charges");
     // S5b: time basis of the charge history (Gram matrix + Jacobi)
@@ -841,11 +846,25 @@ void do_extend(wt_ctx* c, wt_precision prec, void* H, size_t bytes, cudaStream_t
     }
     c->last_launches = launches;
     c->ev_recorded = c->timing;
-    if (!dev && prec == WT_FP32) return;     // copied out chunk by chunk above
+    if (!dev && prec == WT_FP32) {           // copied out chunk by chunk above; synchronous: report now
+        const int e = read_err(c);
+        if (e) {
+            clear_err(c);
+            fail(e == DERR_TIMEOUT ? WT_ERR_TIMEOUT : WT_ERR_NAN, "device-side failure during the extension");
+        }
+        return;
+    }
     if (!dev) {
         const void* src = prec == WT_FP64 ? (const void*)c->stage64.p : (const void*)c->stage32.p;
         WT_CUDA(cudaMemcpyAsync(H, src, need, cudaMemcpyDeviceToHost, s));
         WT_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!dev) {       // synchronous: report a device-side failure now (device H: at wt_sync)
+        const int e = read_err(c);
+        if (e) {
+            clear_err(c);
+            fail(e == DERR_TIMEOUT ? WT_ERR_TIMEOUT : WT_ERR_NAN, "device-side failure during the extension");
+        }
     }
 }
 
@@ -1842,6 +1861,21 @@ wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double 
         if ((size_t)n_out * 12 > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "n_out too large for one block's shared memory");
         shape_launch(static_cast<cudaStream_t>(stream), i, n_tracks, n_out, dt, sh->tau, sh->order, sh->gain,
                      sh->noise_rms, noise, v);
+    });
+}
+
+wt_status wt_sync(wt_ctx* ctx, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_sync", [&] {
+        WT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        WT_CUDA(cudaStreamSynchronize(ctx->s_copy));
+        const int e = read_err(ctx);          // synchronises the context's stream
+        if (e) {
+            clear_err(ctx);
+            WT_CUDA(cudaStreamSynchronize(ctx->s));
+            fail(e == DERR_TIMEOUT ? WT_ERR_TIMEOUT : e == DERR_NOT_SPD ? WT_ERR_NOT_SPD : WT_ERR_NAN,
+                 "device-side failure in earlier asynchronous work on this context");
+        }
     });
 }
 

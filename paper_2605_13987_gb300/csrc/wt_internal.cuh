@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -36,6 +37,15 @@ struct Error {
 };
 
 [[noreturn]] void fail(wt_status code, const std::string& msg);
+
+// Host-side fault injection: WT_FAULT is a comma-separated list of names
+// (fit_singular, alloc, nan_q, queue_stall); each forces one error path.
+inline bool fault_enabled(const char* name) {
+    const char* env = std::getenv("WT_FAULT");
+    if (!env) return false;
+    const std::string list = std::string(",") + env + ",";
+    return list.find(std::string(",") + name + ",") != std::string::npos;
+}
 void cuda_check(cudaError_t e, const char* what);
 #define WT_CUDA(call) ::wt::cuda_check((call), #call)
 #define WT_LAUNCH(what) ::wt::cuda_check(cudaGetLastError(), what)
@@ -76,6 +86,7 @@ struct DBuf {
         if (count == n && p) return;
         release();
         if (count == 0) return;
+        if (fault_enabled("alloc")) fail(WT_ERR_OOM, "injected allocation failure (WT_FAULT=alloc)");
         cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
         if (e != cudaSuccess) {
             cudaGetLastError();

@@ -107,6 +107,10 @@ class Sensor:
         """Launch shapes of the FP32 path (nb, lb, nch, nepi), set by the autotuner."""
         return B.wt_get_tuning(self.ctx)
 
+    def sync(self, stream=None):
+        """Wait and raise on a device-side failure of earlier asynchronous calls."""
+        B.wt_sync(self.ctx, stream)
+
     def charges(self):
         return B.wt_get_charges(self.ctx, len(self.times), self.n_sources)
 
