@@ -29,6 +29,9 @@ listed in the module docstrings:
 * ``eq1``      the Ramo-Shockley-Riegler convolution, Eq. 1.
 * ``electronics`` CR-(RC)^n shaping of the currents (parameterised; the paper
                gives no transfer function).
+* ``features`` signal-shape features of the currents (amplitude, peak time,
+               charge, threshold and constant-fraction crossings) and their
+               sensitivities, for the geometry scans of Sec. 5.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 except the brute-force finite-difference model (``bruteforce``), which is a
