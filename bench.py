@@ -44,6 +44,10 @@ WORKLOADS = {
             "(profiling case: the spectral kernels at c2 sizes, about 2.5 GB on the device)",
     "c4": "c4: 3x3 pixel cell at grid 96x96x192, radius 5 um, 256 time samples, 1e4 straight tracks of 100 "
           "steps; the Eq. 1 loss and its gradient (resistivities, radius, pitch)",
+    "scan": "scan: Sec. 5's bias-diameter scan (6-14 um in 2 um steps) on the 3x3 pixel cell 165x165x500 um, "
+            "grid 20x20x64, 18 columns, 256 time samples, 1000 tracks of 100 steps through the central pixel; "
+            "per variant fit, relaxation, currents with their four parameter tangents, CR-RC^2 shaping, "
+            "signal features and their sensitivities",
     "c3": "c3: 64 single cells, pitch 40-110 um, thickness 300-500 um, radius 4-10 um, grids 64^2x128 to "
           "128^2x256 (uneven), 256 time samples each; batched in waves through an H arena",
 }
@@ -344,6 +348,55 @@ def run_adjoint(args):
     return 0
 
 
+def run_scan_bench(args):
+    """Sec. 5's bias-diameter scan through the scan driver: a step is the
+    whole scan (five variants: fit, relaxation, currents and tangents,
+    shaping, features and sensitivities).  Reports variants per second and
+    the features' track medians per diameter."""
+    import numpy as np
+    import torch
+    import paper_2605_13987_gb300 as P
+    import workloads as W
+    from paper_2605_13987_gb300.scan import run_scan
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    P.load_library()
+    pts = W.scan_bias_diameter()
+    shaper = dict(tau=0.5e-9, order=2)
+    for _ in range(args.warmup):
+        run_scan(pts, sensitivities=True, shaper=shaper, device=local)
+    per = []
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+        barrier(world)
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            res = run_scan(pts, sensitivities=True, shaper=shaper, device=local)
+            torch.cuda.synchronize()
+            per.append(time.perf_counter() - a)
+        barrier(world)
+    s = max_over_ranks(statistics.median(per), world)
+    if rank == 0:
+        summ = {}
+        for r in res:
+            m = r.summary()
+            ds = np.median(r.dfeatures, axis=1)            # [4 params, 6 features], track medians
+            summ[f"{r.value:g}um"] = {"amplitude": m["amplitude"], "rise_time_s": m["rise_time"],
+                                      "t_cfd_s": m["t_cfd"], "charge": m["charge"],
+                                      "dt_cfd_ds_R": float(ds[0, 5]), "dt_cfd_ds_B": float(ds[1, 5]),
+                                      "fit_s": r.info["fit_seconds"], "relax_s": r.info["relax_seconds"]}
+        line = {"metric": "scan variants/sec (fit, relaxation, currents + 4 tangents, shaping, features)",
+                "value": world * len(pts) / s, "unit": "variants/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * s, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 setup, f32 field", "data": "synthetic",
+                "config": {"workload": WORKLOADS["scan"], "variants": len(pts)},
+                "scan": summ, "clocks": clk.summary(local),
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -489,6 +542,7 @@ def run_ours(args):
             "stage_ms": {"column_transform": sum(s[0] for s in stage_ms) / len(stage_ms),
                          "spectral_passes": sum(s[1] for s in stage_ms) / len(stage_ms),
                          "expansion": exp_ms},
+            "tuning": sen.tuning(),
             "step_frac_of_hbm_roof": (alg_bytes / (ms_max / 1e3) / 1e9) / peak,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64_plain": fp64,
             "clocks": clk.summary(local),
@@ -526,6 +580,8 @@ def main():
         return run_batch(args)
     if args.workload == "c4":
         return run_adjoint(args)
+    if args.workload == "scan":
+        return run_scan_bench(args)
     return run_ours(args)
 
 

@@ -159,7 +159,7 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
  * and returns only after that tuning; later calls reuse the choice.  The
- * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct"
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass]"
  * (the values of wt_get_tuning) fixes the shapes without tuning. */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
@@ -268,13 +268,15 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
 /* Launch shapes the FP32 path of this context uses (set by the autotuner;
- * defaults 1, 32, 256, 8, the widest register FFTs, 0): shape7[0] charge
- * vectors per spectral launch, shape7[1] (x, y) lines per z-pass block,
- * shape7[2] time samples per expansion accumulator chunk, shape7[3]
- * expansion epilogue warps, shape7[4] and shape7[5] elements per lane of
+ * defaults 1, 32, 256, 8, the widest register FFTs, 0, 0): shape8[0]
+ * charge vectors per spectral launch, shape8[1] (x, y) lines per z-pass
+ * block, shape8[2] time samples per expansion accumulator chunk, shape8[3]
+ * expansion epilogue warps, shape8[4] and shape8[5] elements per lane of
  * the lateral and z register FFTs (0 before the first extension),
- * shape7[6] 1 if the x transforms store from registers (else staged). */
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape7);
+ * shape8[6] 1 if the x transforms store from registers (else staged),
+ * shape8[7] 1 if the z pass uses the two-pass shared-memory FFT (Nz of 64,
+ * 128 or 256; shape8[5] is then unused). */
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape8);
 
 /* Static field of the electrodes held at fixed potentials (the paper's
  * static drift field, Fig. 2; the sigma -> infinity limit of the
@@ -320,6 +322,39 @@ typedef struct {
 } wt_shaper;
 wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double dt, const wt_shaper* shaper,
                    const float* noise, float* v, void* cuda_stream);
+
+/* Eq. 1 currents and their tangents along the four parameters of
+ * wt_eq1_loss_grad (same chain, same parameters): i ([n_tracks][n_out]) and
+ * di ([4][n_tracks][n_out], di/ds_R, di/ds_B, di/dr, di/dlambda), FP32
+ * device buffers, either may be NULL; loss and grad (4 values) may be NULL.
+ * Forward-mode derivatives of every current sample, for sensitivities of
+ * signal features (wt_features).  Synchronous. */
+wt_status wt_eq1_tangents(wt_ctx* ctx, const wt_tracks* tracks, float* i, float* di, double* loss, double* grad);
+
+/* Signal-shape features of sampled waveforms, for the geometry scans of
+ * Sec. 5 (sensor variants compared by the shape of their signals).  For
+ * waveform r (x[r][m], m = 0..n-1, at tau_m = t0 + m dt):
+ *   f[r][0] amplitude A = x_k, k the first index of the largest |x|;
+ *   f[r][1] peak time tau_k + dt delta, delta the vertex of the parabola
+ *           through samples k-1, k, k+1 (0 at the grid ends);
+ *   f[r][2] charge dt sum_m x_m;
+ *   f[r][3..5] leading-edge crossings of the levels lo A, hi A, cfd A:
+ *           the last sample before k below the level (in s x, s = sign A)
+ *           and linear interpolation to the next; t0 if there is none.
+ * The indices are decided in FP32 (each level is one rounded FP32
+ * product), the features evaluated in FP64.  With n_dir > 0 tangent
+ * waveforms dx[d][r][m] (for example wt_eq1_tangents' di) give
+ * df[d][r][0..5], the features' derivatives at fixed indices.  x, dx: FP32
+ * device arrays; f, df: FP64 device arrays.  opts NULL: lo 0.1, hi 0.9,
+ * cfd 0.5; each fraction in (0, 1].  n >= 1.  Asynchronous on
+ * cuda_stream. */
+#define WT_N_FEATURES 6
+typedef struct {
+    float lo, hi, cfd;
+} wt_feature_opts;
+wt_status wt_features(wt_ctx* ctx, const float* x, int n_tracks, int n, double t0, double dt,
+                      const wt_feature_opts* opts, const float* dx, int n_dir, double* f, double* df,
+                      void* cuda_stream);
 
 /* Wait for the context's work and for cuda_stream, and report a device-side
  * failure of earlier asynchronous calls (wt_extend / wt_batch_run into

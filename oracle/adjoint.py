@@ -66,3 +66,20 @@ def fd_grad(w, tracks, rel_step=1e-4, params=range(N_PARAMS)):
         wm, tm = perturbed(w, tracks, k, -h)
         g[k] = (loss(wp, tp)[0] - loss(wm, tm)[0]) / (2.0 * h)
     return g
+
+
+def fd_currents(w, tracks, rel_step=1e-4, params=range(N_PARAMS)):
+    """Central-difference tangents of the currents, [N_PARAMS, n_tracks, n_out]
+    (rows of parameters not listed are NaN): the reference for the library's
+    forward-mode current tangents."""
+    r0 = w.columns[0].radius
+    out = None
+    for k in params:
+        h = rel_step * (r0 if k == 2 else 1.0)
+        wp, tp = perturbed(w, tracks, k, +h)
+        wm, tm = perturbed(w, tracks, k, -h)
+        d = (loss(wp, tp)[1] - loss(wm, tm)[1]) / (2.0 * h)
+        if out is None:
+            out = np.full((N_PARAMS,) + d.shape, np.nan)
+        out[k] = d
+    return out

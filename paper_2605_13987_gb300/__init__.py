@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     wt_create, wt_add_columns, wt_fit, wt_relax, wt_extend, wt_sample_H, wt_eq1, wt_eq1_noalloc,
     wt_eq1_loss, wt_eq1_loss_grad, wt_batch_run, wt_get_tuning,
     wt_set_resistivity_profile, wt_eq1_loss_grad_profile, wt_shape, wt_static_field, wt_drift, wt_sync,
+    wt_eq1_tangents, wt_features, WT_N_FEATURES, FEATURE_NAMES,
     wt_get_charges, wt_get_capacitance, wt_get_modes, wt_get_info, wt_set_timing, wt_get_timing,
     wt_destroy,
 )

@@ -52,6 +52,14 @@ class wt_shaper(C.Structure):
     _fields_ = [("tau", C.c_double), ("order", C.c_int), ("gain", C.c_double), ("noise_rms", C.c_double)]
 
 
+class wt_feature_opts(C.Structure):
+    _fields_ = [("lo", C.c_float), ("hi", C.c_float), ("cfd", C.c_float)]
+
+
+WT_N_FEATURES = 6
+FEATURE_NAMES = ("amplitude", "t_peak", "charge", "t_lo", "t_hi", "t_cfd")
+
+
 class wt_info(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("n_sources", C.c_int), ("n_colloc", C.c_int), ("n_t", C.c_int),
                 ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
@@ -85,6 +93,10 @@ SIGNATURES = {
     "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
     "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "wt_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "wt_eq1_tangents": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
+    "wt_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double,
+                              C.POINTER(wt_feature_opts), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wt_get_charges": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_capacitance": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_get_modes": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -301,9 +313,44 @@ def wt_batch_run(ctxs, precision, H_list, stream=None):
 
 def wt_get_tuning(ctx):
     lib = load_library()
-    out = (C.c_int * 7)()
+    out = (C.c_int * 8)()
     _check(lib.wt_get_tuning(ctx, out), ctx)
-    return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6])
+    return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6],
+                z_two_pass=out[7])
+
+
+def wt_eq1_tangents(ctx, tracks, i_out=None, di_out=None):
+    """(loss, grad[4]); fills the device tensors i_out [n_tracks, n_out] and
+    di_out [4, n_tracks, n_out] (FP32) when given."""
+    lib = load_library()
+    tr = _tracks_struct(tracks)
+    out = C.c_double(0.0)
+    g = np.zeros(4)
+    _check(lib.wt_eq1_tangents(ctx, C.byref(tr), _ptr(i_out), _ptr(di_out), C.byref(out), _dptr(g)), ctx)
+    return out.value, g
+
+
+def wt_features(ctx, x, t0, dt, lo=0.1, hi=0.9, cfd=0.5, dx=None, f_out=None, df_out=None, stream=None):
+    """Signal features [n_tracks, 6] (FP64 device tensor) of the FP32 device
+    waveforms x [n_tracks, n]; with tangents dx [n_dir, n_tracks, n] also
+    their derivatives [n_dir, n_tracks, 6].  Returns (f, df or None)."""
+    import torch
+    lib = load_library()
+    for t in (x, dx):
+        if t is not None and (t.dtype != torch.float32 or not t.is_contiguous()):
+            raise ValueError("waveforms and tangents must be contiguous float32 tensors")
+    n_tracks, n = int(x.shape[0]), int(x.shape[1])
+    n_dir = 0 if dx is None else int(dx.shape[0])
+    if dx is not None and tuple(dx.shape[1:]) != (n_tracks, n):
+        raise ValueError("tangents must have shape [n_dir, n_tracks, n]")
+    if f_out is None:
+        f_out = torch.empty((n_tracks, WT_N_FEATURES), dtype=torch.float64, device=x.device)
+    if n_dir and df_out is None:
+        df_out = torch.empty((n_dir, n_tracks, WT_N_FEATURES), dtype=torch.float64, device=x.device)
+    o = wt_feature_opts(float(lo), float(hi), float(cfd))
+    _check(lib.wt_features(ctx, _ptr(x), n_tracks, n, float(t0), float(dt), C.byref(o), _ptr(dx), n_dir,
+                           _ptr(f_out), _ptr(df_out if n_dir else None), _stream_handle(stream)), ctx)
+    return f_out, (df_out if n_dir else None)
 
 
 def wt_sync(ctx, stream=None):

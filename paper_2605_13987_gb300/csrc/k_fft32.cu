@@ -157,7 +157,9 @@ std::vector<int> Fast32::radix_options(int N) {
     return out;
 }
 
-void Fast32::set_radix(int r_xy, int r_z) {
+bool Fast32::z_two_pass_supported(int Nz) { return zpass2_supported(Nz); }
+
+void Fast32::set_radix(int r_xy, int r_z, bool z_two_pass) {
     if (g.Nx % r_xy || g.Nz % r_z || !supported_r(r_xy) || !supported_r(r_z))
         fail(WT_ERR_ARG, "register-FFT length does not divide the grid");
     int w = g.Nx / r_xy, wz = g.Nz / r_z;
@@ -167,8 +169,10 @@ void Fast32::set_radix(int r_xy, int r_z) {
     if (sp > 227 * 1024 || sz > 227 * 1024) fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
     plane_allow(r_xy, sp);
     zpass_allow(r_z, sz);
+    if (z_two_pass) zpass2_allow(g.Nz);           // fails for lengths it does not cover
     rxy = r_xy;
     rz = r_z;
+    zsm = z_two_pass;
 }
 
 void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
@@ -188,7 +192,8 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     dim3 gz((unsigned)((nxy + lb - 1) / lb), 3, nb);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(tw_z.p);
     const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
-    zpass_launch(rz, lb, gz, s, g, R, tz, zz, out, out_sb, out_sc);
+    if (zsm) zpass2_launch(lb, gz, s, g, R, tz, zz, out, out_sb, out_sc);
+    else zpass_launch(rz, lb, gz, s, g, R, tz, zz, out, out_sb, out_sc);
 
 }
 

@@ -34,5 +34,11 @@ void plane_launch(int r, bool xdirect, dim3 grid, cudaStream_t s, const GridDev&
 void zpass_allow(int r, size_t smem);
 void zpass_launch(int r, int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
                   const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc);
+// Two-pass shared-memory z FFT (k_fft32_z2.cu), Nz in {64, 128, 256}.
+bool zpass2_supported(int nz);
+size_t zpass2_smem(int A, int B, int lb);
+void zpass2_allow(int nz);
+void zpass2_launch(int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
+                   const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc);
 
 }  // namespace wt

@@ -1,0 +1,166 @@
+// FP32 z pass of the bulk extension, two-pass shared-memory form for
+// power-of-two Nz = A B (A <= B, A, B in {8, 16}): the same cosine and sine
+// series as the register-FFT z pass (k_fft32_z.cu, Makhoul's reordering of
+// the DCT-III with two real lines per complex FFT), with the N-point FFT
+// split as
+//   X[c + B d] = sum_a w_A^{a d} w_N^{a c} sum_b Y[a + A b] w_B^{b c}:
+// pass 1, lane a of a line's A lanes: one B-point DFT in registers, the
+// twiddles w_N^{a c}, the results to shared memory; pass 2: B / A A-point
+// DFTs per lane.  Register DFTs with compile-time twiddles; no shuffles.
+#include "k_fft32_common.cuh"
+
+namespace wt {
+
+// Staged-pair pitch (complex): inputs (N), the pass-1 matrix A (B + 1) and
+// the z-ordered outputs (N + 8); = 1 mod 16, so that the staging stores, the
+// column reads and the two output halves fall into distinct banks.
+__host__ __device__ constexpr int zpass2_pitch(int A, int B) {
+    const int n = A * B + (A > 8 ? A : 8);
+    return ((n + 15) / 16) * 16 + 1;
+}
+size_t zpass2_smem(int A, int B, int lb) {
+    // staged pairs, e^{i pi m / 2N} and the per-lane twiddles w_N^{a c} ([c][a])
+    return ((size_t)(lb / 2) * zpass2_pitch(A, B) + 2 * (size_t)A * B) * sizeof(C2<float>);
+}
+
+template <int A, int B, int LB>
+__global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const float* __restrict__ R,
+                                                            const C2<float>* __restrict__ twz,
+                                                            const C2<float>* __restrict__ zsh, float* __restrict__ out,
+                                                            size_t out_sb, size_t out_sc) {
+    constexpr int N = A * B, S = zpass2_pitch(A, B), G = 32 / A, NP = LB / 2;
+    extern __shared__ unsigned char smem_raw[];
+    const int nx = g.Nx, ny = g.Ny;
+    const size_t nxy = (size_t)nx * ny;
+    const int comp = blockIdx.y, b = blockIdx.z;
+    const size_t L0 = (size_t)blockIdx.x * LB;
+    C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [NP][S]
+    C2<float>* zs = cs + (size_t)NP * S;                                    // [N]
+    C2<float>* tl = zs + N;                                                 // [B][A]: w_N^{a c} at c A + a
+    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        zs[e] = zsh[e];
+        const int c = e / A, a = e % A;
+        tl[e] = twz[a * c];                                                 // a c < N
+    }
+    {   // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
+        constexpr int MS = 256 / LB;
+        const int l = threadIdx.x % LB, m0 = threadIdx.x / LB;
+        const bool lin = L0 + l < nxy;
+        const float* sp = R + ((size_t)b * 3 + comp) * N * nxy + L0 + l;
+        float* dst = reinterpret_cast<float*>(cs) + 2 * (size_t)(l >> 1) * S + (l & 1);
+#pragma unroll 8
+        for (int m = m0; m < N; m += MS) dst[2 * m] = lin ? sp[(size_t)m * nxy] : 0.f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / A, gl = lane % A;
+    const bool sine = comp == 2;
+    float* ob = out + (size_t)b * out_sb + (size_t)comp * out_sc;
+    for (int base = warp * G; base < NP; base += 8 * G) {
+        const int f = base + grp;                 // lines 2f, 2f+1 of this block
+        const bool act = f < NP;
+        C2<float>* cf = cs + (size_t)(act ? f : 0) * S;
+        // pass 1: Y_m = (p - i q) e^{i pi m / 2N} at m = gl + A j, then the B-point DFT over j
+        C2<float> v[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int m = gl + A * j;
+            const C2<float> cm = act ? cf[m] : C2<float>{0.f, 0.f};
+            const C2<float> cr = (act && m) ? cf[N - m] : C2<float>{0.f, 0.f};
+            const C2<float> p = sine ? cr : cm, q = sine ? cm : cr;
+            v[j] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
+        }
+        __syncwarp();                             // every lane has read its inputs before the matrix overwrites them
+        reg_dft_c<B>(v);
+#pragma unroll
+        for (int c = 1; c < B; ++c) v[c] = cmul(v[c], tl[c * A + gl]);
+        if (act)
+#pragma unroll
+            for (int c = 0; c < B; ++c) cf[gl * (B + 1) + c] = v[c];
+        __syncwarp();
+        // pass 2: column c = gl + A r, A-point DFT over a -> X[c + B d]
+        C2<float> o[B];
+#pragma unroll
+        for (int r = 0; r < B / A; ++r) {
+            C2<float> u[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) u[a] = act ? cf[a * (B + 1) + gl + A * r] : C2<float>{0.f, 0.f};
+            reg_dft_c<A>(u);
+#pragma unroll
+            for (int d = 0; d < A; ++d) o[r * A + d] = u[d];
+        }
+        __syncwarp();                             // the matrix is read before the outputs overwrite it
+        // X[j] belongs at z = 2j (j < N/2, d < A/2) or z = 2N - 1 - 2j; stored even z at z/2,
+        // odd z at N/2 + 8 + (z - 1)/2; the sine series takes (-1)^z / 2
+        if (act)
+#pragma unroll
+            for (int r = 0; r < B / A; ++r)
+#pragma unroll
+                for (int d = 0; d < A; ++d) {
+                    const int j = gl + A * r + B * d;
+                    C2<float> y = o[r * A + d];
+                    if (sine) {
+                        const float sg = (2 * d < A) ? 0.5f : -0.5f;
+                        y = {sg * y.x, sg * y.y};
+                    }
+                    cf[(2 * d < A) ? j : N / 2 + 8 + (N - 1 - j)] = y;
+                }
+        __syncwarp();
+        if (!act) continue;
+        const size_t La = L0 + 2 * f, Lb = La + 1;
+        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)N;
+        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)N;
+        if (Lb < nxy) {
+            for (int z = gl; z < N; z += A) {     // one 64-bit read per lane feeds both lines
+                const C2<float> y = cf[(z & 1) ? N / 2 + 8 + (z >> 1) : (z >> 1)];
+                ob[pa + z] = y.x;
+                ob[pb + z] = y.y;
+            }
+        } else if (La < nxy) {
+            for (int z = gl; z < N; z += A) ob[pa + z] = cf[(z & 1) ? N / 2 + 8 + (z >> 1) : (z >> 1)].x;
+        }
+    }
+}
+
+// Two-pass forms compiled in: (A, B) = (8, 8), (8, 16), (16, 16), i.e. Nz = 64, 128, 256.
+#define WT_FOR_EACH_Z2(X) X(8, 8) X(8, 16) X(16, 16)
+
+bool zpass2_supported(int nz) { return nz == 64 || nz == 128 || nz == 256; }
+static void z2_shape(int nz, int* A, int* B) {
+    *A = nz == 64 ? 8 : nz == 128 ? 8 : 16;
+    *B = nz / *A;
+}
+
+void zpass2_allow(int nz) {
+    if (!zpass2_supported(nz)) fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 128, 256}");
+    int A, B;
+    z2_shape(nz, &A, &B);
+    const size_t sz = zpass2_smem(A, B, 64);
+#define WT_CASE(AA, BB) \
+    if (A == AA && B == BB) { \
+        allow_dyn_smem(f32_zpass2_kernel<AA, BB, 16>, sz); \
+        allow_dyn_smem(f32_zpass2_kernel<AA, BB, 32>, sz); \
+        allow_dyn_smem(f32_zpass2_kernel<AA, BB, 64>, sz); \
+    }
+    WT_FOR_EACH_Z2(WT_CASE)
+#undef WT_CASE
+}
+
+void zpass2_launch(int lb, dim3 gz, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* tz,
+                   const C2<float>* zz, float* out, size_t out_sb, size_t out_sc) {
+    if (!zpass2_supported(g.Nz)) fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 128, 256}");
+    int A, B;
+    z2_shape(g.Nz, &A, &B);
+    const size_t sz = zpass2_smem(A, B, lb);
+#define WT_CASE(AA, BB) \
+    if (A == AA && B == BB) { \
+        if (lb == 16) f32_zpass2_kernel<AA, BB, 16><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else if (lb == 32) f32_zpass2_kernel<AA, BB, 32><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        else f32_zpass2_kernel<AA, BB, 64><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+    }
+    WT_FOR_EACH_Z2(WT_CASE)
+#undef WT_CASE
+    WT_LAUNCH("f32_zpass2");
+}
+
+}  // namespace wt

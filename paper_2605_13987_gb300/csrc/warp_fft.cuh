@@ -11,6 +11,7 @@
 // tw: table of w_N^k = exp(+2 pi i k / N), k < N.
 #pragma once
 #include "fft_core.cuh"
+#include <type_traits>
 
 namespace wt {
 
@@ -179,6 +180,78 @@ __device__ __forceinline__ void warp_fft_dit_t(C2<float> (&v)[R], int gl, int W,
 #pragma unroll
     for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t.in[k]);
     lane_stages<R>(v, gl, W, t);
+}
+
+// cos(q pi / 8) for integer q (the sixteenth roots of unity, exp(+2 pi i m / 16) = cos + i sin
+// with q = 2m): exact constants, folded at compile time.
+__host__ __device__ constexpr float cos_pi8(int q) {
+    q = ((q % 16) + 16) % 16;
+    if (q > 8) q = 16 - q;
+    return q == 0 ? 1.0f
+         : q == 1 ? 0.92387953251128675613f
+         : q == 2 ? 0.70710678118654752440f
+         : q == 3 ? 0.38268343236508977173f
+         : q == 4 ? 0.0f
+         : q == 5 ? -0.38268343236508977173f
+         : q == 6 ? -0.70710678118654752440f
+         : q == 7 ? -0.92387953251128675613f
+         : -1.0f;
+}
+
+// x w_R^M, w_R = exp(+2 pi i / R), R in {1, 2, 4, 8, 16}; the quarter turns are exact.
+template <int R, int M>
+__device__ __forceinline__ C2<float> twc(C2<float> x) {
+    constexpr int q = (((M * (16 / R)) % 16) + 16) % 16;      // angle in units of pi / 8
+    if constexpr (q == 0) return x;
+    else if constexpr (q == 4) return {-x.y, x.x};
+    else if constexpr (q == 8) return {-x.x, -x.y};
+    else if constexpr (q == 12) return {x.y, -x.x};
+    else {
+        constexpr float c = cos_pi8(q), s = cos_pi8(q - 4);
+        return {x.x * c - x.y * s, x.x * s + x.y * c};
+    }
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// R-point DFT in registers with compile-time twiddles (exp(+i), natural order
+// in and out), R in {1, 2, 4, 8, 16}: R = 4 B, B-point DFTs over x[j1 + 4 j2],
+// twiddles w_R^{j1 k2}, 4-point DFTs.
+template <int R>
+__device__ __forceinline__ void reg_dft_c(C2<float> (&v)[R]) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2 || R == 4) {
+        reg_dft<R>(v, nullptr, 0);
+    } else {
+        static_assert(R == 8 || R == 16, "compile-time twiddles cover R = 8, 16");
+        constexpr int B = R / 4;
+        C2<float> y[4][B];
+        static_for<0, 4>([&](auto J1) {
+            constexpr int j1 = decltype(J1)::value;
+            C2<float> t[B];
+#pragma unroll
+            for (int j2 = 0; j2 < B; ++j2) t[j2] = v[j1 + 4 * j2];
+            reg_dft_c<B>(t);
+            static_for<0, B>([&](auto K2) {
+                constexpr int k2 = decltype(K2)::value;
+                y[j1][k2] = twc<R, j1 * k2>(t[k2]);
+            });
+        });
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            C2<float> t[4] = {y[0][k2], y[1][k2], y[2][k2], y[3][k2]};
+            reg_dft<4>(t, nullptr, 0);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) v[k2 + B * k1] = t[k1];
+        }
+    }
 }
 
 __device__ __forceinline__ int warp_fft_k2(int gl, int W) {

@@ -63,6 +63,9 @@ size_t eq1_lag64_size();
 void eq1_pack_lag64(void*, int, double, double);
 double dot_f64(cudaStream_t, const double*, const double*, size_t, double*);
 void shape_launch(cudaStream_t, const float*, int, int, double, double, int, double, double, const float*, float*);
+void features_launch(cudaStream_t, const float*, int, int, double, double, float, float, float, const float*, int,
+                     double*, double*);
+void add_f32(cudaStream_t, size_t, const float*, float*);
 void drift_launch(cudaStream_t, const float*, int, int, int, double, double, double, const std::vector<double>&,
                   const double*, const double*, int, int, double, float*, float*, float*, float*, float*, float*);
 
@@ -1078,7 +1081,10 @@ void kline_direction(const wt_ctx* c, const double* delta, std::vector<double>& 
     }
 }
 
-void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, const double* delta = nullptr) {
+// I_out ([n_tracks][n_out]) and dI_out ([4][n_tracks][n_out]), device, optional: the currents and their
+// tangents (parameters 0..3 only).
+void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, const double* delta = nullptr,
+                  float* I_out = nullptr, float* dI_out = nullptr) {
     check_tracks(tr);
     if (c->opts.tikhonov > 0.0) fail(WT_ERR_UNSUPPORTED, "the derivative assumes an unregularised fit");
     ensure_spectral(c);
@@ -1104,6 +1110,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
     I.alloc(nI);
     dI.alloc(nI);
     eq1_run(c, c->stage32.p, false, td, I.p, s);
+    if (I_out) WT_CUDA(cudaMemcpyAsync(I_out, I.p, nI * sizeof(float), cudaMemcpyDeviceToDevice, s));
     *loss = dot_f32(s, I.p, I.p, nI, c->d_scr.p) / (double)nI;
     const double gscale = 2.0 / (double)nI;
 
@@ -1267,14 +1274,18 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
         c->info.grad_trunc_rel = std::max(c->info.grad_trunc_rel, dtr);
         extend32_basis(c, dUb.p, dr, dW.p, nt, dH.p, s, 0, &launches, false);
         eq1_run(c, dH.p, false, td, dI.p, s);
+        float* dIo = (dI_out && p < 4) ? dI_out + (size_t)p * nI : nullptr;
+        if (dIo) WT_CUDA(cudaMemcpyAsync(dIo, dI.p, nI * sizeof(float), cudaMemcpyDeviceToDevice, s));
         double acc = dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
         if (p == 3) {
             // derivative of the field operator itself, and of the lateral velocities
             extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, dH.p, s, 1, &launches, false);
             eq1_run(c, dH.p, false, td, dI.p, s);
             acc += dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
+            if (dIo) add_f32(s, nI, dI.p, dIo);
             eq1_run(c, c->stage32.p, false, td, dI.p, s, zeros.p);
             acc += dot_f32(s, I.p, dI.p, nI, c->d_scr.p);
+            if (dIo) add_f32(s, nI, dI.p, dIo);
         }
         grad[p - p_first] = gscale * acc;
         if (read_err(c)) fail(WT_ERR_NAN, "non-finite or timed-out tangent");
@@ -1290,11 +1301,11 @@ struct BatchEntry {
     unsigned long long uid, version;
     const void* H;
     const void *E, *Zc, *rho, *R, *Ub, *W;
-    int nb, lb, rxy, rz, xd;
+    int nb, lb, rxy, rz, xd, zsm;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
                rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb && rxy == o.rxy &&
-               rz == o.rz && xd == o.xd;
+               rz == o.rz && xd == o.xd && zsm == o.zsm;
     }
 };
 
@@ -1315,7 +1326,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi, rxy, rz, xd;
+    int nb, lb, nch, nepi, rxy, rz, xd, zsm;
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1381,15 +1392,20 @@ TuneResult autotune(wt_ctx* c, float* H) {
         auto it = g_tune.find(tune_key(c));
         if (it != g_tune.end()) return it->second;
     }
-    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct" fixes the shapes without timing
-    // (reproducible profiling runs); the values are checked like tuned ones
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass]" fixes the shapes without
+    // timing (reproducible profiling runs); the values are checked like tuned ones
     if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
         TuneResult t{};
-        if (std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy, &t.rz, &t.xd) != 7 ||
-            (t.nb != 1 && t.nb != 2 && t.nb != 4) || (t.lb != 16 && t.lb != 32 && t.lb != 64) ||
-            (t.nch != 64 && t.nch != 128 && t.nch != 256) || (t.nepi != 8 && t.nepi != 16))
-            fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct with valid values");
-        c->sp32.set_radix(t.rxy, t.rz);       // checks the register-FFT lengths
+        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy, &t.rz,
+                                      &t.xd, &t.zsm);
+        if (nread == 7) t.zsm = 0;
+        if ((nread != 7 && nread != 8) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
+            (t.lb != 16 && t.lb != 32 && t.lb != 64) || (t.nch != 64 && t.nch != 128 && t.nch != 256) ||
+            (t.nepi != 8 && t.nepi != 16))
+            fail(WT_ERR_ARG,
+                 "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass] with valid values");
+        t.zsm = t.zsm ? 1 : 0;
+        c->sp32.set_radix(t.rxy, t.rz, t.zsm);   // checks the register-FFT lengths
         t.xd = t.xd ? 1 : 0;
         t.spectral_ms = t.expand_ms = 0.0;
         return t;
@@ -1398,23 +1414,32 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 1e30, 1e30};
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
     column_ztransform<float>(s, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
-    // register-FFT shapes (lanes per line) of the plane and z passes
+    // register-FFT shapes (lanes per line) of the plane and z passes, and the two-pass z FFT
     {
+        std::vector<std::pair<int, int>> zopts;           // (r_z, two-pass)
+        for (int rz : Fast32::radix_options(g.Nz)) zopts.push_back({rz, 0});
+        if (Fast32::z_two_pass_supported(g.Nz)) zopts.push_back({c->sp32.rz, 1});
         double best_ms = 1e30;
         for (int xd : {0, 1})
             for (int rxy : Fast32::radix_options(g.Nx))
-                for (int rz : Fast32::radix_options(g.Nz)) {
-                    c->sp32.set_radix(rxy, rz);
+                for (const auto& zo : zopts) {
+                    c->sp32.set_radix(rxy, zo.first, zo.second);
                     c->sp32.xdirect = xd;
                     const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
-                    if (ms < best_ms) { best_ms = ms; best.rxy = rxy; best.rz = rz; best.xd = xd; }
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best.rxy = rxy;
+                        best.rz = zo.first;
+                        best.zsm = zo.second;
+                        best.xd = xd;
+                    }
                 }
-        c->sp32.set_radix(best.rxy, best.rz);
+        c->sp32.set_radix(best.rxy, best.rz, best.zsm);
         c->sp32.xdirect = best.xd;
     }
     for (int nb : {1, 2, 4}) {
@@ -1449,7 +1474,7 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
-    c->sp32.set_radix(t.rxy, t.rz);
+    c->sp32.set_radix(t.rxy, t.rz, t.zsm);
     c->sp32.xdirect = t.xd;
     c->tuned = true;
     alloc_fast32(c);
@@ -1457,7 +1482,7 @@ void tune_context(wt_ctx* c, float* H) {
 
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
-                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect};
+                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect, (int)c->sp32.zsm};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1524,7 +1549,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
-        c->sp32.set_radix(t.rxy, t.rz);
+        c->sp32.set_radix(t.rxy, t.rz, t.zsm);
         c->sp32.xdirect = t.xd;
         c->tuned = true;
         alloc_fast32(c);
@@ -1733,17 +1758,18 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
     });
 }
 
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape7) {
+wt_status wt_get_tuning(wt_ctx* ctx, int* shape8) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_get_tuning", [&] {
-        if (!shape7) fail(WT_ERR_ARG, "NULL output");
-        shape7[0] = ctx->tune_nb;
-        shape7[1] = ctx->tune_lb;
-        shape7[2] = ctx->tune_nch;
-        shape7[3] = ctx->tune_nepi;
-        shape7[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
-        shape7[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
-        shape7[6] = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
+        if (!shape8) fail(WT_ERR_ARG, "NULL output");
+        shape8[0] = ctx->tune_nb;
+        shape8[1] = ctx->tune_lb;
+        shape8[2] = ctx->tune_nch;
+        shape8[3] = ctx->tune_nepi;
+        shape8[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
+        shape8[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
+        shape8[6] = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
+        shape8[7] = ctx->sp_ready ? (int)ctx->sp32.zsm : 0;
     });
 }
 
@@ -1861,6 +1887,40 @@ wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double 
         if ((size_t)n_out * 12 > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "n_out too large for one block's shared memory");
         shape_launch(static_cast<cudaStream_t>(stream), i, n_tracks, n_out, dt, sh->tau, sh->order, sh->gain,
                      sh->noise_rms, noise, v);
+    });
+}
+
+wt_status wt_eq1_tangents(wt_ctx* ctx, const wt_tracks* tracks, float* i, float* di, double* loss, double* grad) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_tangents", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_tangents needs wt_relax first");
+        if (!tracks) fail(WT_ERR_ARG, "NULL tracks");
+        if ((i && !is_device_ptr(i)) || (di && !is_device_ptr(di)))
+            fail(WT_ERR_ARG, "current and tangent outputs must be device memory");
+        double l = 0.0, g[4];
+        do_loss_grad(ctx, tracks, &l, g, nullptr, i, di);
+        WT_CUDA(cudaStreamSynchronize(ctx->s));
+        if (loss) *loss = l;
+        if (grad)
+            for (int k = 0; k < 4; ++k) grad[k] = g[k];
+    });
+}
+
+wt_status wt_features(wt_ctx* ctx, const float* x, int n_tracks, int n, double t0, double dt,
+                      const wt_feature_opts* opts, const float* dx, int n_dir, double* f, double* df, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_features", [&] {
+        const wt_feature_opts o = opts ? *opts : wt_feature_opts{0.1f, 0.9f, 0.5f};
+        auto frac_ok = [](float v) { return v > 0.f && v <= 1.f; };
+        if (n_tracks < 0 || n < 1 || n_dir < 0 || !(dt > 0.0) || !std::isfinite(t0))
+            fail(WT_ERR_ARG, "bad sizes, dt or t0");
+        if (!frac_ok(o.lo) || !frac_ok(o.hi) || !frac_ok(o.cfd)) fail(WT_ERR_ARG, "fractions must lie in (0, 1]");
+        if (n_tracks == 0) return;
+        if (!x || !f || !is_device_ptr(x) || !is_device_ptr(f)) fail(WT_ERR_ARG, "x and f must be device memory");
+        if (n_dir > 0 && (!dx || !df || !is_device_ptr(dx) || !is_device_ptr(df)))
+            fail(WT_ERR_ARG, "dx and df must be device memory when n_dir > 0");
+        features_launch(static_cast<cudaStream_t>(stream), x, n_tracks, n, t0, dt, o.lo, o.hi, o.cfd, dx, n_dir, f,
+                        df);
     });
 }
 

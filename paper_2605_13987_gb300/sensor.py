@@ -82,6 +82,22 @@ class Sensor:
         """(loss, dL/deps) along rho_j -> rho_j (1 + eps delta_j)."""
         return B.wt_eq1_loss_grad_profile(self.ctx, tracks, delta)
 
+    def tangents(self, tracks):
+        """(i, di, loss, grad): Eq. 1 currents [n_tracks, n_out] and their
+        derivatives [4, n_tracks, n_out] along (s_R, s_B, r, lambda), device FP32."""
+        import torch
+        n_tr, n_out = int(tracks["n_tracks"]), int(tracks["n_out"])
+        dev = f"cuda:{self.device}"
+        i = torch.empty((n_tr, n_out), dtype=torch.float32, device=dev)
+        di = torch.empty((4, n_tr, n_out), dtype=torch.float32, device=dev)
+        loss, grad = B.wt_eq1_tangents(self.ctx, tracks, i, di)
+        return i, di, loss, grad
+
+    def features(self, x, dt, t0=0.0, dx=None, lo=0.1, hi=0.9, cfd=0.5, stream=None):
+        """Signal features of device waveforms x [n_tracks, n] (and their
+        derivatives along tangents dx [n_dir, n_tracks, n]): (f, df)."""
+        return B.wt_features(self.ctx, x, t0, dt, lo, hi, cfd, dx=dx, stream=stream)
+
     def static_field(self, phi_cols, precision="fp32"):
         """Static field [3, Nx, Ny, Nz] of the electrodes held at phi_cols volts."""
         import torch

@@ -45,3 +45,14 @@ def test_readout_resistivity_dominates_bias():
     tr.y = 55 * UM + np.mod(tr.y, 55 * UM)
     g = A.fd_grad(w, tr, rel_step=1e-4, params=[0, 1])
     assert g[0] < 0 and abs(g[1]) < 0.2 * abs(g[0])
+
+
+def test_current_tangents_give_the_loss_gradient():
+    """Chain rule: dL/dtheta = 2 mean(i di/dtheta), with both sides taken by
+    central differences of the oracle at the same step."""
+    w, tr = _case()
+    L, i = A.loss(w, tr)
+    di = A.fd_currents(w, tr, rel_step=1e-4)
+    g = A.fd_grad(w, tr, rel_step=1e-4)
+    chain = 2.0 * np.mean(i[None] * di, axis=(1, 2))
+    assert np.allclose(chain, g, rtol=1e-6, atol=1e-9 * L)

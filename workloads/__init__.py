@@ -12,5 +12,5 @@ available; these generators stand in for them.
 from .configs import (  # noqa: F401
     GridSpec, ColumnSpec, FitSpec, TrackSet, Workload,
     workload, c1_single_cell, c2_pixel3x3, c3_batch, c4_adjoint, c5_large,
-    tiny_cell, log_times, mip_tracks, drift_tracks,
+    tiny_cell, log_times, mip_tracks, drift_tracks, central_pixel_tracks, scan_bias_diameter, scan_thickness,
 )

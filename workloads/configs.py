@@ -298,6 +298,71 @@ def drift_tracks(grid: GridSpec, cols: List[ColumnSpec], n_tracks: int, n_steps:
     return TrackSet(x, y, z, vx, vy, vz, dt, charge, 2 * n_steps)
 
 
+def central_pixel_tracks(grid: GridSpec, pitch: float, n_tracks: int, n_steps: int, seed: int) -> TrackSet:
+    """mip_tracks with entry points folded into the central pixel of a 3x3
+    matrix (the driven readout's pixel)."""
+    tr = mip_tracks(grid, n_tracks, n_steps, np.random.default_rng(seed))
+    x0 = tr.x[:, :1]
+    y0 = tr.y[:, :1]
+    sx = pitch + np.mod(x0, pitch) - x0
+    sy = pitch + np.mod(y0, pitch) - y0
+    tr.x = np.mod(tr.x + sx, grid.Lx)
+    tr.y = np.mod(tr.y + sy, grid.Ly)
+    return tr
+
+
+def scan_bias_diameter(diameters_um=(6, 8, 10, 12, 14), seed: int = 6, n_tracks: int = 1000, n_steps: int = 100,
+                       n_t: int = 256, nx: int = 20, nz: int = 64) -> List[Tuple[float, Workload]]:
+    """Sec. 5's scan of the bias-electrode diameter (6-14 um in 2 um steps) on
+    the 3x3 pixel matrix (pitch 55 um, 500 um thick, readout radius 5 um,
+    0.5 Ohm*cm in every column), one workload per diameter with the same grid
+    and tracks (through the central pixel).  The lateral spacing (165 um / nx,
+    8.25 um at nx = 20) keeps every radius below one spacing: with the
+    box-band kernel the fit turns indefinite for r / h in (1, 2) and (3, 4),
+    and no finer spacing clears all of r = 3..7 um."""
+    out = []
+    pitch, thick = 55 * UM, 500 * UM
+    grid = GridSpec(3 * pitch, 3 * pitch, thick, nx, nx, nz, 5.7)
+    tracks = central_pixel_tracks(grid, pitch, n_tracks, n_steps, seed)
+    for d in diameters_um:
+        cols = []
+        for i in range(3):
+            for j in range(3):
+                cols.append(_column(grid, (i + 0.5) * pitch, (j + 0.5) * pitch, 5 * UM, 0.5 * OHM_CM, 1,
+                                    int(i == 1 and j == 1), nz))
+        for i in range(3):
+            for j in range(3):
+                cols.append(_column(grid, i * pitch, j * pitch, 0.5 * d * UM, 0.5 * OHM_CM, 0, 0, nz))
+        out.append((float(d), Workload(f"scan_d{d}", grid, cols, FitSpec(), log_times(n_t), tracks=tracks,
+                                       seed=seed, notes=f"bias diameter {d} um")))
+    return out
+
+
+def scan_thickness(thick_um=(300, 400, 500), nz_of=None, seed: int = 8, n_tracks: int = 1000, n_steps: int = 100,
+                   n_t: int = 256, nx: int = 20) -> List[Tuple[float, Workload]]:
+    """Sec. 5's thickness study (shorter readout electrodes): the 3x3 matrix
+    at each thickness, columns through the whole bulk, the same lateral grid,
+    Nz close to a 7.8 um spacing, tracks through the central pixel drawn
+    from the same seed (their transit scales with the thickness)."""
+    nz_of = nz_of or {300: 40, 400: 48, 500: 64}
+    out = []
+    pitch = 55 * UM
+    for th in thick_um:
+        grid = GridSpec(3 * pitch, 3 * pitch, th * UM, nx, nx, nz_of[th], 5.7)
+        cols = []
+        for i in range(3):
+            for j in range(3):
+                cols.append(_column(grid, (i + 0.5) * pitch, (j + 0.5) * pitch, 5 * UM, 0.5 * OHM_CM, 1,
+                                    int(i == 1 and j == 1), grid.Nz))
+        for i in range(3):
+            for j in range(3):
+                cols.append(_column(grid, i * pitch, j * pitch, 4 * UM, 0.5 * OHM_CM, 0, 0, grid.Nz))
+        tracks = central_pixel_tracks(grid, pitch, n_tracks, n_steps, seed)
+        out.append((float(th), Workload(f"scan_t{th}", grid, cols, FitSpec(), log_times(n_t), tracks=tracks,
+                                        seed=seed, notes=f"thickness {th} um")))
+    return out
+
+
 _NAMED = {"c1": c1_single_cell, "c2": c2_pixel3x3, "c4": c4_adjoint, "c5": c5_large}
 
 
