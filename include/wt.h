@@ -159,7 +159,7 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
  * and returns only after that tuning; later calls reuse the choice.  The
- * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass]"
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass]"
  * (the values of wt_get_tuning) fixes the shapes without tuning. */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
@@ -274,8 +274,10 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
  * expansion epilogue warps, shape8[4] and shape8[5] elements per lane of
  * the lateral and z register FFTs (0 before the first extension),
  * shape8[6] 1 if the x transforms store from registers (else staged),
- * shape8[7] 1 if the z pass uses the two-pass shared-memory FFT (Nz of 64,
- * 128 or 256; shape8[5] is then unused). */
+ * shape8[7] the two-pass shared-memory FFTs in use, a bit mask: 1 the z
+ * pass (Nz of 64, 128 or 256; shape8[5] is then unused), 2 the y
+ * transforms (Ny of 64 or 128; shape8[4] then sets the x transforms
+ * only). */
 wt_status wt_get_tuning(wt_ctx* ctx, int* shape8);
 
 /* Static field of the electrodes held at fixed potentials (the paper's

@@ -316,7 +316,7 @@ def wt_get_tuning(ctx):
     out = (C.c_int * 8)()
     _check(lib.wt_get_tuning(ctx, out), ctx)
     return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6],
-                z_two_pass=out[7])
+                two_pass=out[7])
 
 
 def wt_eq1_tangents(ctx, tracks, i_out=None, di_out=None):

@@ -11,11 +11,20 @@ namespace wt {
 // Register-FFT lengths compiled in: elements per lane R = N / W.
 #define WT_FOR_EACH_R(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(24)
 
-inline int plane_ldp(const GridDev& g) { return (g.Ny + 1) | 1; }     // odd row pitch (complex units)
-inline size_t plane_smem(const GridDev& g) {
-    const int nxh = g.Nx / 2 + 1;
-    return ((size_t)nxh * plane_ldp(g) + g.Ny + g.Nx) * sizeof(C2<float>);
+// Two-pass y transforms of Ny = ny2 in {64, 128, 256}: ny2 = A B with A lanes per row
+// (A = 16 for 256, else 8); each row holds the A x (B + 1) exchange matrix.
+__host__ __device__ constexpr int plane_y2_a(int ny2) { return ny2 == 256 ? 16 : 8; }
+// odd row pitch (complex units): Ny + 1 entries, or the two-pass exchange matrix
+__host__ __device__ constexpr int plane_ldp_of(int ny, int ny2) {
+    return ny2 ? (plane_y2_a(ny2) * (ny2 / plane_y2_a(ny2) + 1)) | 1 : (ny + 1) | 1;
 }
+inline size_t plane_smem(const GridDev& g, int ny2 = 0) {
+    const int nxh = g.Nx / 2 + 1;
+    return ((size_t)nxh * plane_ldp_of(g.Ny, ny2) + g.Ny + g.Nx + ny2) * sizeof(C2<float>);
+}
+// (Ny, elements per lane of the x transforms) compiled with two-pass y transforms: 16 or 32 lanes per x
+// line (a 256 x 256 plane does not fit one block's shared memory on either y path)
+#define WT_FOR_EACH_Y2(X) X(64, 2) X(64, 4) X(128, 4) X(128, 8)
 // Row pitch of a staged z line pair: room for the skewed inputs and the skewed outputs.
 __host__ __device__ __forceinline__ int zpass_pitch(int nz, int R) {
     const int a = (nz - 1) + (nz - 1) / R + 1, b = (nz - 1) + ((nz - 1) >> 4) + 1;
@@ -28,8 +37,9 @@ inline size_t zpass_smem(const GridDev& g, int lb, int R) {
 }
 
 // Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.
-void plane_allow(int r, size_t smem);
-void plane_launch(int r, bool xdirect, dim3 grid, cudaStream_t s, const GridDev& g, const C2<float>* rho,
+void plane_allow(int r, int ny2, size_t smem);
+bool plane_y2_supported(int ny, int r);
+void plane_launch(int r, bool xdirect, int ny2, dim3 grid, cudaStream_t s, const GridDev& g, const C2<float>* rho,
                   const C2<float>* twy, const C2<float>* twx, float* R, int mode);
 void zpass_allow(int r, size_t smem);
 void zpass_launch(int r, int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,

@@ -1301,11 +1301,11 @@ struct BatchEntry {
     unsigned long long uid, version;
     const void* H;
     const void *E, *Zc, *rho, *R, *Ub, *W;
-    int nb, lb, rxy, rz, xd, zsm;
+    int nb, lb, rxy, rz, xd, tp;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
                rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb && rxy == o.rxy &&
-               rz == o.rz && xd == o.xd && zsm == o.zsm;
+               rz == o.rz && xd == o.xd && tp == o.tp;
     }
 };
 
@@ -1326,7 +1326,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi, rxy, rz, xd, zsm;
+    int nb, lb, nch, nepi, rxy, rz, xd, tp;    // tp: two-pass FFTs, bit 0 z pass, bit 1 y transforms
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1392,20 +1392,19 @@ TuneResult autotune(wt_ctx* c, float* H) {
         auto it = g_tune.find(tune_key(c));
         if (it != g_tune.end()) return it->second;
     }
-    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass]" fixes the shapes without
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass]" fixes the shapes without
     // timing (reproducible profiling runs); the values are checked like tuned ones
     if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
         TuneResult t{};
         const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy, &t.rz,
-                                      &t.xd, &t.zsm);
-        if (nread == 7) t.zsm = 0;
+                                      &t.xd, &t.tp);
+        if (nread == 7) t.tp = 0;
         if ((nread != 7 && nread != 8) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
             (t.lb != 16 && t.lb != 32 && t.lb != 64) || (t.nch != 64 && t.nch != 128 && t.nch != 256) ||
-            (t.nepi != 8 && t.nepi != 16))
+            (t.nepi != 8 && t.nepi != 16) || t.tp < 0 || t.tp > 3)
             fail(WT_ERR_ARG,
-                 "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,z_two_pass] with valid values");
-        t.zsm = t.zsm ? 1 : 0;
-        c->sp32.set_radix(t.rxy, t.rz, t.zsm);   // checks the register-FFT lengths
+                 "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass] with valid values");
+        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);   // checks the FFT lengths
         t.xd = t.xd ? 1 : 0;
         t.spectral_ms = t.expand_ms = 0.0;
         return t;
@@ -1421,25 +1420,29 @@ TuneResult autotune(wt_ctx* c, float* H) {
     column_ztransform<float>(s, c->Ub.p, c->rank, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
     // register-FFT shapes (lanes per line) of the plane and z passes, and the two-pass z FFT
     {
-        std::vector<std::pair<int, int>> zopts;           // (r_z, two-pass)
+        std::vector<std::pair<int, int>> zopts, xyopts;   // (elements per lane, two-pass)
         for (int rz : Fast32::radix_options(g.Nz)) zopts.push_back({rz, 0});
         if (Fast32::z_two_pass_supported(g.Nz)) zopts.push_back({c->sp32.rz, 1});
+        for (int rxy : Fast32::radix_options(g.Nx)) {
+            xyopts.push_back({rxy, 0});
+            if (Fast32::y_two_pass_supported(g.Ny, rxy)) xyopts.push_back({rxy, 1});
+        }
         double best_ms = 1e30;
         for (int xd : {0, 1})
-            for (int rxy : Fast32::radix_options(g.Nx))
+            for (const auto& xo : xyopts)
                 for (const auto& zo : zopts) {
-                    c->sp32.set_radix(rxy, zo.first, zo.second);
+                    c->sp32.set_radix(xo.first, zo.first, zo.second, xo.second);
                     c->sp32.xdirect = xd;
                     const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
                     if (ms < best_ms) {
                         best_ms = ms;
-                        best.rxy = rxy;
+                        best.rxy = xo.first;
                         best.rz = zo.first;
-                        best.zsm = zo.second;
+                        best.tp = zo.second | (xo.second << 1);
                         best.xd = xd;
                     }
                 }
-        c->sp32.set_radix(best.rxy, best.rz, best.zsm);
+        c->sp32.set_radix(best.rxy, best.rz, best.tp & 1, best.tp & 2);
         c->sp32.xdirect = best.xd;
     }
     for (int nb : {1, 2, 4}) {
@@ -1474,7 +1477,7 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
-    c->sp32.set_radix(t.rxy, t.rz, t.zsm);
+    c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);
     c->sp32.xdirect = t.xd;
     c->tuned = true;
     alloc_fast32(c);
@@ -1482,7 +1485,8 @@ void tune_context(wt_ctx* c, float* H) {
 
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
-                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect, (int)c->sp32.zsm};
+                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect,
+                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1)};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1549,7 +1553,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
-        c->sp32.set_radix(t.rxy, t.rz, t.zsm);
+        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);
         c->sp32.xdirect = t.xd;
         c->tuned = true;
         alloc_fast32(c);
@@ -1769,7 +1773,7 @@ wt_status wt_get_tuning(wt_ctx* ctx, int* shape8) {
         shape8[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
         shape8[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
         shape8[6] = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
-        shape8[7] = ctx->sp_ready ? (int)ctx->sp32.zsm : 0;
+        shape8[7] = ctx->sp_ready ? (int)ctx->sp32.zsm | ((int)ctx->sp32.ysm << 1) : 0;
     });
 }
 

@@ -1,8 +1,10 @@
-"""Every z-pass variant of the FP32 path (the register FFT at each lane
-count, and the two-pass shared-memory FFT for Nz = 64, 128, 256), forced
-through WT_LAUNCH_SHAPES, against the FP64 plain path of the same context
-(itself checked against the oracle in test_gpu_c1 / test_gpu_edges) and,
-for one case per length, against the oracle directly."""
+"""Every FFT variant of the FP32 path, forced through WT_LAUNCH_SHAPES:
+the z pass by the register FFT at each lane count and by the two-pass
+shared-memory FFT (Nz = 64, 128, 256), and the y transforms of the plane
+pass by the register FFT and by the two-pass FFT (Ny = 64, 128) at
+16 and 32 lanes per x line, against the FP64 plain path of the same
+context (itself checked against the oracle, here for Nz = 64 and in
+test_gpu_c1 / test_gpu_edges)."""
 import numpy as np
 import pytest
 
@@ -61,7 +63,33 @@ def test_every_z_variant_matches_fp64(P, torch, monkeypatch, nz):
             t = s.tuning()
         finally:
             s.close()
-        assert t["z_two_pass"] == two_pass and (two_pass or t["r_z"] == rz)
+        assert t["two_pass"] == two_pass and (two_pass or t["r_z"] == rz)
         e = rel_l2(H32, H64)
         print("nz", nz, "r_z", rz, "two-pass", two_pass, "rel L2", e)
         assert e < 1e-5, (nz, rz, two_pass, e)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_two_pass_y_transforms_match_fp64(P, torch, monkeypatch, n):
+    """Lateral grids of n x n (z: 16 cells), both x lane counts, staged and
+    direct x stores."""
+    n_t = {64: 5, 128: 6}[n]
+    w = W.tiny_cell(nx=n, nz=16, n_t=n_t, pitch=55 * UM * n / 32, radius=5 * UM)
+    H64 = None
+    for rxy in (n // 32, n // 16):
+        for xd in (0, 1):
+            monkeypatch.setenv("WT_LAUNCH_SHAPES", f"2,32,256,8,{rxy},1,{xd},2")
+            s = P.Sensor(w.grid, w.columns)
+            try:
+                s.fit()
+                s.relax(w.times)
+                if H64 is None:
+                    H64 = s.extend("fp64").cpu().numpy()
+                H32 = s.extend("fp32").double().cpu().numpy()
+                t = s.tuning()
+            finally:
+                s.close()
+            assert t["two_pass"] == 2 and t["r_xy"] == rxy and t["x_direct"] == xd
+            e = rel_l2(H32, H64)
+            print("n", n, "r_xy", rxy, "x_direct", xd, "rel L2", e)
+            assert e < 1e-5, (n, rxy, xd, e)
