@@ -13,8 +13,8 @@
 // (hi*hi + hi*lo + lo*hi, kind::tf32, FP32 accumulation in tensor memory)
 // give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
 // grid point, column = time sample), double buffered in two 256-column
-// halves; eight or sixteen epilogue warps (two or four per TMEM lane quadrant,
-// alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
+// halves; eight, twelve or sixteen epilogue warps (two to four per TMEM lane
+// quadrant, alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
 // lane quads by shuffles and write H with 16-byte stores: each warp store
 // covers 4 time samples x 32 consecutive grid points (four full 128-byte
 // lines), a quarter of the store instructions of one float per lane.
@@ -524,8 +524,9 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     WT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
-    if (nepi != 8 && nepi != 16) fail(WT_ERR_ARG, "expansion epilogue warps must be 8 or 16");
+    if (nepi != 8 && nepi != 12 && nepi != 16) fail(WT_ERR_ARG, "expansion epilogue warps must be 8, 12 or 16");
     if (nepi == 8) allow_dyn_smem(tc::expand_tc_kernel<8>, sh);
+    else if (nepi == 12) allow_dyn_smem(tc::expand_tc_kernel<12>, sh);
     else allow_dyn_smem(tc::expand_tc_kernel<16>, sh);
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
@@ -533,6 +534,8 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     // bounded waits run out and the kernel unwinds with DERR_TIMEOUT (tests of the failure path)
     const int stall = fault_enabled("queue_stall") ? 1 : 0;
     if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    else if (nepi == 12)
+        tc::expand_tc_kernel<12><<<grid, 64 + 32 * 12, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     WT_LAUNCH("expand_tc");
 }

@@ -1401,7 +1401,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
         if (nread == 7) t.tp = 0;
         if ((nread != 7 && nread != 8) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
             (t.lb != 16 && t.lb != 32 && t.lb != 64) || (t.nch != 64 && t.nch != 128 && t.nch != 256) ||
-            (t.nepi != 8 && t.nepi != 16) || t.tp < 0 || t.tp > 3)
+            (t.nepi != 8 && t.nepi != 12 && t.nepi != 16) || t.tp < 0 || t.tp > 3)
             fail(WT_ERR_ARG,
                  "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass] with valid values");
         c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);   // checks the FFT lengths
@@ -1459,7 +1459,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     spectral_all(c, s);
-    for (int nepi : {8, 16})
+    for (int nepi : {8, 12, 16})
         for (int nch : {64, 128, 256}) {
             ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
             const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi); });
