@@ -159,7 +159,7 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
  * and returns only after that tuning; later calls reuse the choice.  The
- * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass]"
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec]]"
  * (the values of wt_get_tuning) fixes the shapes without tuning. */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
@@ -267,18 +267,23 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
  * same context concurrently. */
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
-/* Launch shapes the FP32 path of this context uses (set by the autotuner;
- * defaults 1, 32, 256, 8, the widest register FFTs, 0, 0): shape8[0]
- * charge vectors per spectral launch, shape8[1] (x, y) lines per z-pass
- * block, shape8[2] time samples per expansion accumulator chunk, shape8[3]
- * expansion epilogue warps, shape8[4] and shape8[5] elements per lane of
- * the lateral and z register FFTs (0 before the first extension),
- * shape8[6] 1 if the x transforms store from registers (else staged),
- * shape8[7] the two-pass shared-memory FFTs in use, a bit mask: 1 the z
- * pass (Nz of 64, 128 or 256; shape8[5] is then unused), 2 the y
- * transforms (Ny of 64 or 128; shape8[4] then sets the x transforms
- * only). */
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape8);
+/* Launch shapes the FP32 path of this context uses, set by the autotuner
+ * (before the first extension: the defaults 1, 32, 256, 8, 0, 0, 0, 0, 4). */
+typedef struct {
+    int nb;         /* charge vectors per spectral launch: 1, 2, 4 */
+    int lb;         /* (x, y) lines per z-pass block: 16, 32, 64 */
+    int nch;        /* time samples per expansion accumulator chunk: 64, 128, 256 */
+    int nepi;       /* expansion epilogue warps: 8, 12, 16 */
+    int r_xy, r_z;  /* elements per lane of the lateral and z register FFTs */
+    int x_direct;   /* 1: the x transforms store from registers (else staged) */
+    int two_pass;   /* two-pass shared-memory FFTs in use, a bit mask: 1 the z pass (Nz of 64, 128
+                       or 256; r_z then unused), 2 the y transforms (Ny of 64 or 128; r_xy then
+                       sets the x transforms only), 4 the x transforms too (with 2, Nx = Ny;
+                       r_xy and x_direct then unused) */
+    int store_vec;  /* floats per expansion store: 4 (4 x 4 lane-quad transposes), 2 (2 x 2
+                       lane-pair transposes) or 1 (straight from the accumulator layout) */
+} wt_tuning;
+wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out);
 
 /* Static field of the electrodes held at fixed potentials (the paper's
  * static drift field, Fig. 2; the sigma -> infinity limit of the

@@ -52,6 +52,11 @@ class wt_shaper(C.Structure):
     _fields_ = [("tau", C.c_double), ("order", C.c_int), ("gain", C.c_double), ("noise_rms", C.c_double)]
 
 
+class wt_tuning(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("nb", "lb", "nch", "nepi", "r_xy", "r_z", "x_direct", "two_pass",
+                                       "store_vec")]
+
+
 class wt_feature_opts(C.Structure):
     _fields_ = [("lo", C.c_float), ("hi", C.c_float), ("cfd", C.c_float)]
 
@@ -91,7 +96,7 @@ SIGNATURES = {
     "wt_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.POINTER(wt_shaper),
                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "wt_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p), C.c_void_p]),
-    "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "wt_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(wt_tuning)]),
     "wt_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
     "wt_eq1_tangents": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
@@ -313,10 +318,9 @@ def wt_batch_run(ctxs, precision, H_list, stream=None):
 
 def wt_get_tuning(ctx):
     lib = load_library()
-    out = (C.c_int * 8)()
-    _check(lib.wt_get_tuning(ctx, out), ctx)
-    return dict(nb=out[0], lb=out[1], nch=out[2], nepi=out[3], r_xy=out[4], r_z=out[5], x_direct=out[6],
-                two_pass=out[7])
+    out = wt_tuning()
+    _check(lib.wt_get_tuning(ctx, C.byref(out)), ctx)
+    return {k: getattr(out, k) for k, _ in wt_tuning._fields_}
 
 
 def wt_eq1_tangents(ctx, tracks, i_out=None, di_out=None):

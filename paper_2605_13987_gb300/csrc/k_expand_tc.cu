@@ -17,7 +17,11 @@
 // quadrant, alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
 // lane quads by shuffles and write H with 16-byte stores: each warp store
 // covers 4 time samples x 32 consecutive grid points (four full 128-byte
-// lines), a quarter of the store instructions of one float per lane.
+// lines), a quarter of the store instructions of one float per lane.  The
+// 8-byte variant (2 x 2 transposes within lane pairs) halves the shuffles,
+// which share the load/store data pipe with the stores, for twice the stores;
+// the 4-byte variant stores straight from the TMEM layout (one 128-byte line
+// per warp store, no shuffles).
 //
 // A launch may cover several expansions at once (one per sensor geometry of a
 // batch, each with its own basis fields, coefficients, grid size and time
@@ -238,7 +242,19 @@ __device__ __forceinline__ void load_coeffs(const float* __restrict__ W, int nt,
     }
 }
 
-template <int NEPI>
+// 2 x 2 transposes within lane pairs: on entry lane 2g + i holds v[2b + j] =
+// D[point 2g + i][time 2b + j]; on return v[2b + j] = D[point 2g + j][time 2b + i].
+__device__ __forceinline__ void pair_transpose(float (&v)[32], int lane) {
+    const bool b0 = lane & 1;
+#pragma unroll
+    for (int bb = 0; bb < 16; ++bb) {
+        float* m = v + 2 * bb;
+        const float r = __shfl_xor_sync(0xffffffffu, b0 ? m[0] : m[1], 1);
+        if (b0) m[0] = r; else m[1] = r;
+    }
+}
+
+template <int NEPI, int VEC>
 __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int stall,
                      int* __restrict__ d_err) {
@@ -407,8 +423,8 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             const size_t npts = J.npts[cur];
             const int nt = J.nt[cur], nt_pad = pad32(nt);
             const int n_chunks = (nt_pad + nch - 1) / nch;
-            // after the quad transpose lane 4g + i stores points 4g..4g+3 (16 bytes) of time 4b + i
-            const size_t p4 = (size_t)tile * BM + q * 32 + 4 * (lane >> 2);
+            // after the transposes lane VEC g + i stores points VEC g .. VEC g + VEC - 1 of time VEC b + i
+            const size_t p4 = (size_t)tile * BM + q * 32 + VEC * (lane / VEC);
             const bool in = p4 < npts;                 // npts is a multiple of 4
             float* hp = J.H[cur] + (size_t)c * npts + p4;
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
@@ -430,14 +446,31 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                         float v[32];
 #pragma unroll
                         for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(h ? rb[e] : ra[e]);
-                        quad_transpose(v, lane);
-                        const int t0 = ch * nch + (h ? j2 : j) + (lane & 3);
-                        if (in) {
+                        const int t0 = ch * nch + (h ? j2 : j) + (lane & (VEC - 1));
+                        if constexpr (VEC == 4) {
+                            quad_transpose(v, lane);
+                            if (in) {
 #pragma unroll
-                            for (int bb = 0; bb < 8; ++bb)
-                                if (t0 + 4 * bb < nt)
-                                    *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
-                                        make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
+                                for (int bb = 0; bb < 8; ++bb)
+                                    if (t0 + 4 * bb < nt)
+                                        *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
+                                            make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
+                            }
+                        } else if constexpr (VEC == 1) {
+                            if (in) {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    if (t0 + e < nt) hp[(size_t)(t0 + e) * 3 * npts] = v[e];
+                            }
+                        } else {
+                            pair_transpose(v, lane);
+                            if (in) {
+#pragma unroll
+                                for (int bb = 0; bb < 16; ++bb)
+                                    if (t0 + 2 * bb < nt)
+                                        *reinterpret_cast<float2*>(hp + (size_t)(t0 + 2 * bb) * 3 * npts) =
+                                            make_float2(v[2 * bb], v[2 * bb + 1]);
+                            }
                         }
                     }
                 }
@@ -490,7 +523,23 @@ int expand_tc_max_jobs() { return tc::MAX_JOBS; }
 
 // jobs[j]: E [3][32][npts] FP32, W [nt][32] FP32, H [nt][3][npts] FP32; all
 // expansions in one persistent launch of at most `max_ctas` CTAs (0: one per SM).
-void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err, int nepi) {
+template <int VEC>
+static void launch_expand(int nepi, int grid, size_t sh, cudaStream_t s, const tc::Jobs& J, int nt_pad_max, int units,
+                          int nch, int stall, int* d_err) {
+    if (nepi == 8) {
+        allow_dyn_smem(tc::expand_tc_kernel<8, VEC>, sh);
+        tc::expand_tc_kernel<8, VEC><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    } else if (nepi == 12) {
+        allow_dyn_smem(tc::expand_tc_kernel<12, VEC>, sh);
+        tc::expand_tc_kernel<12, VEC><<<grid, 64 + 32 * 12, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    } else {
+        allow_dyn_smem(tc::expand_tc_kernel<16, VEC>, sh);
+        tc::expand_tc_kernel<16, VEC><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    }
+}
+
+void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err, int nepi,
+                    int vec) {
     if (n_jobs < 1) return;
     if (nch != 64 && nch != 128 && nch != 256) fail(WT_ERR_ARG, "expansion time chunk must be 64, 128 or 256");
     if (n_jobs > tc::MAX_JOBS) fail(WT_ERR_UNSUPPORTED, "too many expansion jobs for one launch");
@@ -525,18 +574,15 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
     WT_CUDA(cudaDeviceGetAttribute(&max_sh, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (sh > (size_t)max_sh) fail(WT_ERR_UNSUPPORTED, "expansion tile does not fit shared memory");
     if (nepi != 8 && nepi != 12 && nepi != 16) fail(WT_ERR_ARG, "expansion epilogue warps must be 8, 12 or 16");
-    if (nepi == 8) allow_dyn_smem(tc::expand_tc_kernel<8>, sh);
-    else if (nepi == 12) allow_dyn_smem(tc::expand_tc_kernel<12>, sh);
-    else allow_dyn_smem(tc::expand_tc_kernel<16>, sh);
+    if (vec != 1 && vec != 2 && vec != 4) fail(WT_ERR_ARG, "expansion store width must be 1, 2 or 4 floats");
     int grid = std::min(n_sm, units);
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
     // WT_FAULT=queue_stall: the MMA warp withholds its accumulator-ready signals, so the epilogue's
     // bounded waits run out and the kernel unwinds with DERR_TIMEOUT (tests of the failure path)
     const int stall = fault_enabled("queue_stall") ? 1 : 0;
-    if (nepi == 8) tc::expand_tc_kernel<8><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
-    else if (nepi == 12)
-        tc::expand_tc_kernel<12><<<grid, 64 + 32 * 12, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
-    else tc::expand_tc_kernel<16><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+    if (vec == 4) launch_expand<4>(nepi, grid, sh, s, J, nt_pad_max, units, nch, stall, d_err);
+    else if (vec == 2) launch_expand<2>(nepi, grid, sh, s, J, nt_pad_max, units, nch, stall, d_err);
+    else launch_expand<1>(nepi, grid, sh, s, J, nt_pad_max, units, nch, stall, d_err);
     WT_LAUNCH("expand_tc");
 }
 
@@ -544,7 +590,7 @@ void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_c
 void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W, int nt, size_t npts, float* H,
                int* d_err) {
     ExpandJob jb{E, r_pad, r, W, nt, npts, H};
-    expand_tc_jobs(s, &jb, 1, 0, tc::NCH, d_err, 8);
+    expand_tc_jobs(s, &jb, 1, 0, tc::NCH, d_err, 8, 4);
 }
 
 }  // namespace wt

@@ -55,12 +55,13 @@ struct Fast32 {
     bool xdirect = false;          // x transforms store from registers (else staged for coalescing)
     bool zsm = false;              // z pass: two-pass shared-memory FFT (else the register FFT of rz)
     bool ysm = false;              // y transforms: two-pass shared-memory FFT (rxy then serves x only)
+    bool xsm = false;              // x transforms two-pass as well (with ysm; rxy, xdirect unused)
     DBuf<float> tw_y, tw_x, tw_z;
     DBuf<float> phx, phy, zsh;     // complex tables
     void init(const GridDev& gd, const std::vector<double>& xy, cudaStream_t s);
     // register-FFT shapes: the elements per lane that give a power-of-two lane count 4..32
     static std::vector<int> radix_options(int N);
-    void set_radix(int r_xy, int r_z, bool z_two_pass = false, bool y_two_pass = false);
+    void set_radix(int r_xy, int r_z, bool z_two_pass = false, bool y_two_pass = false, bool x_two_pass = false);
     static bool z_two_pass_supported(int Nz);
     static bool y_two_pass_supported(int Ny, int r_xy);
     // rho scratch: nb * Nz * (Nx/2+1) * Ny complex; R scratch: nb * 3 * Nz * Nx * Ny real.

@@ -160,24 +160,27 @@ std::vector<int> Fast32::radix_options(int N) {
 bool Fast32::z_two_pass_supported(int Nz) { return zpass2_supported(Nz); }
 bool Fast32::y_two_pass_supported(int Ny, int r_xy) { return plane_y2_supported(Ny, r_xy); }
 
-void Fast32::set_radix(int r_xy, int r_z, bool z_two_pass, bool y_two_pass) {
+void Fast32::set_radix(int r_xy, int r_z, bool z_two_pass, bool y_two_pass, bool x_two_pass) {
     if (g.Nx % r_xy || g.Nz % r_z || !supported_r(r_xy) || !supported_r(r_z))
         fail(WT_ERR_ARG, "register-FFT length does not divide the grid");
     int w = g.Nx / r_xy, wz = g.Nz / r_z;
     if ((w & (w - 1)) || w > 32 || (wz & (wz - 1)) || wz > 32)
         fail(WT_ERR_ARG, "lanes per FFT line must be a power of two up to 32");
     const int ny2 = y_two_pass ? g.Ny : 0;
-    if (y_two_pass && !plane_y2_supported(g.Ny, r_xy))
+    if (x_two_pass && !(y_two_pass && g.Nx == g.Ny && plane_y2_supported(g.Ny, 0)))
+        fail(WT_ERR_UNSUPPORTED, "two-pass x transforms need the two-pass y transforms and Nx = Ny in {64, 128}");
+    if (y_two_pass && !x_two_pass && !plane_y2_supported(g.Ny, r_xy))
         fail(WT_ERR_UNSUPPORTED, "two-pass y transforms need Ny in {64, 128} and 16 or 32 lanes per x line");
     const size_t sp = plane_smem(g, ny2), sz = zpass_smem(g, 64, r_z);
     if (sp > 227 * 1024 || sz > 227 * 1024) fail(WT_ERR_UNSUPPORTED, "grid too large for the FP32 plane kernels");
-    plane_allow(r_xy, ny2, sp);
+    plane_allow(x_two_pass ? 0 : r_xy, ny2, sp);
     zpass_allow(r_z, sz);
     if (z_two_pass) zpass2_allow(g.Nz);           // fails for lengths it does not cover
     rxy = r_xy;
     rz = r_z;
     zsm = z_two_pass;
     ysm = y_two_pass;
+    xsm = x_two_pass;
 }
 
 void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
@@ -191,7 +194,7 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     dim3 gp(g.Nz, 3, nb);
     const C2<float>* ty = reinterpret_cast<const C2<float>*>(tw_y.p);
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(tw_x.p);
-    plane_launch(rxy, xdirect, ysm ? g.Ny : 0, gp, s, g, rc, ty, tx, R, mode);
+    plane_launch(xsm ? 0 : rxy, xdirect, ysm ? g.Ny : 0, gp, s, g, rc, ty, tx, R, mode);
 
     const size_t nxy = (size_t)g.Nx * g.Ny;
     dim3 gz((unsigned)((nxy + lb - 1) / lb), 3, nb);

@@ -37,6 +37,7 @@ inline size_t zpass_smem(const GridDev& g, int lb, int R) {
 }
 
 // Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.
+// r = 0 with ny2: the two-pass x transforms as well
 void plane_allow(int r, int ny2, size_t smem);
 bool plane_y2_supported(int ny, int r);
 void plane_launch(int r, bool xdirect, int ny2, dim3 grid, cudaStream_t s, const GridDev& g, const C2<float>* rho,

@@ -13,8 +13,10 @@ namespace wt {
 // times (-3 + 2 k_perp^2/|k|^2) for W_x, W_y and (-2 + 2 k_perp^2/|k|^2) for W_z.
 // NY2 = 0: y transforms by the register FFT of RY elements per lane; NY2 = Ny
 // in {64, 128}: two-pass shared-memory y transforms (as in the z pass), Y[y]
-// stored at column y.
-template <int RY, int RX, bool XDIRECT, int NY2>
+// stored at column y.  X2 (with NY2 = Nx = Ny): the x transforms two-pass as
+// well, their exchange matrix in the pair's own two columns, stores from
+// registers (RX and XDIRECT unused).
+template <int RY, int RX, bool XDIRECT, int NY2, bool X2 = false>
 __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev g, const C2<float>* __restrict__ rho,
                                                         const C2<float>* __restrict__ twy,
                                                         const C2<float>* __restrict__ twx, float* __restrict__ R,
@@ -140,6 +142,68 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
         }
     }
     __syncthreads();
+    if constexpr (X2) {
+        // two-pass x transforms of Nx = YA YB, two real lines (ya, yb) per complex FFT with the
+        // Hermitian completion of the register path below; pass 1 reads the pair's columns, then
+        // holds the YA x YB exchange matrix there (slot k = a + YA c at row k / 2, column
+        // (k odd ? yb : ya); the pair's rows 0..nx/2 - 1 of both columns hold nx slots)
+        constexpr int GX = 32 / YA;
+        const int grp = lane / YA, gl = lane % YA;
+        for (int base = warp * GX; base < ny / 2; base += 8 * GX) {
+            const int pp = base + grp;
+            const bool act = pp < ny / 2;
+            const int ya = 2 * pp, yb = ya + 1;
+            const int ca = act ? ya : 0, cb = act ? yb : 0;
+            C2<float> v[YB];
+#pragma unroll
+            for (int j = 0; j < YB; ++j) {
+                const int mx = gl + YA * j;
+                C2<float> z = {0.f, 0.f};
+                if (act) {
+                    if (mx == 0) {
+                        z = {P[ca].x, P[cb].x};
+                    } else if (mx < nxq) {
+                        const C2<float> a = P[mx * ldp + ca], bb = P[mx * ldp + cb];
+                        z = {0.5f * (a.x - bb.y), 0.5f * (a.y + bb.x)};
+                    } else if (mx > nxq) {
+                        const C2<float> a = P[(nx - mx) * ldp + ca], bb = P[(nx - mx) * ldp + cb];
+                        z = {0.5f * (a.x + bb.y), 0.5f * (bb.x - a.y)};
+                    }
+                }
+                v[j] = z;
+            }
+            __syncwarp();                         // the pair's columns are read before they hold the matrix
+            reg_dft_c<YB>(v);
+#pragma unroll
+            for (int c = 1; c < YB; ++c) v[c] = cmul(v[c], tl[c * YA + gl]);
+            auto slot = [&](int k) -> C2<float>& { return P[(k >> 1) * ldp + ((k & 1) ? cb : ca)]; };
+            if (act)
+#pragma unroll
+                for (int c = 0; c < YB; ++c) slot(gl + YA * c) = v[c];
+            __syncwarp();
+            C2<float> o[YB];
+#pragma unroll
+            for (int r = 0; r < YB / YA; ++r) {
+                C2<float> u[YA];
+#pragma unroll
+                for (int a = 0; a < YA; ++a) u[a] = act ? slot(a + YA * (gl + YA * r)) : C2<float>{0.f, 0.f};
+                reg_dft_c<YA>(u);
+#pragma unroll
+                for (int d = 0; d < YA; ++d) o[r * YA + d] = u[d];
+            }
+            if (act) {
+                float* ra = Rout + (size_t)ya * nx;
+#pragma unroll
+                for (int r = 0; r < YB / YA; ++r)
+#pragma unroll
+                    for (int d = 0; d < YA; ++d) {
+                        const int x = gl + YA * r + YB * d;
+                        ra[x] = o[r * YA + d].x;
+                        ra[nx + x] = o[r * YA + d].y;
+                    }
+            }
+        }
+    } else
     {   // x: ny real lines of length nx from the half spectrum, two lines (y = 2p, 2p + 1) per
         // complex FFT: Z[m] = A'[m] + i B'[m] with the Hermitian completions A'[0] = Re a[0],
         // A'[m] = a[m] / 2, A'[nx - m] = conj(a[m]) / 2 (0 < m < nx/2; a carries the x fold
@@ -213,6 +277,10 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
 
 void plane_allow(int r, int ny2, size_t sp) {
     if (ny2) {
+        if (r == 0) {                         // two-pass x transforms as well
+            if (ny2 == 64) { allow_dyn_smem(f32_plane_kernel<2, 2, true, 64, true>, sp); return; }
+            if (ny2 == 128) { allow_dyn_smem(f32_plane_kernel<4, 4, true, 128, true>, sp); return; }
+        }
 #define WT_CASE(NN, RR) \
         if (ny2 == NN && r == RR) { allow_dyn_smem(f32_plane_kernel<RR, RR, false, NN>, sp); \
                                     allow_dyn_smem(f32_plane_kernel<RR, RR, true, NN>, sp); return; }
@@ -230,6 +298,7 @@ void plane_allow(int r, int ny2, size_t sp) {
 }
 
 bool plane_y2_supported(int ny, int r) {
+    if (r == 0) return ny == 64 || ny == 128;     // with two-pass x transforms
 #define WT_CASE(NN, RR) if (ny == NN && r == RR) return true;
     WT_FOR_EACH_Y2(WT_CASE)
 #undef WT_CASE
@@ -240,6 +309,13 @@ void plane_launch(int r, bool xdirect, int ny2, dim3 gp, cudaStream_t s, const G
                   const C2<float>* ty, const C2<float>* tx, float* R, int mode) {
     const size_t sp = plane_smem(g, ny2);
     if (ny2) {
+        if (r == 0) {                         // two-pass x transforms as well
+            if (ny2 == 64) f32_plane_kernel<2, 2, true, 64, true><<<gp, 256, sp, s>>>(g, rc, ty, tx, R, mode);
+            else if (ny2 == 128) f32_plane_kernel<4, 4, true, 128, true><<<gp, 256, sp, s>>>(g, rc, ty, tx, R, mode);
+            else fail(WT_ERR_UNSUPPORTED, "two-pass x transforms: Nx = Ny in {64, 128}");
+            WT_LAUNCH("f32_plane");
+            return;
+        }
 #define WT_CASE(NN, RR) \
         if (ny2 == NN && r == RR) { \
             if (xdirect) f32_plane_kernel<RR, RR, true, NN><<<gp, 256, sp, s>>>(g, rc, ty, tx, R, mode); \

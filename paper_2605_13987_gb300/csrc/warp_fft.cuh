@@ -164,6 +164,17 @@ __device__ __forceinline__ void lane_stages(C2<float> (&v)[R], int gl, int W, co
     }
 }
 
+template <int R>
+__device__ __forceinline__ void reg_dft_c(C2<float> (&v)[R]);
+
+// R-point register DFT of the warp FFTs: compile-time twiddles where they exist
+// (R = 8, 16: the same correctly rounded values as the table), else the table.
+template <int R>
+__device__ __forceinline__ void reg_dft_any(C2<float> (&v)[R], const C2<float>* __restrict__ tw, int W) {
+    if constexpr (R == 8 || R == 16) reg_dft_c<R>(v);
+    else reg_dft<R>(v, tw, W);
+}
+
 // warp_fft / warp_fft_dit with per-lane twiddles (same input and output orders).
 template <int R>
 __device__ __forceinline__ void warp_fft_t(C2<float> (&v)[R], int gl, int W, const LaneTw<R>& t,
@@ -171,12 +182,12 @@ __device__ __forceinline__ void warp_fft_t(C2<float> (&v)[R], int gl, int W, con
     lane_stages<R>(v, gl, W, t);
 #pragma unroll
     for (int j = 1; j < R; ++j) v[j] = cmul(v[j], t.in[j]);
-    reg_dft<R>(v, tw, W);
+    reg_dft_any<R>(v, tw, W);
 }
 template <int R>
 __device__ __forceinline__ void warp_fft_dit_t(C2<float> (&v)[R], int gl, int W, const LaneTw<R>& t,
                                                const C2<float>* __restrict__ tw) {
-    reg_dft<R>(v, tw, W);
+    reg_dft_any<R>(v, tw, W);
 #pragma unroll
     for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t.in[k]);
     lane_stages<R>(v, gl, W, t);

@@ -145,7 +145,7 @@ struct wt_ctx {
     int last_launches = 0;
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
-    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8;
+    int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_vec = 4;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -756,7 +756,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
             float* o = out + (size_t)t0 * 3 * npts;
             if (tc) {
                 ExpandJob jb{c->E32.p, rp, r, W32 + (size_t)t0 * rp, n, npts, o};
-                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
+                expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_vec);
             } else {
                 expand_simt(s, c->E32.p, rp, W32 + (size_t)t0 * rp, n, rp, npts, o);
             }
@@ -773,7 +773,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
     }
     if (tc) {
         ExpandJob jb{c->E32.p, rp, r, W32, nt, npts, out};
-        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi);
+        expand_tc_jobs(s, &jb, 1, 0, c->tune_nch, c->d_err.p, c->tune_nepi, c->tune_vec);
     } else {
         expand_simt(s, c->E32.p, rp, W32, nt, rp, npts, out);
     }
@@ -1311,7 +1311,7 @@ struct BatchEntry {
 
 struct BatchPlan {
     std::vector<BatchEntry> ents;
-    int nch = 256, nepi = 8;
+    int nch = 256, nepi = 8, vec = 4;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long last_use = 0;
@@ -1326,7 +1326,7 @@ wt_ctx::~wt_ctx() = default;
 namespace {
 
 struct TuneResult {
-    int nb, lb, nch, nepi, rxy, rz, xd, tp;    // tp: two-pass FFTs, bit 0 z pass, bit 1 y transforms
+    int nb, lb, nch, nepi, rxy, rz, xd, tp, vec;   // tp: two-pass FFTs, bits: 1 z pass, 2 y, 4 x transforms
     double spectral_ms, expand_ms;
 };
 using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
@@ -1392,19 +1392,20 @@ TuneResult autotune(wt_ctx* c, float* H) {
         auto it = g_tune.find(tune_key(c));
         if (it != g_tune.end()) return it->second;
     }
-    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass]" fixes the shapes without
-    // timing (reproducible profiling runs); the values are checked like tuned ones
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec]]" fixes the shapes
+    // without timing (reproducible profiling runs); the values are checked like tuned ones
     if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
         TuneResult t{};
-        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy, &t.rz,
-                                      &t.xd, &t.tp);
-        if (nread == 7) t.tp = 0;
-        if ((nread != 7 && nread != 8) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
+        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy,
+                                      &t.rz, &t.xd, &t.tp, &t.vec);
+        if (nread < 8) t.tp = 0;
+        if (nread < 9) t.vec = 4;
+        if (nread < 7 || (t.vec != 1 && t.vec != 2 && t.vec != 4) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
             (t.lb != 16 && t.lb != 32 && t.lb != 64) || (t.nch != 64 && t.nch != 128 && t.nch != 256) ||
-            (t.nepi != 8 && t.nepi != 12 && t.nepi != 16) || t.tp < 0 || t.tp > 3)
+            (t.nepi != 8 && t.nepi != 12 && t.nepi != 16) || t.tp < 0 || t.tp > 7)
             fail(WT_ERR_ARG,
-                 "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass] with valid values");
-        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);   // checks the FFT lengths
+                 "WT_LAUNCH_SHAPES must be nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec]] with valid values");
+        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);   // checks the FFT lengths
         t.xd = t.xd ? 1 : 0;
         t.spectral_ms = t.expand_ms = 0.0;
         return t;
@@ -1413,7 +1414,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 4, 1e30, 1e30};
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
@@ -1425,24 +1426,25 @@ TuneResult autotune(wt_ctx* c, float* H) {
         if (Fast32::z_two_pass_supported(g.Nz)) zopts.push_back({c->sp32.rz, 1});
         for (int rxy : Fast32::radix_options(g.Nx)) {
             xyopts.push_back({rxy, 0});
-            if (Fast32::y_two_pass_supported(g.Ny, rxy)) xyopts.push_back({rxy, 1});
+            if (Fast32::y_two_pass_supported(g.Ny, rxy)) xyopts.push_back({rxy, 2});
         }
+        if (g.Nx == g.Ny && Fast32::y_two_pass_supported(g.Ny, 0)) xyopts.push_back({c->sp32.rxy, 6});
         double best_ms = 1e30;
         for (int xd : {0, 1})
             for (const auto& xo : xyopts)
                 for (const auto& zo : zopts) {
-                    c->sp32.set_radix(xo.first, zo.first, zo.second, xo.second);
+                    c->sp32.set_radix(xo.first, zo.first, zo.second, xo.second & 2, xo.second & 4);
                     c->sp32.xdirect = xd;
                     const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
                     if (ms < best_ms) {
                         best_ms = ms;
                         best.rxy = xo.first;
                         best.rz = zo.first;
-                        best.tp = zo.second | (xo.second << 1);
+                        best.tp = zo.second | xo.second;
                         best.xd = xd;
                     }
                 }
-        c->sp32.set_radix(best.rxy, best.rz, best.tp & 1, best.tp & 2);
+        c->sp32.set_radix(best.rxy, best.rz, best.tp & 1, best.tp & 2, best.tp & 4);
         c->sp32.xdirect = best.xd;
     }
     for (int nb : {1, 2, 4}) {
@@ -1459,12 +1461,18 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     spectral_all(c, s);
-    for (int nepi : {8, 12, 16})
-        for (int nch : {64, 128, 256}) {
-            ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
-            const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi); });
-            if (ms < best.expand_ms) { best.expand_ms = ms; best.nch = nch; best.nepi = nepi; }
-        }
+    for (int vec : {4, 2, 1})
+        for (int nepi : {8, 12, 16})
+            for (int nch : {64, 128, 256}) {
+                ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
+                const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi, vec); });
+                if (ms < best.expand_ms) {
+                    best.expand_ms = ms;
+                    best.nch = nch;
+                    best.nepi = nepi;
+                    best.vec = vec;
+                }
+            }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out while tuning");
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[tune_key(c)] = best;
@@ -1477,7 +1485,8 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
     c->tune_nepi = t.nepi;
-    c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);
+    c->tune_vec = t.vec;
+    c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);
     c->sp32.xdirect = t.xd;
     c->tuned = true;
     alloc_fast32(c);
@@ -1486,7 +1495,7 @@ void tune_context(wt_ctx* c, float* H) {
 BatchEntry entry_of(wt_ctx* c, const void* H) {
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
                       c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect,
-                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1)};
+                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1) | ((int)c->sp32.xsm << 2)};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1509,7 +1518,7 @@ void capture_batch(BatchPlan& P, wt_ctx* const* ctxs, int n, float* const* H) {
         }
         const int mj = expand_tc_max_jobs();
         for (int j0 = 0; j0 < n; j0 += mj)
-            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi);
+            expand_tc_jobs(cs, jobs.data() + j0, std::min(mj, n - j0), 0, P.nch, ctxs[0]->d_err.p, P.nepi, P.vec);
     } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
@@ -1553,36 +1562,37 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         c->tune_lb = t.lb;
         c->tune_nch = t.nch;
         c->tune_nepi = t.nepi;
-        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2);
+        c->tune_vec = t.vec;
+        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);
         c->sp32.xdirect = t.xd;
         c->tuned = true;
         alloc_fast32(c);
     }
-    // one (time chunk, epilogue warps) pair for the shared expansion launch: the one most of the
-    // grid points asked for
-    std::map<std::pair<int, int>, double> votes;
+    // one (time chunk, epilogue warps, store width) for the shared expansion launch: the one most
+    // of the grid points asked for
+    std::map<std::tuple<int, int, int>, double> votes;
     for (int i = 0; i < n; ++i) {
         const wt_grid& g = ctxs[i]->grid;
-        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi}] += (double)g.Nx * g.Ny * g.Nz;
+        votes[{ctxs[i]->tune_nch, ctxs[i]->tune_nepi, ctxs[i]->tune_vec}] += (double)g.Nx * g.Ny * g.Nz;
     }
-    int nch = 256, nepi = 8;
+    int nch = 256, nepi = 8, vec = 4;
     double top = -1;
     for (auto& v : votes)
         if (v.second > top) {
             top = v.second;
-            nch = v.first.first;
-            nepi = v.first.second;
+            std::tie(nch, nepi, vec) = v.first;
         }
     std::vector<BatchEntry> want;
     for (int i = 0; i < n; ++i) want.push_back(entry_of(ctxs[i], H[i]));
     BatchPlan* plan = nullptr;
     for (auto& p : c0->plans)
-        if (p->nch == nch && p->nepi == nepi && p->ents == want) plan = p.get();
+        if (p->nch == nch && p->nepi == nepi && p->vec == vec && p->ents == want) plan = p.get();
     if (!plan) {
         auto P = std::make_unique<BatchPlan>();
         P->ents = want;
         P->nch = nch;
         P->nepi = nepi;
+        P->vec = vec;
         capture_batch(*P, ctxs, n, reinterpret_cast<float* const*>(H));
         if (c0->plans.size() >= 4) {         // keep the four most recently used graphs
             auto old = std::min_element(c0->plans.begin(), c0->plans.end(),
@@ -1762,18 +1772,19 @@ wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* cons
     });
 }
 
-wt_status wt_get_tuning(wt_ctx* ctx, int* shape8) {
+wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_get_tuning", [&] {
-        if (!shape8) fail(WT_ERR_ARG, "NULL output");
-        shape8[0] = ctx->tune_nb;
-        shape8[1] = ctx->tune_lb;
-        shape8[2] = ctx->tune_nch;
-        shape8[3] = ctx->tune_nepi;
-        shape8[4] = ctx->sp_ready ? ctx->sp32.rxy : 0;
-        shape8[5] = ctx->sp_ready ? ctx->sp32.rz : 0;
-        shape8[6] = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
-        shape8[7] = ctx->sp_ready ? (int)ctx->sp32.zsm | ((int)ctx->sp32.ysm << 1) : 0;
+        if (!out) fail(WT_ERR_ARG, "NULL output");
+        out->nb = ctx->tune_nb;
+        out->lb = ctx->tune_lb;
+        out->nch = ctx->tune_nch;
+        out->nepi = ctx->tune_nepi;
+        out->r_xy = ctx->sp_ready ? ctx->sp32.rxy : 0;
+        out->r_z = ctx->sp_ready ? ctx->sp32.rz : 0;
+        out->x_direct = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
+        out->two_pass = ctx->sp_ready ? (int)ctx->sp32.zsm | ((int)ctx->sp32.ysm << 1) | ((int)ctx->sp32.xsm << 2) : 0;
+        out->store_vec = ctx->tune_vec;
     });
 }
 

@@ -164,8 +164,8 @@ void expand_tc(cudaStream_t s, const float* E, int r_pad, int r, const float* W,
                int* d_err);
 // Several expansions in one persistent launch (at most max_ctas CTAs, 0 = one
 // per SM; nch = time samples per accumulator chunk: 64, 128 or 256; nepi =
-// epilogue warps: 8, 12 or 16).
+// epilogue warps: 8, 12 or 16; vec = floats per store: 4, 2 or 1).
 void expand_tc_jobs(cudaStream_t s, const ExpandJob* jobs, int n_jobs, int max_ctas, int nch, int* d_err,
-                    int nepi = 8);
+                    int nepi = 8, int vec = 4);
 
 }  // namespace wt

@@ -81,7 +81,7 @@ def test_tuned_shapes_are_candidates(P, torch, small_batch):
     for s in sens:
         t = s.tuning()
         assert t["nb"] in (1, 2, 4) and t["lb"] in (16, 32, 64) and t["nch"] in (64, 128, 256)
-        assert t["nepi"] in (8, 16)
+        assert t["nepi"] in (8, 12, 16) and t["store_vec"] in (1, 2, 4)
 
 
 def test_batch_fp64_equals_plain(P, torch, small_batch):

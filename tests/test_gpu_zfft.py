@@ -1,8 +1,8 @@
 """Every FFT variant of the FP32 path, forced through WT_LAUNCH_SHAPES:
 the z pass by the register FFT at each lane count and by the two-pass
-shared-memory FFT (Nz = 64, 128, 256), and the y transforms of the plane
-pass by the register FFT and by the two-pass FFT (Ny = 64, 128) at
-16 and 32 lanes per x line, against the FP64 plain path of the same
+shared-memory FFT (Nz = 64, 128, 256), the y transforms of the plane pass
+by the register FFT and by the two-pass FFT (Ny = 64, 128) at 16 and 32
+lanes per x line, and two-pass x transforms on top, against the FP64 plain path of the same
 context (itself checked against the oracle, here for Nz = 64 and in
 test_gpu_c1 / test_gpu_edges)."""
 import numpy as np
@@ -93,3 +93,28 @@ def test_two_pass_y_transforms_match_fp64(P, torch, monkeypatch, n):
             e = rel_l2(H32, H64)
             print("n", n, "r_xy", rxy, "x_direct", xd, "rel L2", e)
             assert e < 1e-5, (n, rxy, xd, e)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_two_pass_x_transforms_match_fp64(P, torch, monkeypatch, n):
+    """Two-pass y and x transforms (mask 6), with the register and the
+    two-pass z pass (mask 7)."""
+    n_t = {64: 3, 128: 2}[n]
+    w = W.tiny_cell(nx=n, nz=64, n_t=n_t, pitch=55 * UM * n / 32, radius=5 * UM)
+    H64 = None
+    for mask in (6, 7):
+        monkeypatch.setenv("WT_LAUNCH_SHAPES", f"1,32,256,8,{n // 32},2,1,{mask}")
+        s = P.Sensor(w.grid, w.columns)
+        try:
+            s.fit()
+            s.relax(w.times)
+            if H64 is None:
+                H64 = s.extend("fp64").cpu().numpy()
+            H32 = s.extend("fp32").double().cpu().numpy()
+            t = s.tuning()
+        finally:
+            s.close()
+        assert t["two_pass"] == mask
+        e = rel_l2(H32, H64)
+        print("n", n, "mask", mask, "rel L2", e)
+        assert e < 1e-5, (n, mask, e)
