@@ -37,24 +37,29 @@ __global__ void f32_tables_kernel(const double* __restrict__ xy, int n_cols, int
 }
 
 // rho^ planes; grid (Nz, nb, F32_DEP_SPLIT): each block takes a slice of the
-// m_x rows of one plane (warps over 2-row x 64-column tiles, lanes over m_y).  Shared tables:
-// px[c][mx] = e^{-i kx x_c} (the block's rows), qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
-constexpr int F32_DEP_SPLIT = 5;
+// m_x rows 0 <= m_x < Nx/2 of one plane (the x Nyquist row is never read: the
+// plane pass keeps it zero), warps over 4-row x 64-column tiles, lanes over m_y.
+// Shared tables: px[c][mx] = e^{-i kx x_c} (the block's rows),
+// qy[c][my] = e^{-i ky y_c} Zc[b][c][mz].
+constexpr int F32_DEP_SPLIT = 4;
+__host__ __device__ inline int deposit_rows(int nx) {          // rows per block, a multiple of 4
+    return (((nx / 2 + F32_DEP_SPLIT - 1) / F32_DEP_SPLIT) + 3) & ~3;
+}
 __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __restrict__ phx,
                                    const C2<float>* __restrict__ phy, const float* __restrict__ Zc,
                                    C2<float>* __restrict__ rho) {
     extern __shared__ unsigned char smem_raw[];
     const int mz = blockIdx.x, b = blockIdx.y;
-    const int nxh = g.Nx / 2 + 1, ny = g.Ny;
-    const int rows = (nxh + F32_DEP_SPLIT - 1) / F32_DEP_SPLIT;
-    const int mx0 = blockIdx.z * rows, mx1 = min(nxh, mx0 + rows);
+    const int nxh = g.Nx / 2 + 1, nxq = g.Nx / 2, ny = g.Ny;
+    const int rows = deposit_rows(g.Nx);
+    const int mx0 = blockIdx.z * rows, mx1 = min(nxq, mx0 + rows);
     if (mx0 >= mx1) return;
     const int nr = mx1 - mx0;
     C2<float>* px = reinterpret_cast<C2<float>*>(smem_raw);        // [n_cols][rows]
     C2<float>* qy = px + (size_t)n_cols * rows;                      // [n_cols][ny]
-    for (int e = threadIdx.x; e < n_cols * nr; e += blockDim.x) {
-        const int c = e / nr, r = e - c * nr;
-        px[c * rows + r] = phx[c * nxh + mx0 + r];
+    for (int e = threadIdx.x; e < n_cols * rows; e += blockDim.x) {
+        const int c = e / rows, r = e - c * rows;
+        px[e] = r < nr ? phx[c * nxh + mx0 + r] : C2<float>{0.f, 0.f};
     }
     for (int e = threadIdx.x; e < n_cols * ny; e += blockDim.x) {
         const float z = Zc[((size_t)b * n_cols + e / ny) * g.Nz + mz];
@@ -64,31 +69,34 @@ __global__ void f32_deposit_kernel(GridDev g, int n_cols, const C2<float>* __res
     __syncthreads();
     C2<float>* out = rho + ((size_t)b * g.Nz + mz) * nxh * ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    // register tiles of 2 rows x 2 columns per lane (64-column chunks): per column 2 broadcast
-    // loads of px and 2 loads of qy feed 4 complex multiply-adds
-    const int n_rp = (nr + 1) / 2, n_ch = (ny + 63) / 64;
-    for (int item = warp; item < n_rp * n_ch; item += nw) {
-        const int r = 2 * (item / n_ch), my = (item % n_ch) * 64 + lane;
-        const bool r1 = r + 1 < nr, c0 = my < ny, c1 = my + 32 < ny;
-        C2<float> a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
+    // register tiles of 4 rows x 2 columns per lane (64-column chunks): per column 4 broadcast
+    // loads of px (zero past the block's rows) and 2 loads of qy feed 8 complex multiply-adds
+    const int n_rq = (nr + 3) / 4, n_ch = (ny + 63) / 64;
+    for (int item = warp; item < n_rq * n_ch; item += nw) {
+        const int r = 4 * (item / n_ch), my = (item % n_ch) * 64 + lane;
+        const bool c0 = my < ny, c1 = my + 32 < ny;
+        C2<float> a[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i][0] = a[i][1] = C2<float>{0.f, 0.f};
         const C2<float>* pr = px + r;
         const C2<float>* qm = qy + my;
-#pragma unroll 6
+#pragma unroll 3
         for (int c = 0; c < n_cols; ++c) {
-            const C2<float> p0 = pr[c * rows], p1 = r1 ? pr[c * rows + 1] : C2<float>{0.f, 0.f};
             const C2<float> q0 = c0 ? qm[c * ny] : C2<float>{0.f, 0.f};
             const C2<float> q1 = c1 ? qm[c * ny + 32] : C2<float>{0.f, 0.f};
-            a00 = {fmaf(p0.x, q0.x, fmaf(-p0.y, q0.y, a00.x)), fmaf(p0.x, q0.y, fmaf(p0.y, q0.x, a00.y))};
-            a01 = {fmaf(p0.x, q1.x, fmaf(-p0.y, q1.y, a01.x)), fmaf(p0.x, q1.y, fmaf(p0.y, q1.x, a01.y))};
-            a10 = {fmaf(p1.x, q0.x, fmaf(-p1.y, q0.y, a10.x)), fmaf(p1.x, q0.y, fmaf(p1.y, q0.x, a10.y))};
-            a11 = {fmaf(p1.x, q1.x, fmaf(-p1.y, q1.y, a11.x)), fmaf(p1.x, q1.y, fmaf(p1.y, q1.x, a11.y))};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const C2<float> p = pr[c * rows + i];
+                a[i][0] = {fmaf(p.x, q0.x, fmaf(-p.y, q0.y, a[i][0].x)), fmaf(p.x, q0.y, fmaf(p.y, q0.x, a[i][0].y))};
+                a[i][1] = {fmaf(p.x, q1.x, fmaf(-p.y, q1.y, a[i][1].x)), fmaf(p.x, q1.y, fmaf(p.y, q1.x, a[i][1].y))};
+            }
         }
-        C2<float>* o0 = out + (size_t)(mx0 + r) * ny + my;
-        if (c0) o0[0] = a00;
-        if (c1) o0[32] = a01;
-        if (r1) {
-            if (c0) o0[ny] = a10;
-            if (c1) o0[ny + 32] = a11;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (r + i >= nr) break;
+            C2<float>* o = out + (size_t)(mx0 + r + i) * ny + my;
+            if (c0) o[0] = a[i][0];
+            if (c1) o[32] = a[i][1];
         }
     }
 }
@@ -103,8 +111,7 @@ __global__ void f32_twiddle_kernel(float* tw, int N) {
 }
 
 static size_t deposit_smem(const GridDev& g, int n_cols) {
-    const int rows = (g.Nx / 2 + 1 + F32_DEP_SPLIT - 1) / F32_DEP_SPLIT;
-    return (size_t)n_cols * (rows + g.Ny) * sizeof(C2<float>);
+    return (size_t)n_cols * (deposit_rows(g.Nx) + g.Ny) * sizeof(C2<float>);
 }
 
 

@@ -11,13 +11,12 @@ namespace wt {
 // Register-FFT lengths compiled in: elements per lane R = N / W.
 #define WT_FOR_EACH_R(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(24)
 
-// Two-pass y transforms of Ny = ny2 in {64, 128, 256}: ny2 = A B with A lanes per row
-// (A = 16 for 256, else 8); each row holds the A x (B + 1) exchange matrix.
+// Two-pass y transforms of Ny = ny2 in {64, 128}: ny2 = A B with A = 8 lanes per row; each
+// row holds the A x B exchange matrix (skewed, no padding).
 __host__ __device__ constexpr int plane_y2_a(int ny2) { return ny2 == 256 ? 16 : 8; }
-// odd row pitch (complex units): Ny + 1 entries, or the two-pass exchange matrix
-__host__ __device__ constexpr int plane_ldp_of(int ny, int ny2) {
-    return ny2 ? (plane_y2_a(ny2) * (ny2 / plane_y2_a(ny2) + 1)) | 1 : (ny + 1) | 1;
-}
+// odd row pitch (complex units, Ny + 1 entries; = 1 mod 16 for the power-of-two Ny of the
+// two-pass forms)
+__host__ __device__ constexpr int plane_ldp_of(int ny, int ny2) { return (void)ny2, (ny + 1) | 1; }
 inline size_t plane_smem(const GridDev& g, int ny2 = 0) {
     const int nxh = g.Nx / 2 + 1;
     return ((size_t)nxh * plane_ldp_of(g.Ny, ny2) + g.Ny + g.Nx + ny2) * sizeof(C2<float>);

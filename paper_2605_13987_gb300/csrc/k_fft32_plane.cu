@@ -100,12 +100,14 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
     } else {
         // two-pass y transforms, Ny = YA YB: lane a of a row's YA lanes takes m_y = a + YA j
         // (a YB-point DFT over j, twiddles w_ny^{a c}, the matrix to the row's own
-        // storage), then YB / YA YA-point DFTs per lane; Y[y] at column y.
+        // storage, entry (a, c) at a YB + ((a + c) mod YB)), then YB / YA YA-point DFTs per
+        // lane; Y[y] at column y.  The four rows of a warp are 8 apart: with the pitch = 1
+        // mod 16 the two rows of a half-warp fall into disjoint bank halves.
         // (no prefetch of the next row here: the YB inputs would double the live registers)
-        constexpr int GY = 32 / YA;
+        static_assert(YA == 8, "the row mapping assumes 8 lanes per line");
         const int grp = lane / YA, gl = lane % YA;
-        for (int base = warp * GY; base < nxq; base += 8 * GY) {
-            const int mx = base + grp;
+        for (int k0 = 0; k0 < nxq; k0 += 32) {
+            const int mx = k0 + warp + 8 * grp;
             const bool act = mx < nxq;
             const float kx = ckx * mx;
             const float fold = mx ? 2.f : 1.f;
@@ -121,14 +123,15 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
             for (int c = 1; c < YB; ++c) v[c] = cmul(v[c], tl[c * YA + gl]);
             if (act)
 #pragma unroll
-                for (int c = 0; c < YB; ++c) row[gl * (YB + 1) + c] = v[c];
+                for (int c = 0; c < YB; ++c) row[gl * YB + ((gl + c) & (YB - 1))] = v[c];
             __syncwarp();
             C2<float> o[YB];
 #pragma unroll
             for (int r = 0; r < YB / YA; ++r) {
                 C2<float> u[YA];
 #pragma unroll
-                for (int a = 0; a < YA; ++a) u[a] = act ? row[a * (YB + 1) + gl + YA * r] : C2<float>{0.f, 0.f};
+                for (int a = 0; a < YA; ++a)
+                    u[a] = act ? row[a * YB + ((a + gl + YA * r) & (YB - 1))] : C2<float>{0.f, 0.f};
                 reg_dft_c<YA>(u);
 #pragma unroll
                 for (int d = 0; d < YA; ++d) o[r * YA + d] = u[d];
@@ -145,12 +148,14 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
     if constexpr (X2) {
         // two-pass x transforms of Nx = YA YB, two real lines (ya, yb) per complex FFT with the
         // Hermitian completion of the register path below; pass 1 reads the pair's columns, then
-        // holds the YA x YB exchange matrix there (slot k = a + YA c at row k / 2, column
-        // (k odd ? yb : ya); the pair's rows 0..nx/2 - 1 of both columns hold nx slots)
-        constexpr int GX = 32 / YA;
+        // holds the YA x YB exchange matrix there: entry (a, c) at slot s = 8 c + ((a + c) mod 8)
+        // < Nx, row s mod (Nx/2) of column ya (s < Nx/2) or yb (rows 0..Nx/2 - 1 of both
+        // columns; the plane has Nx/2 + 1 rows).  The pairs of a half-warp are 4 apart
+        // (columns 8 apart): disjoint bank halves.
+        static_assert(YA == 8, "the pair mapping assumes 8 lanes per line");
         const int grp = lane / YA, gl = lane % YA;
-        for (int base = warp * GX; base < ny / 2; base += 8 * GX) {
-            const int pp = base + grp;
+        for (int k0 = 0; k0 < ny / 2; k0 += 32) {
+            const int pp = k0 + 16 * (warp >> 2) + (warp & 3) + 4 * grp;
             const bool act = pp < ny / 2;
             const int ya = 2 * pp, yb = ya + 1;
             const int ca = act ? ya : 0, cb = act ? yb : 0;
@@ -176,17 +181,20 @@ __global__ void __launch_bounds__(256, RX <= 5 ? 3 : 2) f32_plane_kernel(GridDev
             reg_dft_c<YB>(v);
 #pragma unroll
             for (int c = 1; c < YB; ++c) v[c] = cmul(v[c], tl[c * YA + gl]);
-            auto slot = [&](int k) -> C2<float>& { return P[(k >> 1) * ldp + ((k & 1) ? cb : ca)]; };
+            auto slot = [&](int a, int c) -> C2<float>& {
+                const int sl = 8 * c + ((a + c) & 7);
+                return P[(sl & (nxq - 1)) * ldp + (sl < nxq ? ca : cb)];     // nx a power of two
+            };
             if (act)
 #pragma unroll
-                for (int c = 0; c < YB; ++c) slot(gl + YA * c) = v[c];
+                for (int c = 0; c < YB; ++c) slot(gl, c) = v[c];
             __syncwarp();
             C2<float> o[YB];
 #pragma unroll
             for (int r = 0; r < YB / YA; ++r) {
                 C2<float> u[YA];
 #pragma unroll
-                for (int a = 0; a < YA; ++a) u[a] = act ? slot(a + YA * (gl + YA * r)) : C2<float>{0.f, 0.f};
+                for (int a = 0; a < YA; ++a) u[a] = act ? slot(a, gl + YA * r) : C2<float>{0.f, 0.f};
                 reg_dft_c<YA>(u);
 #pragma unroll
                 for (int d = 0; d < YA; ++d) o[r * YA + d] = u[d];
