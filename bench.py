@@ -48,6 +48,8 @@ WORKLOADS = {
             "grid 20x20x64, 18 columns, 256 time samples, 1000 tracks of 100 steps through the central pixel; "
             "per variant fit, relaxation, currents with their four parameter tangents, CR-RC^2 shaping, "
             "signal features and their sensitivities",
+    "c5": "c5: 5x5 pixel cell 275x275x500 um, grid 192x192x384, 50 columns x 256 sources, 256 time samples "
+          "(H 43.5 GB), Eq. 1 against 1e5 electron/hole drift tracks of 200 steps",
     "c3": "c3: 64 single cells, pitch 40-110 um, thickness 300-500 um, radius 4-10 um, grids 64^2x128 to "
           "128^2x256 (uneven), 256 time samples each; batched in waves through an H arena",
 }
@@ -348,6 +350,100 @@ def run_adjoint(args):
     return 0
 
 
+def run_large(args):
+    """c5: the largest single-GPU case.  A step is one FP32 extension (H 43.5 GB in HBM) followed
+    by Eq. 1 for 1e5 drift tracks.  The oracle cannot solve this size in a test, so the line
+    carries full-size checks on the GPU: the FP32 field against the FP64 plain path over the
+    whole of H, and the FP64 grid against the exact point evaluation at sampled grid points."""
+    import numpy as np
+    import torch
+    import paper_2605_13987_gb300 as P
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load_library()
+    w = make_workload("c5")
+    g = w.grid
+    npts = g.Nx * g.Ny * g.Nz
+    nt = len(w.times)
+    tr = w.tracks
+    t0 = time.perf_counter()
+    sen = P.Sensor(w.grid, w.columns, device=local)
+    cond = sen.fit()
+    sen.relax(w.times)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    info = sen.info()
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    tracks = dict(n_tracks=tr.n_tracks, n_steps=tr.n_steps, n_out=tr.n_out, dt=tr.dt, charge=1.0,
+                  x=d(tr.x), y=d(tr.y), z=d(tr.z), vx=d(tr.vx), vy=d(tr.vy), vz=d(tr.vz), q=d(tr.charge))
+    H = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, device=dev)
+    cur = torch.empty((tr.n_tracks, tr.n_out), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sen.extend("fp32", out=H)
+        sen.eq1(H, tracks, out=cur)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            ev[3 * k].record(stream)
+            sen.extend("fp32", out=H)
+            ev[3 * k + 1].record(stream)
+            sen.eq1(H, tracks, out=cur)
+            ev[3 * k + 2].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ext_ms = statistics.median(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps))
+    eq1_ms = statistics.median(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps))
+    step_ms = max_over_ranks(ext_ms + eq1_ms, world)
+    # full-size checks: FP32 against the FP64 plain path (whole H, per time sample), FP64 grid
+    # values against the exact point evaluation at sampled grid points
+    checks = {}
+    if rank == 0:
+        H64 = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float64, device=dev)
+        a = time.perf_counter()
+        sen.extend("fp64", out=H64)
+        torch.cuda.synchronize()
+        fp64_s = time.perf_counter() - a
+        num = den = 0.0
+        for t in range(nt):
+            diff = H[t].double() - H64[t]
+            num += float((diff * diff).sum())
+            den += float((H64[t] * H64[t]).sum())
+        checks["fp32_vs_fp64_rel_l2"] = (num / den) ** 0.5
+        rng = np.random.default_rng(5)
+        ix, iy, iz = rng.integers(0, g.Nx, 64), rng.integers(0, g.Ny, 64), rng.integers(0, g.Nz, 64)
+        ts = np.sort(rng.choice(nt, 4, replace=False))
+        xyz = np.stack([ix * g.Lx / g.Nx, iy * g.Ly / g.Ny, (iz + 0.5) * g.Lz / g.Nz], axis=1)
+        exact = sen.sample_H(xyz, w.times[ts])                     # [4][64][3]
+        grid = H64[torch.as_tensor(ts, device=dev)][:, :, ix, iy, iz].permute(0, 2, 1).cpu().numpy()
+        checks["fp64_grid_vs_point_rel_l2"] = float(np.linalg.norm(grid - exact) / np.linalg.norm(exact))
+        checks["fp64_plain_s"] = fp64_s
+        checks["eq1_finite"] = bool(torch.isfinite(cur).all())
+        del H64
+    if rank == 0:
+        ps = npts * nt
+        line = {"metric": "H grid-point*time-samples/sec (FP32 extension) with Eq. 1 for 1e5 drift tracks per step",
+                "value": world * ps / (step_ms / 1e3), "unit": "point-samples/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["c5"], "grid_points": npts, "time_samples": nt,
+                           "tracks": tr.n_tracks, "rank": info["rank"],
+                           "l2": "inputs and outputs (43.5 GB of H) far above L2"},
+                "stage_ms": {"extension": ext_ms, "eq1": eq1_ms},
+                "extension_frac_of_hbm_roof": 12.0 * ps / (ext_ms / 1e3) / 1e9 / peaks()[0],
+                "checks": checks, "tuning": sen.tuning(), "clocks": clk.summary(local), "setup_s": setup,
+                "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    sen.close()
+    return 0
+
+
 def run_scan_bench(args):
     """Sec. 5's bias-diameter scan through the scan driver: a step is the
     whole scan (five variants: fit, relaxation, currents and tangents,
@@ -582,6 +678,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "scan":
         return run_scan_bench(args)
+    if args.workload == "c5":
+        return run_large(args)
     return run_ours(args)
 
 

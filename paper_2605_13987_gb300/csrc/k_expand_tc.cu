@@ -447,29 +447,25 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
 #pragma unroll
                         for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(h ? rb[e] : ra[e]);
                         const int t0 = ch * nch + (h ? j2 : j) + (lane & (VEC - 1));
-                        if constexpr (VEC == 4) {
-                            quad_transpose(v, lane);
-                            if (in) {
+                        // rows t0 + VEC k (k < 32 / VEC) of this lane; all of them exist unless the
+                        // slice reaches past nt (then each store is checked)
+                        const bool full = t0 + 32 - VEC < nt;
+                        const size_t rs = (size_t)VEC * 3 * npts;      // row step between stores
+                        float* hr = hp + (size_t)t0 * 3 * npts;
+                        if constexpr (VEC == 4) quad_transpose(v, lane);
+                        else if constexpr (VEC == 2) pair_transpose(v, lane);
+                        if (in) {
 #pragma unroll
-                                for (int bb = 0; bb < 8; ++bb)
-                                    if (t0 + 4 * bb < nt)
-                                        *reinterpret_cast<float4*>(hp + (size_t)(t0 + 4 * bb) * 3 * npts) =
-                                            make_float4(v[4 * bb], v[4 * bb + 1], v[4 * bb + 2], v[4 * bb + 3]);
-                            }
-                        } else if constexpr (VEC == 1) {
-                            if (in) {
-#pragma unroll
-                                for (int e = 0; e < 32; ++e)
-                                    if (t0 + e < nt) hp[(size_t)(t0 + e) * 3 * npts] = v[e];
-                            }
-                        } else {
-                            pair_transpose(v, lane);
-                            if (in) {
-#pragma unroll
-                                for (int bb = 0; bb < 16; ++bb)
-                                    if (t0 + 2 * bb < nt)
-                                        *reinterpret_cast<float2*>(hp + (size_t)(t0 + 2 * bb) * 3 * npts) =
-                                            make_float2(v[2 * bb], v[2 * bb + 1]);
+                            for (int k = 0; k < 32 / VEC; ++k) {
+                                if (!full && t0 + VEC * k >= nt) break;
+                                float* dst = hr + k * rs;
+                                if constexpr (VEC == 4)
+                                    *reinterpret_cast<float4*>(dst) =
+                                        make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                                else if constexpr (VEC == 2)
+                                    *reinterpret_cast<float2*>(dst) = make_float2(v[2 * k], v[2 * k + 1]);
+                                else
+                                    *dst = v[k];
                             }
                         }
                     }

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
         const bool lin = L0 + l < nxy;
         const float* sp = R + ((size_t)b * 3 + comp) * N * nxy + L0 + l;
         float* dst = reinterpret_cast<float*>(cs) + 2 * (size_t)(l >> 1) * S + (l & 1);
-#pragma unroll 8
+#pragma unroll 16
         for (int m = m0; m < N; m += MS) dst[2 * m] = lin ? sp[(size_t)m * nxy] : 0.f;
     }
     __syncthreads();
