@@ -203,6 +203,20 @@ wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, 
 #define WT_EQ1_NOALLOC_MAX_OUT 16384
 wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tracks, float* i, void* cuda_stream);
 
+/* Eq. 1 without writing H: the currents of wt_eq1 on wt_extend(WT_FP32)'s
+ * field, computed from the rank-r form that the extension expands,
+ * H[t][c][p] = sum_m W[t][m] E_m[c][p].  Interpolation is linear, so per
+ * track step the r basis fields are interpolated once (r x 24 gathers
+ * instead of n_t x 24 from H) and combined with the time coefficients;
+ * lags, accumulation and currents as in wt_eq1.  Equal to wt_eq1 on the
+ * FP32 H up to FP32 rounding.  The basis fields are computed when the
+ * context does not hold them already (after wt_relax, or after another
+ * call overwrote them).  Track arrays and i: host or device memory (as in
+ * wt_eq1).  Ordered after the caller's work on cuda_stream; returns when i
+ * is written.  Shares the FP32 work buffers of wt_extend and wt_batch_run:
+ * do not run them concurrently on one context. */
+wt_status wt_eq1_direct(wt_ctx* ctx, const wt_tracks* tracks, float* i, void* cuda_stream);
+
 /* Loss of Eq. 1 currents, L = mean over tracks and output times of i(tau)^2
  * (Sec. 4's current of each track with its own charge, Eq. 1), computed in
  * one call: the field of the relaxed charges (WT_FP32: the fast path of

@@ -9,7 +9,7 @@ load the library; the first call does, and fails if it was not built.
 from ._binding import (  # noqa: F401
     WTError, load_library, LIB_PATH,
     WT_FP32, WT_FP64,
-    wt_create, wt_add_columns, wt_fit, wt_relax, wt_extend, wt_sample_H, wt_eq1, wt_eq1_noalloc,
+    wt_create, wt_add_columns, wt_fit, wt_relax, wt_extend, wt_sample_H, wt_eq1, wt_eq1_noalloc, wt_eq1_direct,
     wt_eq1_loss, wt_eq1_loss_grad, wt_batch_run, wt_get_tuning,
     wt_set_resistivity_profile, wt_eq1_loss_grad_profile, wt_shape, wt_static_field, wt_drift, wt_sync,
     wt_eq1_tangents, wt_features, WT_N_FEATURES, FEATURE_NAMES,

@@ -84,6 +84,7 @@ SIGNATURES = {
                               C.POINTER(C.c_double)]),
     "wt_eq1": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
     "wt_eq1_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
+    "wt_eq1_direct": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.c_void_p, C.c_void_p]),
     "wt_eq1_loss": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(wt_tracks), C.POINTER(C.c_double)]),
     "wt_eq1_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(wt_tracks), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]),
@@ -234,6 +235,14 @@ def wt_eq1_noalloc(ctx, H, tracks, i_out, stream=None):
     lib = load_library()
     tr = _tracks_struct(tracks)
     _check(lib.wt_eq1_noalloc(ctx, _ptr(H), C.byref(tr), _ptr(i_out), _stream_handle(stream)), ctx)
+
+
+def wt_eq1_direct(ctx, tracks, i_out, stream=None):
+    """Eq. 1 currents from the context's rank-r field form, without H."""
+    lib = load_library()
+    tr = _tracks_struct(tracks)
+    st = _stream_handle(stream) if (hasattr(i_out, "is_cuda") and i_out.is_cuda) else None
+    _check(lib.wt_eq1_direct(ctx, C.byref(tr), _ptr(i_out), st), ctx)
 
 
 def wt_eq1_loss(ctx, precision, tracks):

@@ -123,6 +123,109 @@ void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int n
     eq1_launch_t<double, Eq1Lag64, double>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst,
                                            n_tracks, n_steps, n_out, dt, v_w, lags, out);
 }
+// Eq. 1 straight from the rank-r form of the FP32 field, H[t][c][p] = sum_m W[t][m] E[c][m][p]
+// (the representation the tensor-core expansion writes out): the staged dot products are
+// W(x_j, t_n) . v_j = sum_m W[t_n][m] (E_m(x_j) . v_j), the interpolation being linear, so per
+// track step the r basis fields are interpolated once instead of the field at every time
+// sample (r x 24 gathers from E instead of n_t x 24 from H).  Lags, accumulation and currents
+// as in eq1_kernel.
+__global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict__ E, int r,
+                                                        const float* __restrict__ W32, int Nx, int Ny, int Nz,
+                                                        int nt, float inv_hx, float inv_hy, float inv_hz,
+                                                        const float* __restrict__ X, const float* __restrict__ Y,
+                                                        const float* __restrict__ Z, const float* __restrict__ VX,
+                                                        const float* __restrict__ VY, const float* __restrict__ VZ,
+                                                        const float* __restrict__ qtrack, float qconst, int n_steps,
+                                                        int n_out, double dt, double inv_vw,
+                                                        const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Wt = reinterpret_cast<float*>(smem_raw);                          // [r][nt]
+    float* sv = Wt + (size_t)r * nt;                                         // [EQ1_MC][32]
+    float* f = sv + EQ1_MC * 32;                                             // [EQ1_MC][nt]
+    double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * nt + EQ1_MC * 32 + (size_t)EQ1_MC * nt) *
+                                                        sizeof(float) + 15) & ~(size_t)15));   // [n_out]
+    const int tr = blockIdx.x;
+    const size_t npts = (size_t)Nx * Ny * Nz;
+    for (int e = threadIdx.x; e < r * nt; e += blockDim.x) {
+        const int m = e / nt, n = e - m * nt;
+        Wt[e] = W32[(size_t)n * 32 + m];
+    }
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x) Q[m] = 0.0;
+    for (int c0 = 0; c0 < n_steps; c0 += EQ1_MC) {
+        const int mc = min(EQ1_MC, n_steps - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < mc * r; e += blockDim.x) {
+            const int j = e / r, m = e - j * r;
+            const size_t s = (size_t)tr * n_steps + c0 + j;
+            const float vx = VX[s], vy = VY[s], vz = VZ[s];
+            float acc = 0.f;
+            if (vx != 0.f || vy != 0.f || vz != 0.f) {
+                const float fx = X[s] * inv_hx, fy = Y[s] * inv_hy;
+                float fz = Z[s] * inv_hz - 0.5f;
+                fz = fz < 0.f ? 0.f : (fz > (float)(Nz - 1) ? (float)(Nz - 1) : fz);
+                const float flx = floorf(fx), fly = floorf(fy);
+                const int k0 = min((int)floorf(fz), Nz - 2);
+                const float wx = fx - flx, wy = fy - fly, wz = fz - (float)k0;
+                const int i0 = ((int)flx % Nx + Nx) % Nx, j0 = ((int)fly % Ny + Ny) % Ny;
+                const int i1 = (i0 + 1) % Nx, j1 = (j0 + 1) % Ny;
+                const size_t a00 = ((size_t)i0 * Ny + j0) * Nz + k0, a01 = ((size_t)i0 * Ny + j1) * Nz + k0;
+                const size_t a10 = ((size_t)i1 * Ny + j0) * Nz + k0, a11 = ((size_t)i1 * Ny + j1) * Nz + k0;
+                float w[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float* h = E + ((size_t)c * 32 + m) * npts;
+                    const float v00 = (1.f - wz) * h[a00] + wz * h[a00 + 1];
+                    const float v01 = (1.f - wz) * h[a01] + wz * h[a01 + 1];
+                    const float v10 = (1.f - wz) * h[a10] + wz * h[a10 + 1];
+                    const float v11 = (1.f - wz) * h[a11] + wz * h[a11 + 1];
+                    w[c] = (1.f - wx) * ((1.f - wy) * v00 + wy * v01) + wx * ((1.f - wy) * v10 + wy * v11);
+                }
+                acc = w[0] * vx + w[1] * vy + w[2] * vz;
+            }
+            sv[j * 32 + m] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < mc * nt; e += blockDim.x) {
+            const int j = e / nt, n = e - j * nt;
+            float acc = 0.f;
+            for (int m = 0; m < r; ++m) acc = fmaf(Wt[m * nt + n], sv[j * 32 + m], acc);
+            f[j * nt + n] = acc;
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+            double q = 0.0;
+            const int jmax = min(mc - 1, m - c0);
+            for (int j = 0; j <= jmax; ++j) {
+                const Eq1Lag lg = lags[m - (c0 + j)];
+                q += (double)lg.w0 * (double)f[j * nt + lg.n] + (double)lg.w1 * (double)f[j * nt + min(lg.n + 1, nt - 1)];
+            }
+            Q[m] += q * dt;
+        }
+    }
+    __syncthreads();
+    const float qc = qtrack ? qtrack[tr] : qconst;
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+        const double dq = Q[m] - (m ? Q[m - 1] : 0.0);
+        out[(size_t)tr * n_out + m] = (float)(-(double)qc * inv_vw * dq / dt);
+    }
+}
+
+void eq1_basis_launch(cudaStream_t s, const float* E, int r, const float* W32, int Nx, int Ny, int Nz, int nt,
+                      double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
+                      const float* vx, const float* vy, const float* vz, const float* q, float qconst, int n_tracks,
+                      int n_steps, int n_out, double dt, double v_w, const void* lags, float* out) {
+    if (r < 1 || r > 32) fail(WT_ERR_ARG, "eq1: basis rank out of range");
+    const size_t sh = ((((size_t)r * nt + EQ1_MC * 32 + (size_t)EQ1_MC * nt) * sizeof(float) + 15) & ~(size_t)15) +
+                      (size_t)n_out * sizeof(double);
+    if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
+    allow_dyn_smem(eq1_basis_kernel, sh);
+    if (n_tracks > 0)
+        eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(E, r, W32, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly),
+                                                   (float)(Nz / Lz), x, y, z, vx, vy, vz, q, qconst, n_steps, n_out,
+                                                   dt, 1.0 / v_w, static_cast<const Eq1Lag*>(lags), out);
+    WT_LAUNCH("eq1_basis");
+}
+
 size_t eq1_lag_size() { return sizeof(Eq1Lag); }
 void eq1_pack_lag(void* dst, int n, float w0, float w1) { *static_cast<Eq1Lag*>(dst) = Eq1Lag{n, w0, w1}; }
 size_t eq1_lag64_size() { return sizeof(Eq1Lag64); }

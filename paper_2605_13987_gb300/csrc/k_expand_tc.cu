@@ -12,8 +12,8 @@
 // shared memory for the whole kernel.  Three tcgen05.mma products
 // (hi*hi + hi*lo + lo*hi, kind::tf32, FP32 accumulation in tensor memory)
 // give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
-// grid point, column = time sample), double buffered in two 256-column
-// halves; eight, twelve or sixteen epilogue warps (two to four per TMEM lane
+// grid point, column = time sample), in 512 / chunk buffers of one chunk
+// each (2, 4 or 8) so that the MMAs run ahead of the epilogue; eight, twelve or sixteen epilogue warps (two to four per TMEM lane
 // quadrant, alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
 // lane quads by shuffles and write H with 16-byte stores: each warp store
 // covers 4 time samples x 32 consecutive grid points (four full 128-byte
@@ -48,7 +48,8 @@ namespace tc {
 constexpr int BM = 128;            // grid points per unit (TMEM lanes)
 // epilogue warps: a template parameter of the kernel (8 or 16, chosen by the autotuner)
 constexpr int KR = 32;             // basis rank (TF32 elements per 128-byte row)
-constexpr int NCH = 256;           // time samples per accumulator half (at most; the chunk is a launch argument)
+constexpr int NCH = 256;           // default time samples per accumulator chunk (a launch argument: 64, 128, 256)
+constexpr int TMEM_COLS = 512;     // allocated accumulator columns: 512 / chunk buffers
 constexpr int TILE_BYTES = BM * 128;  // one 128 x 32 TF32 tile
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 constexpr int MAX_JOBS = 64;       // expansion jobs per launch
@@ -202,7 +203,7 @@ __device__ __forceinline__ void quad_transpose(float (&v)[32], int lane) {
 struct Smem {
     // tiles first (1024-byte aligned base):
     // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo], raw[2][32][128] FP32
-    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain, b_free;
+    unsigned long long a_full[2], a_empty[2], acc_full[8], acc_empty[8], raw_full[2], drain, b_free;
     unsigned tmem_base;
     int abort_flag;
 };
@@ -273,9 +274,11 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S->a_full[i], 32);
             mbar_init(&S->a_empty[i], 1);
+            mbar_init(&S->raw_full[i], 1);
+        }
+        for (int i = 0; i < 8; ++i) {
             mbar_init(&S->acc_full[i], 1);
             mbar_init(&S->acc_empty[i], 32 * NEPI);
-            mbar_init(&S->raw_full[i], 1);
         }
         mbar_init(&S->drain, 1);
         mbar_init(&S->b_free, 1);
@@ -285,13 +288,14 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     load_coeffs(J.W[job0], J.nt[job0], pad32(J.nt[job0]), b_hi, b_lo, threadIdx.x, blockDim.x);
     fence_proxy_async();
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&S->tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)), "n"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         tc_fence_before();
     }
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = S->tmem_base;
+    const int nbuf = TMEM_COLS / nch;        // accumulator chunk buffers in tensor memory (8, 4 or 2)
     volatile int* abort_flag = &S->abort_flag;
 
     if (warp == 0) {
@@ -373,8 +377,8 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             const unsigned a_hi = smem_u32(a_tiles + (size_t)(2 * st) * TILE_BYTES);
             const unsigned a_lo = a_hi + TILE_BYTES;
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
-                const int b = g & 1;
-                if (!mbar_wait(&S->acc_empty[b], ((g >> 1) & 1) ^ 1, abort_flag, d_err)) { ok = false; break; }
+                const int b = g % nbuf;
+                if (!mbar_wait(&S->acc_empty[b], ((g / nbuf) & 1) ^ 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
                 const int n = min(nch, nt_pad - ch * nch);
                 const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) |
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 if (lane == 0) {
                     const unsigned bh = smem_u32(b_hi + (size_t)ch * nch * 128);
                     const unsigned bl = smem_u32(b_lo + (size_t)ch * nch * 128);
-                    const unsigned d = tmem + (unsigned)(b * NCH);
+                    const unsigned d = tmem + (unsigned)(b * nch);
 #pragma unroll
                     for (int ks = 0; ks < KR / 8; ++ks) {
                         const unsigned off = ks * 32;   // 8 TF32 = 32 bytes along K
@@ -428,8 +432,8 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             const bool in = p4 < npts;                 // npts is a multiple of 4
             float* hp = J.H[cur] + (size_t)c * npts + p4;
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
-                const int b = g & 1;
-                if (!mbar_wait(&S->acc_full[b], (g >> 1) & 1, abort_flag, d_err)) { ok = false; break; }
+                const int b = g % nbuf;
+                if (!mbar_wait(&S->acc_full[b], (g / nbuf) & 1, abort_flag, d_err)) { ok = false; break; }
                 tc_fence_after();
                 const int n = min(nch, nt_pad - ch * nch);
                 // two 32-column slices per round: both TMEM loads in flight before one wait
@@ -437,8 +441,8 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                     const int j2 = j + 32 * NSL;
                     const bool two = j2 < n;
                     unsigned ra[32], rb[32];
-                    tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j), ra);
-                    if (two) tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * NCH + j2), rb);
+                    tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * nch + j), ra);
+                    if (two) tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * nch + j2), rb);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
     }
 }
 

@@ -16,7 +16,7 @@ namespace wt {
 __host__ __device__ constexpr int plane_y2_a(int ny2) { return ny2 == 256 ? 16 : 8; }
 // odd row pitch (complex units, Ny + 1 entries; = 1 mod 16 for the power-of-two Ny of the
 // two-pass forms)
-__host__ __device__ constexpr int plane_ldp_of(int ny, int ny2) { return (void)ny2, (ny + 1) | 1; }
+__host__ __device__ constexpr int plane_ldp_of(int ny, int /*ny2*/) { return (ny + 1) | 1; }
 inline size_t plane_smem(const GridDev& g, int ny2 = 0) {
     const int nxh = g.Nx / 2 + 1;
     return ((size_t)nxh * plane_ldp_of(g.Ny, ny2) + g.Ny + g.Nx + ny2) * sizeof(C2<float>);

@@ -63,6 +63,9 @@ size_t eq1_lag64_size();
 void eq1_pack_lag64(void*, int, double, double);
 double dot_f64(cudaStream_t, const double*, const double*, size_t, double*);
 void shape_launch(cudaStream_t, const float*, int, int, double, double, int, double, double, const float*, float*);
+void eq1_basis_launch(cudaStream_t, const float*, int, const float*, int, int, int, int, double, double, double,
+                      const float*, const float*, const float*, const float*, const float*, const float*,
+                      const float*, float, int, int, int, double, double, const void*, float*);
 void features_launch(cudaStream_t, const float*, int, int, double, double, float, float, float, const float*, int,
                      double*, double*);
 void add_f32(cudaStream_t, size_t, const float*, float*);
@@ -149,6 +152,8 @@ struct wt_ctx {
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
+    // version for which E32 holds the basis fields of this relaxation (0: anything else)
+    unsigned long long e32_stamp = 0;
     std::vector<std::unique_ptr<struct BatchPlan>> plans;
     ~wt_ctx();
 };
@@ -720,8 +725,10 @@ void ensure_spectral(wt_ctx* c) {
 // lateral-scale derivative) and the expansion into out [nt][3][npts].
 // host_out != NULL: out is a device staging buffer; the expansion runs in time chunks and each
 // chunk is copied to host_out on the context's copy stream while the next one is computed.
-void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt, float* out, cudaStream_t s, int mode,
-                    int* launches, bool timing, float* host_out = nullptr) {
+// Basis fields E32[c][m][p] (m < r) of the charge vectors Ub (column transform and the
+// spectral passes), at the context's launch shapes.  Marks E32 as the relaxation's own fields
+// when Ub is the context's basis (mode 0), as anything else otherwise.
+void basis_fields32(wt_ctx* c, const double* Ub, int r, cudaStream_t s, int mode, int* launches, bool timing) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size();
@@ -732,6 +739,7 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
     c->rho32.alloc(c->sp32.rho_elems(nb));
     c->R32.alloc(c->sp32.r_elems(nb));
     c->E32.alloc((size_t)3 * rp * npts);
+    c->e32_stamp = 0;
     // the tensor-core expansion reads only the r rows in use; the FMA one reads all 32
     if (!tc && r < rp) WT_CUDA(cudaMemsetAsync(c->E32.p, 0, c->E32.n * sizeof(float), s));
     column_ztransform<float>(s, Ub, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
@@ -744,6 +752,16 @@ void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt
         *launches += 3;
     }
     if (timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
+    if (mode == 0 && Ub == c->Ub.p && r == c->rank) c->e32_stamp = c->version;
+}
+
+void extend32_basis(wt_ctx* c, const double* Ub, int r, const float* W32, int nt, float* out, cudaStream_t s, int mode,
+                    int* launches, bool timing, float* host_out = nullptr) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    const int rp = 32;
+    const bool tc = c->use_tc && expand_tc_available();
+    basis_fields32(c, Ub, r, s, mode, launches, timing);
     if (host_out) {
         // about 2 GB of H per chunk (whole 32-sample tiles): copies overlap the later chunks' expansion
         const size_t per_t = 3 * npts * sizeof(float);
@@ -998,6 +1016,56 @@ void do_eq1(wt_ctx* c, const void* H, const wt_tracks* tr, float* iout, cudaStre
     }
 }
 
+// Eq. 1 from the rank-r form of the FP32 field (the context's basis fields E32 and time
+// coefficients W32), without writing H; the basis fields are computed when E32 does not hold
+// them already.
+void eq1_basis_run(wt_ctx* c, const float* E, int r, const float* W32, const TrackDev& t, float* out, cudaStream_t s,
+                   const float* vz_override = nullptr) {
+    const wt_grid& g = c->grid;
+    const int nt = (int)c->times.size();
+    DBuf<unsigned char> dlag;
+    build_lags(c, t.dt, t.n_out, dlag, s, false);
+    eq1_basis_launch(s, E, r, W32, g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
+                     vz_override ? vz_override : t.vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt,
+                     c->opts.v_w, dlag.p, out);
+    WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
+}
+
+void ensure_base_fields(wt_ctx* c, cudaStream_t s) {
+    ensure_spectral(c);
+    if (c->e32_stamp == c->version && c->E32.p) return;
+    int launches = 0;
+    basis_fields32(c, c->Ub.p, c->rank, s, 0, &launches, false);
+}
+
+void do_eq1_direct(wt_ctx* c, const wt_tracks* tr, float* iout, cudaStream_t us) {
+    check_tracks(tr);
+    if (tr->n_tracks == 0) return;
+    if (!iout) fail(WT_ERR_ARG, "NULL argument");
+    const bool dev_in = is_device_ptr(tr->x);
+    const bool dev_out = is_device_ptr(iout);
+    cudaStream_t s = c->s;
+    if (dev_in && dev_out && us != s) {       // after the caller's pending work on its stream
+        cudaEvent_t ev;
+        WT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        WT_CUDA(cudaEventRecord(ev, us));
+        WT_CUDA(cudaStreamWaitEvent(s, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    DBuf<float> keep[7];
+    const TrackDev td = stage_tracks(c, tr, keep, s);
+    ensure_base_fields(c, s);
+    DBuf<float> dout;
+    float* o = iout;
+    if (!dev_out) { dout.alloc((size_t)tr->n_tracks * tr->n_out); o = dout.p; }
+    eq1_basis_run(c, c->E32.p, c->rank, c->W32.p, td, o, s);
+    if (!dev_out) {
+        dout.download(iout, (size_t)tr->n_tracks * tr->n_out, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+    }
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out");
+}
+
 // H M (right Householder product) for M rows x ns, in place.
 void house_right(wt_ctx* c, double* M, int rows) {
     DBuf<double> w;
@@ -1024,27 +1092,21 @@ double do_loss(wt_ctx* c, wt_precision prec, const wt_tracks* tr) {
     DBuf<float> keep[7];
     const TrackDev td = stage_tracks(c, tr, keep, s);
     int launches = 0;
-    const void* H;
-    if (prec == WT_FP64) {
-        c->stage64.alloc((size_t)nt * 3 * npts);
-        extend64(c, c->stage64.p, s, &launches);
-        H = c->stage64.p;
-    } else {
-        c->stage32.alloc((size_t)nt * 3 * npts);
-        extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, c->stage32.p, s, 0, &launches, false);
-        H = c->stage32.p;
-    }
     const size_t nI = (size_t)tr->n_tracks * tr->n_out;
     double sum;
     if (prec == WT_FP64) {
+        c->stage64.alloc((size_t)nt * 3 * npts);
+        extend64(c, c->stage64.p, s, &launches);
         DBuf<double> I;
         I.alloc(nI);
-        eq1_run(c, H, true, td, I.p, s);
+        eq1_run(c, c->stage64.p, true, td, I.p, s);
         sum = dot_f64(s, I.p, I.p, nI, c->d_scr.p);
     } else {
+        // FP32 field in its rank-r form: no H is written
+        ensure_base_fields(c, s);
         DBuf<float> I;
         I.alloc(nI);
-        eq1_run(c, H, false, td, I.p, s);
+        eq1_basis_run(c, c->E32.p, c->rank, c->W32.p, td, I.p, s);
         sum = dot_f32(s, I.p, I.p, nI, c->d_scr.p);
     }
     if (read_err(c)) fail(WT_ERR_TIMEOUT, "device wait timed out");
@@ -1387,6 +1449,7 @@ float time_min(cudaStream_t s, int reps, F&& f) {
 // then the expansion's time chunk in {64, 128, 256}.  Results are cached per
 // (device, grid, n_t) for the process.
 TuneResult autotune(wt_ctx* c, float* H) {
+    c->e32_stamp = 0;                       // trial shapes overwrite the basis fields
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(tune_key(c));
@@ -1603,6 +1666,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         plan = c0->plans.back().get();
     }
     plan->last_use = ++g_plan_clock;
+    for (int i = 0; i < n; ++i) ctxs[i]->e32_stamp = 0;     // written by the graph on the caller's stream
     // the graph runs on the caller's stream after the contexts' own pending work
     cudaEvent_t ev;
     WT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1902,6 +1966,14 @@ wt_status wt_shape(wt_ctx* ctx, const float* i, int n_tracks, int n_out, double 
         if ((size_t)n_out * 12 > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "n_out too large for one block's shared memory");
         shape_launch(static_cast<cudaStream_t>(stream), i, n_tracks, n_out, dt, sh->tau, sh->order, sh->gain,
                      sh->noise_rms, noise, v);
+    });
+}
+
+wt_status wt_eq1_direct(wt_ctx* ctx, const wt_tracks* tracks, float* i, void* stream) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_eq1_direct", [&] {
+        if (ctx->stage < 2) fail(WT_ERR_STATE, "wt_eq1_direct needs wt_relax first");
+        do_eq1_direct(ctx, tracks, i, static_cast<cudaStream_t>(stream));
     });
 }
 

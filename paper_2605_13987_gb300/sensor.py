@@ -65,6 +65,15 @@ class Sensor:
         B.wt_eq1(self.ctx, H, tracks, out, stream)
         return out
 
+    def eq1_direct(self, tracks, out=None, stream=None):
+        """Eq. 1 currents without writing H (from the field's rank-r form)."""
+        import torch
+        if out is None:
+            out = torch.empty((int(tracks["n_tracks"]), int(tracks["n_out"])), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        B.wt_eq1_direct(self.ctx, tracks, out, stream)
+        return out
+
     def loss(self, tracks, precision="fp32"):
         """Mean squared Eq. 1 current over tracks and output times."""
         prec = B.WT_FP64 if precision in ("fp64", B.WT_FP64) else B.WT_FP32

@@ -101,6 +101,25 @@ def test_eq1_currents(case, torch):
     assert rel_l2(i.cpu().numpy(), want) < TOL32
 
 
+def test_eq1_direct_matches_oracle_and_eq1_on_H(case, torch):
+    """Eq. 1 from the rank-r field form (no H): against the oracle, against
+    Eq. 1 on the stored FP32 H, with host and device tracks, and with a
+    ragged chunk of steps (37 steps: two full chunks of 16 and a tail)."""
+    w, sol, sen, H64, H32, ref = case
+    tr = W.configs.mip_tracks(w.grid, 24, 37, np.random.default_rng(8))
+    t = device_tracks(tr, torch)
+    i_h = sen.eq1(H32, t).cpu().numpy()
+    i_d = sen.eq1_direct(t).cpu().numpy()
+    want = OE.currents(sol.grid, sol.times, ref, tr)
+    assert rel_l2(i_d, want) < TOL32
+    assert rel_l2(i_d, i_h) < 2e-6
+    host = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in t.items()}
+    out = np.zeros((tr.n_tracks, tr.n_out), dtype=np.float32)
+    P = __import__("paper_2605_13987_gb300")
+    P.wt_eq1_direct(sen.ctx, host, out)
+    assert np.array_equal(out, i_d)
+
+
 def test_diagnostics(case):
     w, sol, sen, *_ = case
     info = sen.info()

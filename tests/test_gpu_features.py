@@ -178,3 +178,19 @@ def test_shaped_scan_features_match_oracle(P, torch):
     amp = np.abs(ref_f[:, 0]).max()
     assert np.all(np.abs(f[:, 0] - ref_f[:, 0]) <= 1e-4 * amp)
     assert np.all(np.abs(f[:, [1, 3, 4, 5]] - ref_f[:, [1, 3, 4, 5]]) <= 2e-3 * tr.dt)
+
+
+def test_thickness_scan_through_the_batch_matches_oracle(P, torch):
+    """Three thicknesses (Nz 40, 48, 64) in one captured batch of uneven
+    grids: every variant's features against the oracle's features of its
+    own FP64 currents."""
+    from paper_2605_13987_gb300.scan import run_scan
+    pts = W.scan_thickness(n_t=12, n_tracks=4, n_steps=20)
+    res = run_scan(pts, sensitivities=False)
+    for (th, w), r in zip(pts, res):
+        tr = w.tracks
+        ref_f = OF.features(A.loss(w, tr)[1], 0.0, tr.dt)
+        amp = np.abs(ref_f[:, 0]).max()
+        assert np.all(np.abs(r.features[:, 0] - ref_f[:, 0]) <= 1e-4 * amp), th
+        assert np.all(np.abs(r.features[:, [1, 3, 4, 5]] - ref_f[:, [1, 3, 4, 5]]) <= 2e-3 * tr.dt), th
+        print("thickness", th, r.summary())
