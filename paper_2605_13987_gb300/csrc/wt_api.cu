@@ -1444,10 +1444,12 @@ float time_min(cudaStream_t s, int reps, F&& f) {
 }
 
 // Autotuner: times every candidate launch shape of the FP32 path on this
-// context (its own basis vectors, writing into H) and keeps the fastest:
-// spectral batch nb in {1, 2, 4} x z-pass lines per block in {16, 32, 64},
-// then the expansion's time chunk in {64, 128, 256}.  Results are cached per
-// (device, grid, n_t) for the process.
+// context (its own basis vectors, writing into H; the minimum of 3 runs, 5 for
+// the expansion) and keeps the fastest: the FFT forms (register-FFT lanes,
+// two-pass y / x / z transforms, direct or staged x stores), then spectral
+// batch nb in {1, 2, 4} x z-pass lines per block in {16, 32, 64}, then the
+// expansion's time chunk {64, 128, 256} x epilogue warps {8, 12, 16} x store
+// width {4, 2, 1}.  Results are cached per (device, grid, n_t) for the process.
 TuneResult autotune(wt_ctx* c, float* H) {
     c->e32_stamp = 0;                       // trial shapes overwrite the basis fields
     {
@@ -1498,7 +1500,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
                 for (const auto& zo : zopts) {
                     c->sp32.set_radix(xo.first, zo.first, zo.second, xo.second & 2, xo.second & 4);
                     c->sp32.xdirect = xd;
-                    const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
+                    const float ms = time_min(s, 3, [&] { spectral_all(c, s); });
                     if (ms < best_ms) {
                         best_ms = ms;
                         best.rxy = xo.first;
@@ -1516,7 +1518,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
         alloc_fast32(c);
         for (int lb : {16, 32, 64}) {
             c->tune_lb = lb;
-            const float ms = time_min(s, 2, [&] { spectral_all(c, s); });
+            const float ms = time_min(s, 3, [&] { spectral_all(c, s); });
             if (ms < best.spectral_ms) { best.spectral_ms = ms; best.nb = nb; best.lb = lb; }
         }
     }
@@ -1528,7 +1530,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
         for (int nepi : {8, 12, 16})
             for (int nch : {64, 128, 256}) {
                 ExpandJob jb{c->E32.p, 32, c->rank, c->W32.p, nt, npts, H};
-                const float ms = time_min(s, 2, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi, vec); });
+                const float ms = time_min(s, 5, [&] { expand_tc_jobs(s, &jb, 1, 0, nch, c->d_err.p, nepi, vec); });
                 if (ms < best.expand_ms) {
                     best.expand_ms = ms;
                     best.nch = nch;
