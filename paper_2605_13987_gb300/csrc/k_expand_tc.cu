@@ -12,8 +12,8 @@
 // shared memory for the whole kernel.  Three tcgen05.mma products
 // (hi*hi + hi*lo + lo*hi, kind::tf32, FP32 accumulation in tensor memory)
 // give FP32-level accuracy.  The accumulator D[p][t] lives in TMEM (lane =
-// grid point, column = time sample), in 512 / chunk buffers of one chunk
-// each (2, 4 or 8) so that the MMAs run ahead of the epilogue; eight, twelve or sixteen epilogue warps (two to four per TMEM lane
+// grid point, column = time sample), double buffered in two 256-column
+// halves; eight, twelve or sixteen epilogue warps (two to four per TMEM lane
 // quadrant, alternate 32-column slices) drain it with tcgen05.ld, transpose 4 x 4 blocks within
 // lane quads by shuffles and write H with 16-byte stores: each warp store
 // covers 4 time samples x 32 consecutive grid points (four full 128-byte
@@ -203,7 +203,7 @@ __device__ __forceinline__ void quad_transpose(float (&v)[32], int lane) {
 struct Smem {
     // tiles first (1024-byte aligned base):
     // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo], raw[2][32][128] FP32
-    unsigned long long a_full[2], a_empty[2], acc_full[8], acc_empty[8], raw_full[2], drain, b_free;
+    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain, b_free;
     unsigned tmem_base;
     int abort_flag;
 };
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             mbar_init(&S->a_empty[i], 1);
             mbar_init(&S->raw_full[i], 1);
         }
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&S->acc_full[i], 1);
             mbar_init(&S->acc_empty[i], 32 * NEPI);
         }
@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = S->tmem_base;
-    const int nbuf = TMEM_COLS / nch;        // accumulator chunk buffers in tensor memory (8, 4 or 2)
+    // two accumulator buffers of TMEM_COLS / 2 columns (one chunk each); deeper buffering (512 / chunk
+    // buffers) measured 2-3 % slower on c2
+    constexpr int nbuf = 2, bstride = TMEM_COLS / 2;
     volatile int* abort_flag = &S->abort_flag;
 
     if (warp == 0) {
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 if (lane == 0) {
                     const unsigned bh = smem_u32(b_hi + (size_t)ch * nch * 128);
                     const unsigned bl = smem_u32(b_lo + (size_t)ch * nch * 128);
-                    const unsigned d = tmem + (unsigned)(b * nch);
+                    const unsigned d = tmem + (unsigned)(b * bstride);
 #pragma unroll
                     for (int ks = 0; ks < KR / 8; ++ks) {
                         const unsigned off = ks * 32;   // 8 TF32 = 32 bytes along K
@@ -441,8 +443,8 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                     const int j2 = j + 32 * NSL;
                     const bool two = j2 < n;
                     unsigned ra[32], rb[32];
-                    tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * nch + j), ra);
-                    if (two) tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * nch + j2), rb);
+                    tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * bstride + j), ra);
+                    if (two) tmem_ld32_nowait(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * bstride + j2), rb);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
