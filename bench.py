@@ -321,6 +321,8 @@ def run_adjoint(args):
     for _ in range(args.warmup):
         sen.loss_grad(t)
     per = []
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStart()
     with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
         barrier(world)
         for _ in range(args.steps):
@@ -329,6 +331,8 @@ def run_adjoint(args):
             L, g = sen.loss_grad(t)
             torch.cuda.synchronize()
             per.append(time.perf_counter() - a)
+        if args.profile:
+            torch.cuda.cudart().cudaProfilerStop()
         barrier(world)
         a = time.perf_counter()
         L32 = sen.loss(t, "fp32")
