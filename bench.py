@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+METRIC = "H grid-point*time-samples/sec (FP32 extension, 12 B/point-sample written once)"
 WORKLOADS = {
     "c2": "c2: 3x3 pixel cell 165x165x500 um, grid 128x128x256, 18 columns x 256 sources, 512 time samples",
     "c1": "c1: single cell 55x55x100 um, grid 32x32x64, 2 columns x 64 sources, 64 time samples",
@@ -186,7 +187,7 @@ def run_reference(args):
         tot_s += s
     v = tot_ps / tot_s
     cores = os.cpu_count()
-    line = {"impl": "reference", "metric": "H grid-point*time-samples/sec", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "point-samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -271,7 +272,7 @@ def run_batch(args):
         tun[f"{w.grid.Nx}x{w.grid.Ny}x{w.grid.Nz}"] = s_.tuning()
     if rank == 0:
         line = {
-            "metric": "H grid-point*time-samples/sec (FP32 extension, 12 B/point-sample written once)",
+            "metric": METRIC,
             "value": value, "unit": "point-samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -640,7 +641,7 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": "H grid-point*time-samples/sec (FP32 extension, 12 B/point-sample written once)",
+            "metric": METRIC,
             "value": value, "unit": "point-samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
