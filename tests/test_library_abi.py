@@ -49,3 +49,32 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert L.wt_relax(None, None, 0) == B.WT_ERR_ARG
     assert L.wt_extend(None, 0, None, 0, None) == B.WT_ERR_ARG
     L.wt_destroy(None)
+
+
+def undocumented_prototypes(text):
+    """Prototypes whose block of contiguous lines (typedefs, macros, other
+    prototypes of a group) does not start right below a comment."""
+    lines = text.splitlines()
+    proto = re.compile(r"^(wt_status|const char\*|void)\s+(wt_[A-Za-z_0-9]+)\s*\(")
+    bad = []
+    for k, line in enumerate(lines):
+        m = proto.match(line)
+        if not m:
+            continue
+        j = k - 1
+        while j >= 0 and lines[j].strip() and not lines[j].strip().endswith("*/"):
+            j -= 1
+        if j < 0 or not lines[j].strip():
+            bad.append(m.group(2))
+    return bad
+
+
+def test_undocumented_prototypes_are_found():
+    assert undocumented_prototypes("/* doc */\nwt_status wt_a(int x);\n\nint y;\nwt_status wt_b(int y);\n") == ["wt_b"]
+    assert undocumented_prototypes("/* doc */\ntypedef struct {\n    int a;\n} t;\nwt_status wt_c(t* x);\n") == []
+
+
+def test_every_entry_point_is_documented():
+    """Each prototype (or group of prototypes) of the header sits directly
+    below a comment that states what the call computes."""
+    assert not undocumented_prototypes(open(HEADER).read())
