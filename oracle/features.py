@@ -1,7 +1,7 @@
 """Signal-shape features of induced-current (or shaped) waveforms and their
 first-order sensitivities, for the geometry scans of Sec. 5 (bias-electrode
-diameter 6-14 um, diamond thickness), where each sensor variant is judged by
-the shape of its signals.  The paper reports time resolution, which needs
+diameter 6-14 um, diamond thickness), where the sensor variants are compared
+by the shape of their signals.  The paper reports time resolution, which needs
 the ionisation and noise model it takes from HEED/Garfield++; the features
 here are the deterministic signal properties that time resolution is built
 from (amplitude, peak time, collected charge, leading-edge threshold and

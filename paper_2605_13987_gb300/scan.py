@@ -1,6 +1,6 @@
 """Geometry what-if scans (Sec. 5: the bias-electrode diameter from 6 to
-14 um in 2 um steps, and the diamond thickness), each sensor variant judged
-by the shape of its signals.
+14 um in 2 um steps, and the diamond thickness), the sensor variants
+compared by the shape of their signals.
 
 For every variant: fit and relaxation (``Sensor.fit``, ``Sensor.relax``);
 then either the fields of all variants in one captured batch
