@@ -588,7 +588,14 @@ def run_ours(args):
     # end to end through the C ABI: pinned host output, device compute + D2H copy of H
     e2e = None
     if not args.no_e2e and not args.profile:
-        Hh = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, pin_memory=True)
+        # pinned host memory (25.8 GB per rank for c2); should the host refuse that much pinned
+        # memory (several ranks on one node), the same call runs into pageable memory
+        try:
+            Hh = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32, pin_memory=True)
+            host_mem = "pinned"
+        except RuntimeError:
+            Hh = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float32)
+            host_mem = "pageable (the pinned allocation was refused)"
         sen.set_timing(False)
         sen.extend("fp32", out=Hh)
         barrier(world)
@@ -602,7 +609,8 @@ def run_ours(args):
             per_call.append(time.perf_counter() - t1)
         el = max_over_ranks(statistics.median(per_call), world)
         e2e = {"value": world * ps_step / el, "unit": "point-samples/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": int(Hh.numel() * 4), "ms_per_call": [1e3 * t for t in per_call]}
+               "d2h_bytes_per_step": int(Hh.numel() * 4), "ms_per_call": [1e3 * t for t in per_call],
+               "host_memory": host_mem}
         del Hh
 
     # the comparison path of the metric: the FP64 plain extension (one FP64 spectral transform per
