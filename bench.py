@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -79,8 +80,9 @@ def peaks():
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    def __init__(self, path):
-        self.path = path
+    def __init__(self, tag=""):
+        fd, self.path = tempfile.mkstemp(prefix=f"wt_bench_clocks{tag}_", suffix=".csv")
+        os.close(fd)
         self.p = None
 
     def __enter__(self):
@@ -103,6 +105,12 @@ class Clocks:
             except Exception:
                 self.p.kill()
             self.f.close()
+
+    def __del__(self):
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
 
     def summary(self, gpu_index):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
@@ -155,17 +163,74 @@ def max_over_ranks(x, world):
 def oracle_sample(w, sol, rng_seed=11, n_t=4, n_side=12):
     """Bounded oracle sample of the workload's H: n_t time samples on an
     n_side^3 random tensor-product subgrid.  Returns (point-samples, seconds)."""
+    return _subgrid_sample(w.grid, sol.lay.src, sol.q, rng_seed, n_t, n_side)
+
+
+def _subgrid_sample(grid, src, q, rng_seed, n_t=4, n_side=12):
     import numpy as np
+    from oracle import extend as OX
     rng = np.random.default_rng(rng_seed)
-    g = w.grid
-    ti = np.sort(rng.choice(len(w.times), n_t, replace=False))
-    ix = np.sort(rng.choice(g.Nx, n_side, replace=False))
-    iy = np.sort(rng.choice(g.Ny, n_side, replace=False))
-    iz = np.sort(rng.choice(g.Nz, n_side, replace=False))
+    ti = np.sort(rng.choice(q.shape[1], n_t, replace=False))
+    ix = np.sort(rng.choice(grid.Nx, n_side, replace=False))
+    iy = np.sort(rng.choice(grid.Ny, n_side, replace=False))
+    iz = np.sort(rng.choice(grid.Nz, n_side, replace=False))
     t0 = time.perf_counter()
-    sol.H_subgrid(t_idx=ti, ix=ix, iy=iy, iz=iz)
+    OX.field_subgrid(grid, src, q[:, ti], ix, iy, iz)
     dt = time.perf_counter() - t0
     return n_t * n_side ** 3, dt
+
+
+def _sample_for(grid, src, q, seconds, seed0=7):
+    """Oracle subgrid draws until `seconds` of CPU work; (point-samples, seconds)."""
+    tot_ps, tot_s, k = 0, 0.0, 0
+    while tot_s < seconds:
+        ps_, s_ = _subgrid_sample(grid, src, q, seed0 + k)
+        tot_ps += ps_
+        tot_s += s_
+        k += 1
+    return tot_ps, tot_s
+
+
+BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def cpu_sample_child(path, seconds):
+    """Child process of the single-threaded CPU baseline: the same oracle draws on the charges
+    saved by the parent (its BLAS limited to one thread by the environment)."""
+    import numpy as np
+    from workloads.configs import GridSpec
+    d = np.load(path, allow_pickle=False)
+    gk = json.loads(str(d["grid"]))
+    ps, s = _sample_for(GridSpec(**gk), d["src"], d["q"], seconds)
+    print(json.dumps({"ps": ps, "s": s}), flush=True)
+    return 0
+
+
+def cpu_baseline_threads(w, sol, seconds, threads):
+    """Oracle draws in a child process whose BLAS runs `threads` threads (None: the default,
+    all cores).  Returns (point-samples/s, seconds) or None if the child failed."""
+    import dataclasses
+    import numpy as np
+    fd, path = tempfile.mkstemp(prefix="wt_bench_oracle_", suffix=".npz")
+    os.close(fd)
+    try:
+        np.savez(path, grid=json.dumps(dataclasses.asdict(w.grid)), src=sol.lay.src, q=sol.q)
+        env = dict(os.environ)
+        for k in BLAS_THREAD_VARS:
+            if threads is None:
+                env.pop(k, None)
+            else:
+                env[k] = str(threads)
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-sample-from", path,
+                            "--cpu-seconds", str(seconds)], env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            return None
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d["ps"] / d["s"], d["s"]
+    except Exception:
+        return None
+    finally:
+        os.unlink(path)
 
 
 def run_reference(args):
@@ -254,7 +319,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+    with Clocks(f"_{rank}") as clk:
         barrier(world)
         torch.cuda.synchronize()
         a.record(stream)
@@ -324,7 +389,7 @@ def run_adjoint(args):
     per = []
     if args.profile:
         torch.cuda.cudart().cudaProfilerStart()
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+    with Clocks(f"_{rank}") as clk:
         barrier(world)
         for _ in range(args.steps):
             torch.cuda.synchronize()
@@ -393,7 +458,7 @@ def run_large(args):
         sen.eq1_direct(tracks, out=cur)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+    with Clocks(f"_{rank}") as clk:
         barrier(world)
         torch.cuda.synchronize()
         for k in range(args.steps):
@@ -480,7 +545,7 @@ def run_scan_bench(args):
     for _ in range(args.warmup):
         run_scan(pts, sensitivities=True, shaper=shaper, device=local)
     per = []
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+    with Clocks(f"_{rank}") as clk:
         barrier(world)
         for _ in range(args.steps):
             torch.cuda.synchronize()
@@ -547,7 +612,7 @@ def run_ours(args):
     launches = 0
     if args.profile:
         torch.cuda.cudart().cudaProfilerStart()
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{rank}.csv")) as clk:
+    with Clocks(f"_{rank}") as clk:
         barrier(world)
         torch.cuda.synchronize()
         for k in range(args.steps):
@@ -599,7 +664,7 @@ def run_ours(args):
         sen.set_timing(False)
         sen.extend("fp32", out=Hh)
         barrier(world)
-        k2 = max(1, min(3, args.steps))
+        k2 = max(1, min(5, args.steps))
         per_call = []
         for _ in range(k2):             # each call is one whole end-to-end step; the median is reported
             torch.cuda.synchronize()
@@ -610,12 +675,16 @@ def run_ours(args):
         el = max_over_ranks(statistics.median(per_call), world)
         e2e = {"value": world * ps_step / el, "unit": "point-samples/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": int(Hh.numel() * 4), "ms_per_call": [1e3 * t for t in per_call],
-               "host_memory": host_mem}
+               "ms_min": 1e3 * min(per_call), "ms_median": 1e3 * statistics.median(per_call),
+               "ms_max": 1e3 * max(per_call), "host_memory": host_mem,
+               "inputs": "none copied per step: the step's inputs (the relaxed charge history and the geometry "
+                         "tables) are already on the device after wt_relax; H (the output) is copied out"}
         del Hh
 
     # the comparison path of the metric: the FP64 plain extension (one FP64 spectral transform per
     # time sample), timed once after one untimed call, into its own device buffer
     fp64 = None
+    accuracy = None
     if not args.no_fp64 and not args.profile:
         H64 = torch.empty((nt, 3, g.Nx, g.Ny, g.Nz), dtype=torch.float64, device=dev)
         sen.set_timing(False)
@@ -630,7 +699,21 @@ def run_ours(args):
         ms64 = e0.elapsed_time(e1)
         fp64 = {"value": ps_step / (ms64 / 1e3), "unit": "point-samples/s", "ms_per_step": ms64,
                 "dtype": "f64", "fp32_speedup": ms64 / ms_max}
-        del H64
+        # the metric's accuracy: the timed FP32 H (last timed step, still in H) against the FP64
+        # plain H, over the whole array and per time sample
+        num = torch.empty(nt, dtype=torch.float64, device=dev)
+        den = torch.empty(nt, dtype=torch.float64, device=dev)
+        for t in range(nt):
+            d = H[t].double() - H64[t]
+            num[t] = (d * d).sum()
+            den[t] = (H64[t] * H64[t]).sum()
+        per = (num / den).sqrt().cpu().numpy()
+        worst = int(per.argmax())
+        accuracy = {"rel_l2_vs_fp64": float((num.sum() / den.sum()).sqrt()), "tolerance": 1e-5,
+                    "worst_sample_rel_l2": float(per[worst]), "worst_sample": worst,
+                    "worst_sample_time_s": float(w.times[worst]), "first_sample_rel_l2": float(per[0]),
+                    "per_sample_max_within_tolerance": bool(per.max() <= 1e-5)}
+        del H64, d
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
@@ -638,14 +721,18 @@ def run_ours(args):
         t2 = time.perf_counter()
         sol = O.solve(w)
         osetup = time.perf_counter() - t2
-        tot_ps, tot_s = 0, 0.0
-        while tot_s < 10.0:
-            ps_, s_ = oracle_sample(w, sol, rng_seed=7 + int(tot_s * 10))
-            tot_ps += ps_
-            tot_s += s_
-        cpu = {"value": tot_ps / tot_s, "unit": "point-samples/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{tot_ps} point-samples (4 time samples x 12^3 random grid points per draw) in "
-                         f"{tot_s:.1f} s; oracle setup ({osetup:.1f} s) excluded like the GPU setup"}
+        # the same oracle draws twice, each in a child process: BLAS on all host cores (its
+        # default) and on one thread (OMP/OPENBLAS/MKL/BLIS_NUM_THREADS=1)
+        allc = cpu_baseline_threads(w, sol, 10.0, None)
+        one = cpu_baseline_threads(w, sol, 10.0, 1)
+        if allc is not None:
+            cpu = {"value": allc[0], "unit": "point-samples/s", "cores": os.cpu_count(),
+                   "threads": f"BLAS default: {os.cpu_count()} host cores", "kind": "oracle",
+                   "sample": f"4 time samples x 12^3 random grid points per draw, {allc[1]:.1f} s of draws; "
+                             f"oracle setup ({osetup:.1f} s) excluded like the GPU setup",
+                   "single_thread": None if one is None else
+                   {"value": one[0], "unit": "point-samples/s", "cores": 1, "threads": 1,
+                    "sample": f"the same draws, {one[1]:.1f} s, BLAS limited to one thread"}}
 
     if rank == 0:
         line = {
@@ -665,7 +752,7 @@ def run_ours(args):
                          "expansion": exp_ms},
             "tuning": sen.tuning(),
             "step_frac_of_hbm_roof": (alg_bytes / (ms_max / 1e3) / 1e9) / peak,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64_plain": fp64,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64_plain": fp64, "accuracy": accuracy,
             "clocks": clk.summary(local),
             "setup_s": setup,
             "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond,
@@ -690,11 +777,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 plain path")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--arena-gb", type=float, default=96.0, help="c3: device memory for one wave's H")
+    ap.add_argument("--cpu-sample-from", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help=argparse.SUPPRESS)
     ap.add_argument("--profile", action="store_true",
                     help="wrap only the timed steps in cudaProfilerStart/Stop (for ncu --profile-from-start off); "
                          "skips the CPU baseline and e2e")
     args = ap.parse_args()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    if args.cpu_sample_from:
+        return cpu_sample_child(args.cpu_sample_from, args.cpu_seconds)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c3":

@@ -57,7 +57,9 @@ typedef enum {
     WT_ERR_TIMEOUT = 7,          /* a bounded device wait gave up */
     WT_ERR_STATE = 8,            /* call out of order */
     WT_ERR_NAN = 9,              /* non-finite input or intermediate */
-    WT_ERR_UNSUPPORTED = 10      /* size or option this build does not handle */
+    WT_ERR_UNSUPPORTED = 10,     /* size or option this build does not handle */
+    WT_ERR_ACCURACY = 11         /* the FP32 path cannot reach its accuracy for this charge history
+                                    (its time basis would need rank > 32): use WT_FP64 */
 } wt_status;
 
 typedef enum { WT_FP32 = 0, WT_FP64 = 1 } wt_precision;
@@ -114,11 +116,14 @@ typedef struct {
     double cond_estimate;        /* 2-norm condition estimate of the column-scaled fit matrix */
     double boundary_residual;    /* ||P q + c - S phi_DC|| / ||S phi_DC|| of the DC state */
     double asymmetry;            /* ||F - F^T|| / ||F|| (Green reciprocity) */
-    double trunc_rel;            /* sigma_{rank+1} / sigma_1 of the charge history */
+    double trunc_rel;            /* largest relative truncation error of one time sample of the
+                                    charge history in the FP32 path's rank-`rank` time basis,
+                                    ||q(t_n) - q_r(t_n)|| / ||q(t_n)|| (exact, from its SVD) */
     double mu_min, mu_max;       /* relaxation rates [1/s] */
     double fit_seconds, relax_seconds;
     double grad_trunc_rel;       /* largest relative truncation of the charge tangents in the
                                     last wt_eq1_loss_grad (rank-32 time bases) */
+    int Nx, Ny, Nz;              /* the context's grid (H holds n_t x 3 x Nx x Ny x Nz values) */
 } wt_info;
 
 /* Create a context on CUDA device `cuda_device` for the given grid.
@@ -144,7 +149,12 @@ wt_status wt_fit(wt_ctx* ctx, const wt_fit_opts* opts, double* cond_estimate_out
  * C_n dphi/dt = K phi + b with the resistive lines of Sec. 5, solved by
  * the generalised symmetric eigenproblem on the neutral subspace; the node
  * charges q(t_n) at the n_t host times t[] (seconds, increasing, > 0), and
- * the rank-r time basis used by the FP32 path.  Synchronous. */
+ * the rank-r time basis used by the FP32 path: the singular value
+ * decomposition of the charge history [q(t_0) ... q(t_{n_t-1})] (one-sided
+ * Jacobi, FP64), truncated at the smallest r <= 32 that leaves at most 1e-7
+ * relative error in every time sample (wt_info.rank, wt_info.trunc_rel).
+ * A history that still leaves more than 1e-6 at r = 32 relaxes normally,
+ * but the FP32 field paths then return WT_ERR_ACCURACY.  Synchronous. */
 wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
 
 /* Bulk extension (Abstract; Sec. 1 DFT; Sec. 3 |k|^2 spectral division):
@@ -159,8 +169,10 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
  * and returns only after that tuning; later calls reuse the choice.  The
- * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec]]"
- * (the values of wt_get_tuning) fixes the shapes without tuning. */
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows]]]"
+ * (the values of wt_get_tuning) fixes the shapes without tuning.
+ * WT_FP32 returns WT_ERR_ACCURACY when the time basis is truncated beyond
+ * its limit (see wt_relax). */
 wt_status wt_extend(wt_ctx* ctx, wt_precision prec, void* H, size_t H_bytes, void* cuda_stream);
 
 /* Exact FP64 point evaluation of H (the band-limited spectral sum, no grid
@@ -192,14 +204,21 @@ wt_status wt_eq1(wt_ctx* ctx, const void* H, const wt_tracks* tracks, float* i, 
  * fixed device array of WT_EQ1_NOALLOC_MAX_OUT entries, which every GPU that
  * loads the library holds (192 KB) until the process exits.  n_out above the
  * limit returns WT_ERR_ARG.  H, the track arrays and i must be device
- * memory (WT_ERR_ARG otherwise: host buffers would need staging).  The
+ * memory (WT_ERR_ARG otherwise: host buffers would need staging).  Each buffer
+ * must lie on the context's device and hold what the call touches: H
+ * n_t x 3 x Nx x Ny x Nz floats (wt_extend's FP32 layout), i n_tracks x n_out
+ * floats, each track array n_tracks x n_steps floats and q (if not NULL)
+ * n_tracks floats; a buffer on another device, or one that ends before that
+ * inside its allocation, returns WT_ERR_ARG.  The
  * call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once; make that first call before any stream
  * capture.  All calls share the one array and each call overwrites the
  * entries it uses, so calls that overlap on the GPU (for example on two
  * streams at once) race on it: order them on one stream.  Asynchronous on
- * cuda_stream. */
+ * cuda_stream; the call reads the relaxation's time samples there, and a
+ * later wt_relax on the context waits for it (through an event recorded on
+ * cuda_stream) before it replaces them. */
 #define WT_EQ1_NOALLOC_MAX_OUT 16384
 wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tracks, float* i, void* cuda_stream);
 
@@ -282,7 +301,7 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
 /* Launch shapes the FP32 path of this context uses, set by the autotuner
- * (before the first extension: the defaults 1, 32, 256, 8, 0, 0, 0, 0, 4). */
+ * (before the first extension: the defaults 1, 32, 256, 8, 0, 0, 0, 0, 4, 0). */
 typedef struct {
     int nb;         /* charge vectors per spectral launch: 1, 2, 4 */
     int lb;         /* (x, y) lines per z-pass block: 16, 32, 64 */
@@ -296,6 +315,11 @@ typedef struct {
                        r_xy and x_direct then unused) */
     int store_vec;  /* floats per expansion store: 4 (4 x 4 lane-quad transposes), 2 (2 x 2
                        lane-pair transposes) or 1 (straight from the accumulator layout) */
+    int table_rows; /* 0: basis fields by the per-basis spectral passes (deposit, lateral FFTs, z
+                       pass); > 0: from the context's per-column lateral tables (Sec. 3's
+                       translated fundamental-solution chunks in spectral form, built once per
+                       context, 12 B x n_columns x Nx x Ny x Nz), combined per basis vector in y
+                       slabs of table_rows rows and followed by the z pass */
 } wt_tuning;
 wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out);
 

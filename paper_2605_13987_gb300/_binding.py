@@ -17,11 +17,12 @@ LIB_PATH = os.path.join(HERE, "libwt.so")
 
 WT_OK, WT_ERR_ARG, WT_ERR_GEOMETRY, WT_ERR_ILL_CONDITIONED, WT_ERR_NOT_SPD = 0, 1, 2, 3, 4
 WT_ERR_OOM, WT_ERR_CUDA, WT_ERR_TIMEOUT, WT_ERR_STATE, WT_ERR_NAN, WT_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
+WT_ERR_ACCURACY = 11
 WT_FP32, WT_FP64 = 0, 1
 WT_Z_MIRROR, WT_Z_PERIODIC = 0, 1
 STATUS_NAMES = {0: "WT_OK", 1: "WT_ERR_ARG", 2: "WT_ERR_GEOMETRY", 3: "WT_ERR_ILL_CONDITIONED",
                 4: "WT_ERR_NOT_SPD", 5: "WT_ERR_OOM", 6: "WT_ERR_CUDA", 7: "WT_ERR_TIMEOUT",
-                8: "WT_ERR_STATE", 9: "WT_ERR_NAN", 10: "WT_ERR_UNSUPPORTED"}
+                8: "WT_ERR_STATE", 9: "WT_ERR_NAN", 10: "WT_ERR_UNSUPPORTED", 11: "WT_ERR_ACCURACY"}
 
 
 class wt_grid(C.Structure):
@@ -54,7 +55,7 @@ class wt_shaper(C.Structure):
 
 class wt_tuning(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("nb", "lb", "nch", "nepi", "r_xy", "r_z", "x_direct", "two_pass",
-                                       "store_vec")]
+                                       "store_vec", "table_rows")]
 
 
 class wt_feature_opts(C.Structure):
@@ -70,7 +71,7 @@ class wt_info(C.Structure):
                 ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
                 ("asymmetry", C.c_double), ("trunc_rel", C.c_double), ("mu_min", C.c_double),
                 ("mu_max", C.c_double), ("fit_seconds", C.c_double), ("relax_seconds", C.c_double),
-                ("grad_trunc_rel", C.c_double)]
+                ("grad_trunc_rel", C.c_double), ("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int)]
 
 
 # name -> (restype, argtypes); the ABI of include/wt.h
@@ -230,9 +231,38 @@ def wt_eq1(ctx, H, tracks, i_out, stream=None):
     _check(lib.wt_eq1(ctx, _ptr(H), C.byref(tr), _ptr(i_out), st), ctx)
 
 
-def wt_eq1_noalloc(ctx, H, tracks, i_out, stream=None):
-    """Eq. 1 with no device allocation: every buffer must be device memory."""
+def _noalloc_buffer(name, t, n_min, device, exact=False):
+    """Checks a wt_eq1_noalloc argument: a contiguous float32 CUDA tensor on `device` holding at
+    least (exactly, for H) n_min values; raises WTError(WT_ERR_ARG) otherwise."""
+    import torch
+    why = None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        why = "must be a CUDA tensor (the call stages nothing)"
+    elif t.dtype != torch.float32:
+        why = f"must be float32, not {t.dtype}"
+    elif not t.is_contiguous():
+        why = "must be contiguous"
+    elif t.device.index != device:
+        why = f"is on cuda:{t.device.index}, the context on cuda:{device}"
+    elif (t.numel() != n_min) if exact else (t.numel() < n_min):
+        why = f"holds {t.numel()} values, needs {'exactly ' if exact else ''}{n_min}"
+    if why:
+        raise WTError(WT_ERR_ARG, f"wt_eq1_noalloc: {name} {why}")
+
+
+def wt_eq1_noalloc(ctx, H, tracks, i_out, stream=None, device=None):
+    """Eq. 1 with no device allocation: every buffer a contiguous float32 CUDA tensor on the
+    context's device (`device`, default: H's), sized as the call needs."""
     lib = load_library()
+    info = wt_get_info(ctx)
+    dev = H.device.index if device is None and hasattr(H, "device") else (device or 0)
+    n_tr, n_st, n_out = int(tracks["n_tracks"]), int(tracks["n_steps"]), int(tracks["n_out"])
+    _noalloc_buffer("H", H, info["n_t"] * 3 * info["Nx"] * info["Ny"] * info["Nz"], dev, exact=True)
+    _noalloc_buffer("i_out", i_out, n_tr * n_out, dev)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        _noalloc_buffer(k, tracks[k], n_tr * n_st, dev)
+    if tracks.get("q") is not None:
+        _noalloc_buffer("q", tracks["q"], n_tr, dev)
     tr = _tracks_struct(tracks)
     _check(lib.wt_eq1_noalloc(ctx, _ptr(H), C.byref(tr), _ptr(i_out), _stream_handle(stream)), ctx)
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 namespace wt {
 
@@ -564,6 +565,152 @@ int jacobi_eig(cudaStream_t s, double* A_in, int n, double* w, double* V_out, in
     }
     WT_CUDA(cudaStreamSynchronize(s));
     return sweeps;
+}
+
+// ------------------------------------------------------ one-sided Jacobi SVD
+// Hestenes' method on the rows of A [m][n]: every round rotates the m/2
+// disjoint row pairs of one circle-method pairing, (a_p, a_q) <- (c a_p - s a_q,
+// s a_p + c a_q) with the angle that makes them orthogonal, and applies the
+// same rotation to rows p, q of V [m][m].  No Gram matrix is formed, so the
+// singular values keep their relative accuracy (a Gram matrix would square
+// the condition number).  One block per pair: three block-wide dot products,
+// then the rotation of both rows.
+__global__ void __launch_bounds__(256) osj_round_kernel(double* __restrict__ A, int n, int lda,
+                                                        double* __restrict__ V, int m_real, int m, int ldv,
+                                                        int round, double tol, double abs_floor,
+                                                        unsigned long long* __restrict__ n_rot) {
+    int p = circle_player(blockIdx.x, round, m), q = circle_player(m - 1 - blockIdx.x, round, m);
+    if (p > q) { const int t = p; p = q; q = t; }
+    if (q >= m_real) return;                      // the padding row of an odd m
+    double* ap = A + (size_t)p * lda;
+    double* aq = A + (size_t)q * lda;
+    double sa = 0.0, sb = 0.0, sg = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double x = ap[k], y = aq[k];
+        sa = fma(x, x, sa);
+        sb = fma(y, y, sb);
+        sg = fma(x, y, sg);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    }
+    __shared__ double red[3][8];
+    __shared__ double rot[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = sa; red[1][warp] = sb; red[2][warp] = sg; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { al += red[0][w]; be += red[1][w]; ga += red[2][w]; }
+        double c = 1.0, sn = 0.0;
+        // rotate when the rows are coupled above rounding relative to their norms and above the
+        // absolute floor (pairs of rounding-level rows would otherwise keep rotating)
+        if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > abs_floor) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = c * t;
+            atomicAdd(n_rot, 1ull);
+        }
+        rot[0] = c;
+        rot[1] = sn;
+    }
+    __syncthreads();
+    const double c = rot[0], sn = rot[1];
+    if (sn == 0.0) return;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double x = ap[k], y = aq[k];
+        ap[k] = c * x - sn * y;
+        aq[k] = sn * x + c * y;
+    }
+    double* vp = V + (size_t)p * ldv;
+    double* vq = V + (size_t)q * ldv;
+    for (int k = threadIdx.x; k < m_real; k += blockDim.x) {
+        const double x = vp[k], y = vq[k];
+        vp[k] = c * x - sn * y;
+        vq[k] = sn * x + c * y;
+    }
+}
+
+__global__ void __launch_bounds__(256) row_norms_kernel(const double* __restrict__ A, int n, int lda,
+                                                        double* __restrict__ out) {
+    const double* a = A + (size_t)blockIdx.x * lda;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s = fma(a[k], a[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[blockIdx.x] = sqrt(t);
+    }
+}
+
+int onesided_jacobi_rows(cudaStream_t s, double* A, int m, int n, int lda, double* V, double* sigma, int* d_err,
+                         int max_sweeps) {
+    const int mp = m + (m & 1);                  // even circle; an odd m has one idle row per round
+    eye_kernel<<<((size_t)m * m + 255) / 256, 256, 0, s>>>(V, m, m);
+    WT_LAUNCH("eye");
+    DBuf<unsigned long long> cnt;
+    cnt.alloc(1);
+    const double tol = fmax(1e-15, sqrt((double)m) * 1.1102230246251565e-16);
+    // absolute floor: (1e-15 ||A||_F)^2, far below the couplings of rows that carry information
+    double abs_floor = 0.0;
+    if (m > 0) {
+        row_norms_kernel<<<m, 256, 0, s>>>(A, n, lda, sigma);
+        WT_LAUNCH("row norms");
+        std::vector<double> h(m);
+        WT_CUDA(cudaMemcpyAsync(h.data(), sigma, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+        WT_CUDA(cudaStreamSynchronize(s));
+        double f2 = 0.0;
+        for (double x : h) f2 += x * x;
+        abs_floor = 1e-30 * f2;
+    }
+    int sweeps = 0;
+    bool converged = m < 2;
+    for (; sweeps < max_sweeps && !converged; ++sweeps) {
+        WT_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+        for (int r = 0; r < mp - 1; ++r)
+            osj_round_kernel<<<mp / 2, 256, 0, s>>>(A, n, lda, V, m, mp, m, r, tol, abs_floor, cnt.p);
+        WT_LAUNCH("one-sided Jacobi sweep");
+        unsigned long long h = 0;
+        WT_CUDA(cudaMemcpyAsync(&h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        WT_CUDA(cudaStreamSynchronize(s));
+        converged = (h == 0);
+    }
+    if (m > 0) {
+        row_norms_kernel<<<m, 256, 0, s>>>(A, n, lda, sigma);
+        WT_LAUNCH("row norms");
+    }
+    if (!converged) {
+        int v = DERR_TIMEOUT;
+        WT_CUDA(cudaMemcpyAsync(d_err, &v, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    WT_CUDA(cudaStreamSynchronize(s));
+    return sweeps;
+}
+
+__global__ void gather_rows_scaled_kernel(const double* __restrict__ A, int n, int lda, const int* __restrict__ idx,
+                                          const double* __restrict__ scale, double* __restrict__ out) {
+    const int r = blockIdx.y;
+    const double* a = A + (size_t)idx[r] * lda;
+    const double f = scale[r];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[(size_t)r * n + k] = f * a[k];
+}
+
+void gather_rows_scaled(cudaStream_t s, const double* A, int n, int lda, const int* idx, const double* scale,
+                        int rows, double* out) {
+    if (rows < 1) return;
+    dim3 g((unsigned)std::min(64, (n + 255) / 256), (unsigned)rows);
+    gather_rows_scaled_kernel<<<g, 256, 0, s>>>(A, n, lda, idx, scale, out);
+    WT_LAUNCH("gather rows");
 }
 
 }  // namespace wt

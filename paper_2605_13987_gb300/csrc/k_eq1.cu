@@ -9,6 +9,9 @@
 // every output time accumulates its lags in FP64.
 #include "wt_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 namespace wt {
@@ -234,8 +237,9 @@ void eq1_pack_lag64(void* dst, int n, double w0, double w1) { *static_cast<Eq1La
 // ------------------------------------------------------------------------
 // Allocation-free variant (wt_eq1_noalloc).  The per-call lag table lives in
 // this fixed device array instead of a cudaMalloc'd buffer; every GPU that
-// loads the library holds it (192 KB) until the process exits.
-constexpr int kEq1NoAllocMaxOut = 16384;
+// loads the library holds it (12 B x WT_EQ1_NOALLOC_MAX_OUT = 192 KB) until the
+// process exits.  The limit is the one the header documents.
+constexpr int kEq1NoAllocMaxOut = WT_EQ1_NOALLOC_MAX_OUT;
 static __device__ __align__(256) Eq1Lag g_eq1_lag_scratch[kEq1NoAllocMaxOut];
 
 // Lag table on the device from the relaxation's time samples: same rule as
@@ -267,13 +271,42 @@ __global__ void eq1_lag_table_kernel(const double* __restrict__ t, int nt, doubl
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-Eq1Lag* g_noalloc_ptr[kMaxDevices] = {};   // device address of the scratch, per device
+// Device address of the scratch per device, and the id of the CUDA context it
+// was looked up in: a context created anew on the device (after a
+// cudaDeviceReset, say) reloads the module, so the address is looked up again.
+struct ScratchAddr {
+    Eq1Lag* p = nullptr;
+    unsigned long long ctx_id = 0;
+};
+ScratchAddr g_noalloc_addr[kMaxDevices];
+
+// id of the current CUDA context (unique for the life of the process), through
+// the runtime's driver entry points (no libcuda link)
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        WT_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &qa));
+        WT_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb));
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            fail(WT_ERR_CUDA, "cuCtxGetCurrent / cuCtxGetId unavailable");
+        get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(a);
+        get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(b);
+    }
+    CUcontext cx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&cx) != CUDA_SUCCESS || !cx || get_id(cx, &id) != CUDA_SUCCESS)
+        fail(WT_ERR_CUDA, "no current CUDA context for the allocation-free scratch");
+    return id;
 }
+}  // namespace
 
-int eq1_noalloc_max_out() { return kEq1NoAllocMaxOut; }
-
-// The caller's device is current.  Resolves the scratch address on first use
-// on this device (the symbol's host-side name is not a device address).
+// The caller's device is current.  Resolves the scratch address on the first
+// call in this device's current context (the symbol's host-side name is not a
+// device address); later calls in the same context reuse it.
 void eq1_noalloc_launch(cudaStream_t s, int device, const float* H, int Nx, int Ny, int Nz, const double* d_times,
                         int nt, double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
                         const float* vx, const float* vy, const float* vz, const float* q, float qconst,
@@ -285,16 +318,19 @@ void eq1_noalloc_launch(cudaStream_t s, int device, const float* H, int Nx, int 
     Eq1Lag* lags = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[device]) {
+        const unsigned long long id = current_context_id();
+        ScratchAddr& a = g_noalloc_addr[device];
+        if (!a.p || a.ctx_id != id) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_eq1_lag_scratch);
             if (e != cudaSuccess || !p) {
                 cudaGetLastError();
                 fail(WT_ERR_CUDA, std::string("cudaGetSymbolAddress(eq1 scratch): ") + cudaGetErrorString(e));
             }
-            g_noalloc_ptr[device] = static_cast<Eq1Lag*>(p);
+            a.p = static_cast<Eq1Lag*>(p);
+            a.ctx_id = id;
         }
-        lags = g_noalloc_ptr[device];
+        lags = a.p;
     }
     eq1_lag_table_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(d_times, nt, dt, n_out, lags);
     WT_LAUNCH("eq1_lag_table");

@@ -70,6 +70,16 @@ struct Fast32 {
     // mode 0: the field, 1: its lateral-scale derivative; lb: (x, y) lines per z-pass block (16, 32, 64)
     void fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
                 cudaStream_t s, int mode = 0, int lb = 32) const;
+    // deposit and plane passes only: R [nb][3][Nz][Ny][Nx] (plane layout [y][x])
+    void lateral(const float* Zc, int nb, float* rho, float* R, cudaStream_t s, int mode = 0) const;
+    // z pass of rows y0 .. y0 + ys - 1: R [nb][3][Nz][ys][Nx] -> out[b * out_sb + c * out_sc + (x Ny + y) Nz + z]
+    void zlines(const float* R, int nb, int y0, int ys, float* out, size_t out_sb, size_t out_sc, cudaStream_t s,
+                int lb) const;
 };
+
+// R[b][a][kz][j] = sum_c Zc[b][c][kz] T[c][a][kz][off + j] for j < nl, b < r <= 32: the planes of the
+// per-column lateral tables T [n_cols][3][Nz][nxy] combined by the basis vectors' column z-transforms.
+void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
+                    size_t off, int nl, float* R);
 
 }  // namespace wt

@@ -190,9 +190,7 @@ void Fast32::set_radix(int r_xy, int r_z, bool z_two_pass, bool y_two_pass, bool
     xsm = x_two_pass;
 }
 
-void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
-                    cudaStream_t s, int mode, int lb) const {
-    if (lb != 16 && lb != 32 && lb != 64) fail(WT_ERR_ARG, "z-pass lines per block must be 16, 32 or 64");
+void Fast32::lateral(const float* Zc, int nb, float* rho, float* R, cudaStream_t s, int mode) const {
     C2<float>* rc = reinterpret_cast<C2<float>*>(rho);
     dim3 gd(g.Nz, nb, F32_DEP_SPLIT);
     f32_deposit_kernel<<<gd, 256, deposit_smem(g, n_cols), s>>>(g, n_cols, reinterpret_cast<const C2<float>*>(phx.p),
@@ -202,14 +200,25 @@ void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, s
     const C2<float>* ty = reinterpret_cast<const C2<float>*>(tw_y.p);
     const C2<float>* tx = reinterpret_cast<const C2<float>*>(tw_x.p);
     plane_launch(xsm ? 0 : rxy, xdirect, ysm ? g.Ny : 0, gp, s, g, rc, ty, tx, R, mode);
+}
 
-    const size_t nxy = (size_t)g.Nx * g.Ny;
-    dim3 gz((unsigned)((nxy + lb - 1) / lb), 3, nb);
+void Fast32::zlines(const float* R, int nb, int y0, int ys, float* out, size_t out_sb, size_t out_sc, cudaStream_t s,
+                    int lb) const {
+    if (lb != 16 && lb != 32 && lb != 64) fail(WT_ERR_ARG, "z-pass lines per block must be 16, 32 or 64");
+    if (y0 < 0 || ys < 1 || y0 + ys > g.Ny) fail(WT_ERR_ARG, "z-pass rows out of range");
+    const size_t nl = (size_t)g.Nx * ys;
+    dim3 gz((unsigned)((nl + lb - 1) / lb), 3, nb);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(tw_z.p);
     const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
-    if (zsm) zpass2_launch(lb, gz, s, g, R, tz, zz, out, out_sb, out_sc);
-    else zpass_launch(rz, lb, gz, s, g, R, tz, zz, out, out_sb, out_sc);
+    const ZLines zl{ys, y0};
+    if (zsm) zpass2_launch(lb, gz, s, g, R, tz, zz, out, out_sb, out_sc, zl);
+    else zpass_launch(rz, lb, gz, s, g, R, tz, zz, out, out_sb, out_sc, zl);
+}
 
+void Fast32::fields(const float* Zc, int nb, float* rho, float* R, float* out, size_t out_sb, size_t out_sc,
+                    cudaStream_t s, int mode, int lb) const {
+    lateral(Zc, nb, rho, R, s, mode);
+    zlines(R, nb, 0, g.Ny, out, out_sb, out_sc, s, lb);
 }
 
 }  // namespace wt

@@ -35,6 +35,12 @@ inline size_t zpass_smem(const GridDev& g, int lb, int R) {
     return ((size_t)(lb / 2) * S + 2 * (size_t)g.Nz + (size_t)g.Nz / R + 1) * sizeof(C2<float>);
 }
 
+// Lines of a z pass: the staged planes hold rows y0 .. y0 + ys - 1 (every x) of each k_z plane,
+// laid out [y - y0][x]; the outputs go to H's point order (x Ny + y) Nz + z of the full grid.
+struct ZLines {
+    int ys, y0;
+};
+
 // Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.
 // r = 0 with ny2: the two-pass x transforms as well
 void plane_allow(int r, int ny2, size_t smem);
@@ -43,12 +49,12 @@ void plane_launch(int r, bool xdirect, int ny2, dim3 grid, cudaStream_t s, const
                   const C2<float>* twy, const C2<float>* twx, float* R, int mode);
 void zpass_allow(int r, size_t smem);
 void zpass_launch(int r, int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
-                  const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc);
+                  const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc, ZLines zl);
 // Two-pass shared-memory z FFT (k_fft32_z2.cu), Nz in {64, 128, 256}.
 bool zpass2_supported(int nz);
 size_t zpass2_smem(int A, int B, int lb);
 void zpass2_allow(int nz);
 void zpass2_launch(int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
-                   const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc);
+                   const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc, ZLines zl);
 
 }  // namespace wt

@@ -1,0 +1,127 @@
+// FP32 basis fields from per-column lateral tables.
+//
+// Sec. 3 builds the potential from rescaled and translated chunks of the
+// fundamental solution.  In the spectral form used here every column c
+// contributes, for each z mode k_z and field component a, a lateral field
+//
+//   T_c[a][k_z](x, y) = IFFT_2D( multiplier_a(k) e^{-i (k_x x_c + k_y y_c)} )
+//
+// that depends on the geometry only (grid, column position), not on the
+// charges.  A basis charge vector b enters only through its column
+// z-transforms Z[b][c][k_z], so the per-plane fields that the z pass turns
+// into basis fields are the linear combination
+//
+//   R[b][a][k_z](x, y) = sum_c Z[b][c][k_z] T_c[a][k_z](x, y),
+//
+// the same sum that the deposit forms in the spectral domain, moved after
+// the lateral transform.  The tables are built once per context with the
+// deposit and plane kernels (a unit z-transform per column); an extension then
+// needs this combination and the z pass only.  The combination runs over
+// slabs of y rows so that the slab's planes stay in L2 for the z pass.
+#include "k_fft32_common.cuh"
+
+#include <type_traits>
+
+namespace wt {
+
+// One block of 128 threads per (line chunk, k_z, component); each thread takes VEC
+// consecutive lines and accumulates RB basis vectors in registers.  The block first stages
+// its table tile T[c][a][k_z][its lines] for every column in shared memory, all loads in
+// flight together (eight per thread at a time), so that the column loop runs on shared
+// memory; the z-transform coefficients Z[b][c][k_z] sit beside it as [c][RB].
+// T: [n_cols][3][Nz][nxy] (plane layout [y][x]); Zc: [nb][n_cols][Nz];
+// R: [r][3][Nz][nl], line j of the slab = line off + j of the plane.
+template <int RB, int VEC>
+__global__ void __launch_bounds__(128) column_combine_kernel(const float* __restrict__ T,
+                                                             const float* __restrict__ Zc, int r, int n_cols,
+                                                             int Nz, size_t nxy, size_t off, int nl,
+                                                             float* __restrict__ R) {
+    using V = typename std::conditional<VEC == 4, float4, typename std::conditional<VEC == 2, float2, float>::type>::type;
+    constexpr int LPB = 128 * VEC;                    // lines per block
+    extern __shared__ __align__(16) float smem[];
+    float* zs = smem;                                 // [n_cols][RB]
+    V* ts = reinterpret_cast<V*>(smem + n_cols * RB); // [n_cols][128] vectors of VEC lines
+    const int kz = blockIdx.y, comp = blockIdx.z;
+    for (int e = threadIdx.x; e < n_cols * RB; e += blockDim.x) {
+        const int c = e / RB, b = e % RB;
+        zs[e] = b < r ? Zc[((size_t)b * n_cols + c) * Nz + kz] : 0.f;
+    }
+    const int j0 = blockIdx.x * LPB;
+    const int j = j0 + threadIdx.x * VEC;
+    const bool act = j < nl;                          // nl is a multiple of VEC
+    const size_t cstride = (size_t)3 * Nz * nxy;
+    const float* tp = T + ((size_t)comp * Nz + kz) * nxy + off + (act ? j : 0);
+    for (int c0 = 0; c0 < n_cols; c0 += 8) {
+        V q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (act && c0 + u < n_cols) q[u] = *reinterpret_cast<const V*>(tp + (c0 + u) * cstride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (act && c0 + u < n_cols) ts[(c0 + u) * 128 + threadIdx.x] = q[u];
+    }
+    __syncthreads();
+    if (!act) return;
+    float acc[RB][VEC];
+#pragma unroll
+    for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[b][v] = 0.f;
+    for (int c = 0; c < n_cols; ++c) {
+        const V q = ts[c * 128 + threadIdx.x];
+        const float* t = reinterpret_cast<const float*>(&q);
+        const float4* z4 = reinterpret_cast<const float4*>(zs + c * RB);
+#pragma unroll
+        for (int b4 = 0; b4 < RB / 4; ++b4) {
+            const float4 z = z4[b4];
+            const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[4 * b4 + i][v] = fmaf(zz[i], t[v], acc[4 * b4 + i][v]);
+        }
+    }
+    float* rp = R + ((size_t)comp * Nz + kz) * nl + j;
+    const size_t bstride = (size_t)3 * Nz * nl;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+        if (b >= r) break;
+        V o;
+        float* of = reinterpret_cast<float*>(&o);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) of[v] = acc[b][v];
+        *reinterpret_cast<V*>(rp + b * bstride) = o;
+    }
+}
+
+template <int RB, int VEC>
+static void combine_launch(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
+                           size_t off, int nl, float* R) {
+    const size_t sh = (size_t)n_cols * (RB + 128 * VEC) * sizeof(float);
+    allow_dyn_smem(column_combine_kernel<RB, VEC>, sh);
+    dim3 gd((unsigned)((nl + 128 * VEC - 1) / (128 * VEC)), (unsigned)Nz, 3);
+    column_combine_kernel<RB, VEC><<<gd, 128, sh, s>>>(T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+}
+
+void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
+                    size_t off, int nl, float* R) {
+    if (r < 1 || r > 32) fail(WT_ERR_ARG, "column combination: rank must be 1..32");
+    if (n_cols < 1 || n_cols > 96) fail(WT_ERR_UNSUPPORTED, "the lateral tables take 1 to 96 columns");
+    // vectors of VEC lines when every line chunk starts aligned to them
+    const uintptr_t al = reinterpret_cast<uintptr_t>(T) | reinterpret_cast<uintptr_t>(R);
+    const bool v4 = (off % 4 == 0) && (nl % 4 == 0) && (nxy % 4 == 0) && (al % 16 == 0);
+    const bool v2 = (off % 2 == 0) && (nl % 2 == 0) && (nxy % 2 == 0) && (al % 8 == 0);
+    if (r <= 8) {
+        if (v4) combine_launch<8, 4>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+        else combine_launch<8, 1>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+    } else if (r <= 16) {
+        if (v4) combine_launch<16, 4>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+        else combine_launch<16, 1>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+    } else {
+        if (v2) combine_launch<32, 2>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+        else combine_launch<32, 1>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+    }
+    WT_LAUNCH("column_combine");
+}
+
+}  // namespace wt

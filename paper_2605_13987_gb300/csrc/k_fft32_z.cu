@@ -26,10 +26,10 @@ template <int RZ, int LB>
 __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev g, const float* __restrict__ R,
                                                         const C2<float>* __restrict__ twz,
                                                         const C2<float>* __restrict__ zsh, float* __restrict__ out,
-                                                        size_t out_sb, size_t out_sc) {
+                                                        size_t out_sb, size_t out_sc, ZLines zl) {
     extern __shared__ unsigned char smem_raw[];
     const int nx = g.Nx, ny = g.Ny, nz = g.Nz;
-    const size_t nxy = (size_t)nx * ny;
+    const size_t nxy = (size_t)nx * zl.ys;      // staged lines: rows y0 .. y0 + ys - 1 of each plane
     const int comp = blockIdx.y, b = blockIdx.z;
     const size_t L0 = (size_t)blockIdx.x * LB;
     const int S = zpass_pitch(nz, RZ);                                      // odd pair pitch
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
         __syncwarp();
         if (!act) continue;
         const size_t La = L0 + 2 * f, Lb = La + 1;
-        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)nz;
-        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)nz;
+        const size_t pa = ((La % nx) * ny + zl.y0 + La / nx) * (size_t)nz;
+        const size_t pb = ((Lb % nx) * ny + zl.y0 + Lb / nx) * (size_t)nz;
         if (Lb < nxy) {
             for (int z = gl; z < nz; z += W) {      // one 64-bit read per lane feeds both lines
                 const C2<float> y = cf[z + (z >> 4)];
@@ -114,13 +114,13 @@ void zpass_allow(int r, size_t sz) {
 }
 
 void zpass_launch(int r, int lb, dim3 gz, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* tz,
-                  const C2<float>* zz, float* out, size_t out_sb, size_t out_sc) {
+                  const C2<float>* zz, float* out, size_t out_sb, size_t out_sc, ZLines zl) {
     const size_t sz = zpass_smem(g, lb, r);
     switch (r) {
 #define WT_CASE(RR) case RR: \
-        if (lb == 16) f32_zpass_kernel<RR, 16><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else if (lb == 32) f32_zpass_kernel<RR, 32><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else f32_zpass_kernel<RR, 64><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        if (lb == 16) f32_zpass_kernel<RR, 16><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
+        else if (lb == 32) f32_zpass_kernel<RR, 32><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
+        else f32_zpass_kernel<RR, 64><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
         break;
         WT_FOR_EACH_R(WT_CASE)
 #undef WT_CASE

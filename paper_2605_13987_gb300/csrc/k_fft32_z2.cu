@@ -27,11 +27,11 @@ template <int A, int B, int LB>
 __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const float* __restrict__ R,
                                                             const C2<float>* __restrict__ twz,
                                                             const C2<float>* __restrict__ zsh, float* __restrict__ out,
-                                                            size_t out_sb, size_t out_sc) {
+                                                            size_t out_sb, size_t out_sc, ZLines zl) {
     constexpr int N = A * B, S = zpass2_pitch(A, B), G = 32 / A, NP = LB / 2;
     extern __shared__ unsigned char smem_raw[];
     const int nx = g.Nx, ny = g.Ny;
-    const size_t nxy = (size_t)nx * ny;
+    const size_t nxy = (size_t)nx * zl.ys;      // staged lines: rows y0 .. y0 + ys - 1 of each plane
     const int comp = blockIdx.y, b = blockIdx.z;
     const size_t L0 = (size_t)blockIdx.x * LB;
     C2<float>* cs = reinterpret_cast<C2<float>*>(smem_raw);                 // [NP][S]
@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
         __syncwarp();
         if (!act) continue;
         const size_t La = L0 + 2 * f, Lb = La + 1;
-        const size_t pa = ((La % nx) * ny + La / nx) * (size_t)N;
-        const size_t pb = ((Lb % nx) * ny + Lb / nx) * (size_t)N;
+        const size_t pa = ((La % nx) * ny + zl.y0 + La / nx) * (size_t)N;
+        const size_t pb = ((Lb % nx) * ny + zl.y0 + Lb / nx) * (size_t)N;
         if (Lb < nxy) {
             for (int z = gl; z < N; z += A) {     // one 64-bit read per lane feeds both lines
                 const C2<float> y = cf[(z & 1) ? N / 2 + 8 + (z >> 1) : (z >> 1)];
@@ -147,16 +147,16 @@ void zpass2_allow(int nz) {
 }
 
 void zpass2_launch(int lb, dim3 gz, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* tz,
-                   const C2<float>* zz, float* out, size_t out_sb, size_t out_sc) {
+                   const C2<float>* zz, float* out, size_t out_sb, size_t out_sc, ZLines zl) {
     if (!zpass2_supported(g.Nz)) fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 128, 256}");
     int A, B;
     z2_shape(g.Nz, &A, &B);
     const size_t sz = zpass2_smem(A, B, lb);
 #define WT_CASE(AA, BB) \
     if (A == AA && B == BB) { \
-        if (lb == 16) f32_zpass2_kernel<AA, BB, 16><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else if (lb == 32) f32_zpass2_kernel<AA, BB, 32><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
-        else f32_zpass2_kernel<AA, BB, 64><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc); \
+        if (lb == 16) f32_zpass2_kernel<AA, BB, 16><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
+        else if (lb == 32) f32_zpass2_kernel<AA, BB, 32><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
+        else f32_zpass2_kernel<AA, BB, 64><<<gz, 256, sz, s>>>(g, R, tz, zz, out, out_sb, out_sc, zl); \
     }
     WT_FOR_EACH_Z2(WT_CASE)
 #undef WT_CASE

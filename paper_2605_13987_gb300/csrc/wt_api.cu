@@ -4,6 +4,9 @@
 #include "wt_internal.cuh"
 #include "k_fft.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -129,6 +132,10 @@ struct wt_ctx {
     Spectral<double> sp64;
     bool sp_ready = false;
     DBuf<float> Zc32, rho32, R32, E32;
+    // per-column lateral tables of the FP32 path ([n_cols][3][Nz][Ny][Nx], geometry only; built once)
+    // and the slab buffer of the combined planes ([32][3][Nz][ys][Nx])
+    DBuf<float> T32, Rsl;
+    bool t32_ready = false;
     DBuf<double> Zc64, G64;
     DBuf<float> stage32;
     DBuf<double> stage64;
@@ -144,11 +151,14 @@ struct wt_ctx {
     bool timing = false;
     bool use_tc = true;          // WT_EXPAND=simt selects the FP32 FMA expansion
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_noalloc = nullptr;    // last wt_eq1_noalloc call, on the caller's stream
+    bool noalloc_pending = false;
     bool ev_recorded = false;
     int last_launches = 0;
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
     int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_vec = 4;
+    int tune_ys = 0;                 // > 0: basis fields from the lateral tables, y slabs of tune_ys rows
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -195,6 +205,36 @@ bool is_device_ptr(const void* p) {
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Empty when [p, p + bytes) is device memory of device `dev` inside one
+// allocation (or managed memory); otherwise why not.  The allocation's extent
+// comes from cuMemGetAddressRange (through the runtime's driver entry point).
+std::string device_span_problem(const void* p, size_t bytes, int dev) {
+    if (!p) return "NULL buffer";
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return "not device memory"; }
+    if (a.type == cudaMemoryTypeManaged) return "";
+    if (a.type != cudaMemoryTypeDevice) return "not device memory";
+    if (a.device != dev) return "device memory of device " + std::to_string(a.device) + ", the context is on " +
+                                std::to_string(dev);
+    static PFN_cuMemGetAddressRange_v3020 range = nullptr;
+    if (!range) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        WT_CUDA(cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 3020, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !f) fail(WT_ERR_CUDA, "cuMemGetAddressRange unavailable");
+        range = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(f);
+    }
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (range(&base, &size, reinterpret_cast<CUdeviceptr>(p)) != CUDA_SUCCESS) return "not device memory";
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+    if (lo + bytes > (uintptr_t)base + size)
+        return "buffer too small: " + std::to_string(bytes) + " bytes needed, " +
+               std::to_string((uintptr_t)base + size - lo) + " in its allocation";
+    return "";
 }
 
 void validate_geometry(const wt_ctx* c) {
@@ -517,64 +557,96 @@ void charges_at(wt_ctx* c, const double* d_t, int nt, double* Q) {
     add_column_vector(s, Q, ns, nt, c->qinf.p);
 }
 
-// Rank-r (r <= 32) time basis of a charge history Q [ns][nt] (Gram matrix +
-// Jacobi, singular values above 1e-9 of the largest): basis charge vectors
-// Ub [r][ns] (unit norm) and FP32 coefficients W32 [nt][32] = sigma_m w_m[t].
+// Time basis of a charge history Q [ns][nt] for the FP32 path: the singular
+// value decomposition Q = sum_i sigma_i u_i v_i^T by one-sided Jacobi on the
+// rows of Q^T (no Gram matrix: the small singular values keep their relative
+// accuracy), then the smallest rank r <= 32 whose truncation error in every
+// time sample, ||q(t_n) - sum_{i<r} sigma_i u_i v_i[n]|| / ||q(t_n)||, is at
+// most kTruncTarget (the FP32 rounding level).  The error is exact from the
+// decomposition: the squared tail sum_{i>=r} (sigma_i v_i[n])^2, summed from
+// the smallest term up.  Samples whose charge is below kTruncFloor of the
+// largest one are measured against that floor (tangent histories can vanish
+// at some times).  Outputs: basis charge vectors Ub [r][ns] (unit norm),
+// FP32 coefficients W32 [nt][32] = sigma_m v_m[n], r, and the largest
+// per-sample truncation at r (trunc_out).
+constexpr double kTruncTarget = 1e-7;
+constexpr double kTruncLimit = 1e-6;     // the FP32 field paths refuse a basis truncated beyond this
+constexpr double kTruncFloor = 1e-6;
 void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf<float>& W32, int& rank_out,
                       double& trunc_out) {
     cudaStream_t s = c->s;
     const int ns = c->ns;
-    DBuf<double> Gt, Wg, lam;
-    Gt.alloc((size_t)nt * nt);
-    dgemm(s, true, false, nt, nt, ns, 1.0, Q, nt, Q, nt, 0.0, Gt.p, nt);
-    Wg.alloc((size_t)nt * nt);
-    lam.alloc(nt);
-    // couplings below the rounding level of the Gram matrix (1e-15 of its trace) are left alone
-    DBuf<double> dg;
-    dg.alloc(nt);
-    get_diag(s, Gt.p, nt, nt, dg.p);
-    std::vector<double> hd(nt);
-    dg.download(hd.data(), nt, s);
-    WT_CUDA(cudaStreamSynchronize(s));
-    double trace = 0;
-    for (double x : hd) trace += x;
+    DBuf<double> A, V, sig;
+    A.alloc((size_t)nt * ns);
+    transpose(s, Q, ns, nt, A.p);                 // rows = time samples
+    V.alloc((size_t)nt * nt);
+    sig.alloc(nt);
     clear_err(c);
-    jacobi_eig(s, Gt.p, nt, lam.p, Wg.p, c->d_err.p, 40, 1e-15 * trace);
-    if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver (time basis) did not converge");
-    std::vector<double> hl(nt), hw((size_t)nt * nt);
-    lam.download(hl.data(), nt, s);
-    Wg.download(hw.data(), (size_t)nt * nt, s);
+    onesided_jacobi_rows(s, A.p, nt, ns, ns, V.p, sig.p, c->d_err.p);
+    if (read_err(c)) fail(WT_ERR_TIMEOUT, "one-sided Jacobi (time basis) did not converge");
+    std::vector<double> hs(nt), hv((size_t)nt * nt);
+    sig.download(hs.data(), nt, s);
+    V.download(hv.data(), (size_t)nt * nt, s);
     WT_CUDA(cudaStreamSynchronize(s));
     std::vector<int> ord(nt);
     std::iota(ord.begin(), ord.end(), 0);
-    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return hl[a] > hl[b]; });
-    const double s0 = std::sqrt(std::max(hl[ord[0]], 0.0));
-    const int r_max = std::min(32, nt);
-    int r = 0;
-    while (r < r_max && s0 > 0 && std::sqrt(std::max(hl[ord[r]], 0.0)) > 1e-9 * s0) ++r;
-    if (r < 1) r = 1;
-    rank_out = r;
-    trunc_out = (r < nt && s0 > 0) ? std::sqrt(std::max(hl[ord[r]], 0.0)) / s0 : 0.0;
-    const int rp = 32;
-    std::vector<double> wsel((size_t)nt * r), coef((size_t)nt * rp, 0.0);
-    for (int m = 0; m < r; ++m) {
-        const double sg = std::sqrt(std::max(hl[ord[m]], 0.0));
-        for (int tt = 0; tt < nt; ++tt) {
-            const double wv = hw[(size_t)tt * nt + ord[m]];
-            wsel[(size_t)tt * r + m] = sg > 0 ? wv / sg : 0.0;
-            coef[(size_t)tt * rp + m] = sg * wv;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hs[a] > hs[b]; });
+    // per-sample squared norms and suffix (tail) sums, smallest terms first
+    auto term = [&](int j, int n) {
+        const double x = hs[ord[j]] * hv[(size_t)ord[j] * nt + n];
+        return x * x;
+    };
+    std::vector<double> norm2(nt, 0.0);
+    for (int n = 0; n < nt; ++n)
+        for (int j = nt - 1; j >= 0; --j) norm2[n] += term(j, n);
+    double nmax = 0.0;
+    for (double v : norm2) nmax = std::max(nmax, std::sqrt(v));
+    const int r_cap = std::min(fault_enabled("rank_cap") ? 4 : 32, nt);    // WT_FAULT=rank_cap: the guard's test
+    // worst per-sample truncation for every r <= r_cap
+    std::vector<double> worst(r_cap + 1, 0.0);
+    std::vector<double> tail(nt, 0.0);
+    for (int j = nt - 1; j >= 0; --j) {
+        for (int n = 0; n < nt; ++n) tail[n] += term(j, n);
+        if (j <= r_cap) {
+            double w = 0.0;
+            for (int n = 0; n < nt; ++n)
+                w = std::max(w, std::sqrt(tail[n]) / std::max(std::sqrt(norm2[n]), kTruncFloor * nmax));
+            worst[j] = nmax > 0 ? w : 0.0;
         }
     }
-    DBuf<double> dws, Ubt, dcoef;
-    dws.upload(wsel.data(), wsel.size(), s);
-    Ubt.alloc((size_t)ns * r);
-    dgemm(s, false, false, ns, r, nt, 1.0, Q, nt, dws.p, r, 0.0, Ubt.p, r);
+    int r = 1;
+    while (r < r_cap && worst[r] > kTruncTarget) ++r;
+    if (r < r_cap && hs[ord[r]] <= 0.0) r = std::max(1, r);
+    rank_out = r;
+    trunc_out = r < nt ? worst[r] : 0.0;
+    const int rp = 32;
+    std::vector<double> coef((size_t)nt * rp, 0.0), scale(r);
+    std::vector<int> idx(r);
+    for (int m = 0; m < r; ++m) {
+        const double sg = hs[ord[m]];
+        idx[m] = ord[m];
+        scale[m] = sg > 0 ? 1.0 / sg : 0.0;
+        for (int n = 0; n < nt; ++n) coef[(size_t)n * rp + m] = sg * hv[(size_t)ord[m] * nt + n];
+    }
+    DBuf<int> didx;
+    DBuf<double> dscale, dcoef;
+    didx.upload(idx.data(), r, s);
+    dscale.upload(scale.data(), r, s);
     Ub.alloc((size_t)r * ns);
-    transpose(s, Ubt.p, ns, r, Ub.p);
+    gather_rows_scaled(s, A.p, ns, ns, didx.p, dscale.p, r, Ub.p);
     dcoef.upload(coef.data(), coef.size(), s);
     W32.alloc(coef.size());
     to_float(s, dcoef.p, coef.size(), 1.0, W32.p);
     WT_CUDA(cudaStreamSynchronize(s));
+}
+
+// The FP32 field paths expand the relaxation's time basis: refuse one that cannot carry the
+// FP32 accuracy (a charge history that needs more than 32 basis vectors).
+void require_fp32_basis(const wt_ctx* c) {
+    if (c->info.trunc_rel > kTruncLimit)
+        fail(WT_ERR_ACCURACY, "the charge history needs a time basis of rank > 32: the rank-32 basis leaves " +
+                                  std::to_string(c->info.trunc_rel) +
+                                  " relative error in a time sample (limit 1e-6); use WT_FP64");
 }
 
 void do_relax(wt_ctx* c, const double* t, int nt) {
@@ -687,6 +759,12 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
     copy_block(s, U.p, n1, c->Vm.p, n1, n1, n1);
     U.release();
     // q(t_n) = q_inf + Cn H [0; V (amp * exp(-mu t_n))]
+    // an allocation-free Eq. 1 call may still read the previous time samples on its own stream
+    if (c->noalloc_pending) {
+        WT_CUDA(cudaStreamWaitEvent(s, c->ev_noalloc, 0));
+        c->noalloc_pending = false;
+    }
+    if (!c->ev_noalloc) WT_CUDA(cudaEventCreateWithFlags(&c->ev_noalloc, cudaEventDisableTiming));
     c->d_times.upload(t, nt, s);
     DBuf<double> Q;
     Q.alloc((size_t)ns * nt);
@@ -728,7 +806,58 @@ void ensure_spectral(wt_ctx* c) {
 // Basis fields E32[c][m][p] (m < r) of the charge vectors Ub (column transform and the
 // spectral passes), at the context's launch shapes.  Marks E32 as the relaxation's own fields
 // when Ub is the context's basis (mode 0), as anything else otherwise.
+// Bytes of the lateral tables of a context, and whether they are worth holding: at most 16 GiB and
+// a quarter of the device memory free now.
+size_t tables_bytes(const wt_ctx* c) {
+    const wt_grid& g = c->grid;
+    return c->cols.size() * (size_t)3 * g.Nz * g.Nx * g.Ny * sizeof(float);
+}
+bool tables_fit(const wt_ctx* c) {
+    if (c->t32_ready) return true;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return false; }
+    const size_t b = tables_bytes(c);
+    return b <= ((size_t)16 << 30) && b <= fr / 4 && c->cols.size() <= 96;
+}
+
+// The lateral tables T_c (Sec. 3's fundamental-solution chunks in spectral form): the deposit and
+// plane passes of one unit column z-transform per column, at the context's FFT shapes.
+void build_tables(wt_ctx* c) {
+    if (c->t32_ready) return;
+    const wt_grid& g = c->grid;
+    const int ncol = (int)c->cols.size();
+    const size_t nxy = (size_t)g.Nx * g.Ny;
+    cudaStream_t s = c->s;
+    c->T32.alloc((size_t)ncol * 3 * g.Nz * nxy);
+    std::vector<float> unit((size_t)ncol * ncol * g.Nz, 0.f);     // [k][c][kz] = (c == k)
+    for (int k = 0; k < ncol; ++k)
+        for (int z = 0; z < g.Nz; ++z) unit[((size_t)k * ncol + k) * g.Nz + z] = 1.f;
+    DBuf<float> Zu;
+    Zu.upload(unit.data(), unit.size(), s);
+    c->rho32.alloc(c->sp32.rho_elems(std::max(1, c->tune_nb)));
+    for (int k = 0; k < ncol; ++k)
+        c->sp32.lateral(Zu.p + (size_t)k * ncol * g.Nz, 1, c->rho32.p, c->T32.p + (size_t)k * 3 * g.Nz * nxy, s, 0);
+    WT_CUDA(cudaStreamSynchronize(s));
+    c->t32_ready = true;
+}
+
+// Basis fields of Zc [r][n_cols][Nz] from the lateral tables: per slab of ys y rows, the
+// combination of the tables' planes (into the L2-sized slab buffer) and the z pass.
+void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
+    const wt_grid& g = c->grid;
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz, nxy = (size_t)g.Nx * g.Ny;
+    const int ncol = (int)c->cols.size(), ys = c->tune_ys;
+    c->Rsl.alloc((size_t)32 * 3 * g.Nz * g.Nx * ys);
+    for (int y0 = 0; y0 < g.Ny; y0 += ys) {
+        const int yn = std::min(ys, g.Ny - y0);
+        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p);
+        c->sp32.zlines(c->Rsl.p, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, s, c->tune_lb);
+    }
+}
+bool use_tables(const wt_ctx* c, int mode) { return mode == 0 && c->tune_ys > 0 && c->t32_ready; }
+
 void basis_fields32(wt_ctx* c, const double* Ub, int r, cudaStream_t s, int mode, int* launches, bool timing) {
+    if (Ub == c->Ub.p) require_fp32_basis(c);
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size();
@@ -745,11 +874,16 @@ void basis_fields32(wt_ctx* c, const double* Ub, int r, cudaStream_t s, int mode
     column_ztransform<float>(s, Ub, r, c->ns, c->ns, c->zcos.p, c->d_col_off.p, ncol, g.Nz, c->Zc32.p);
     *launches += 1;
     if (timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
-    for (int m0 = 0; m0 < r; m0 += nb) {
-        const int b = std::min(nb, r - m0);
-        c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p, c->E32.p + (size_t)m0 * npts,
-                       npts, (size_t)rp * npts, s, mode, c->tune_lb);
-        *launches += 3;
+    if (use_tables(c, mode)) {
+        spectral_tables(c, c->Zc32.p, r, s);
+        *launches += 2 * ((g.Ny + c->tune_ys - 1) / c->tune_ys);
+    } else {
+        for (int m0 = 0; m0 < r; m0 += nb) {
+            const int b = std::min(nb, r - m0);
+            c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p,
+                           c->E32.p + (size_t)m0 * npts, npts, (size_t)rp * npts, s, mode, c->tune_lb);
+            *launches += 3;
+        }
     }
     if (timing) WT_CUDA(cudaEventRecord(c->ev[2], s));
     if (mode == 0 && Ub == c->Ub.p && r == c->rank) c->e32_stamp = c->version;
@@ -1362,12 +1496,12 @@ struct BatchEntry {
     wt_ctx* c;
     unsigned long long uid, version;
     const void* H;
-    const void *E, *Zc, *rho, *R, *Ub, *W;
-    int nb, lb, rxy, rz, xd, tp;
+    const void *E, *Zc, *rho, *R, *Ub, *W, *T, *Rsl;
+    int nb, lb, rxy, rz, xd, tp, ys;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
-               rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && nb == o.nb && lb == o.lb && rxy == o.rxy &&
-               rz == o.rz && xd == o.xd && tp == o.tp;
+               rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && T == o.T && Rsl == o.Rsl && nb == o.nb &&
+               lb == o.lb && rxy == o.rxy && rz == o.rz && xd == o.xd && tp == o.tp && ys == o.ys;
     }
 };
 
@@ -1390,14 +1524,15 @@ namespace {
 struct TuneResult {
     int nb, lb, nch, nepi, rxy, rz, xd, tp, vec;   // tp: two-pass FFTs, bits: 1 z pass, 2 y, 4 x transforms
     double spectral_ms, expand_ms;
+    int ys;                                         // > 0: lateral tables, y slabs of ys rows
 };
-using TuneKey = std::tuple<int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t
+using TuneKey = std::tuple<int, int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t, columns
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneResult> g_tune;
 std::atomic<unsigned long long> g_plan_clock{0};
 
 TuneKey tune_key(const wt_ctx* c) {
-    return TuneKey{c->dev, c->grid.Nx, c->grid.Ny, c->grid.Nz, (int)c->times.size()};
+    return TuneKey{c->dev, c->grid.Nx, c->grid.Ny, c->grid.Nz, (int)c->times.size(), (int)c->cols.size()};
 }
 
 // Buffers of the FP32 path at the context's launch shapes.
@@ -1415,6 +1550,10 @@ void spectral_all(wt_ctx* c, cudaStream_t s) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size();
+    if (use_tables(c, 0)) {
+        spectral_tables(c, c->Zc32.p, c->rank, s);
+        return;
+    }
     for (int m0 = 0; m0 < c->rank; m0 += c->tune_nb) {
         const int b = std::min(c->tune_nb, c->rank - m0);
         c->sp32.fields(c->Zc32.p + (size_t)m0 * ncol * g.Nz, b, c->rho32.p, c->R32.p, c->E32.p + (size_t)m0 * npts,
@@ -1452,19 +1591,17 @@ float time_min(cudaStream_t s, int reps, F&& f) {
 // width {4, 2, 1}.  Results are cached per (device, grid, n_t) for the process.
 TuneResult autotune(wt_ctx* c, float* H) {
     c->e32_stamp = 0;                       // trial shapes overwrite the basis fields
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune.find(tune_key(c));
-        if (it != g_tune.end()) return it->second;
-    }
-    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec]]" fixes the shapes
-    // without timing (reproducible profiling runs); the values are checked like tuned ones
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows]]]" fixes
+    // the shapes without timing (reproducible profiling runs); the values are checked like tuned ones
     if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
         TuneResult t{};
-        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy,
-                                      &t.rz, &t.xd, &t.tp, &t.vec);
+        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy,
+                                      &t.rz, &t.xd, &t.tp, &t.vec, &t.ys);
         if (nread < 8) t.tp = 0;
         if (nread < 9) t.vec = 4;
+        if (nread < 10) t.ys = 0;
+        if (t.ys < 0 || t.ys > c->grid.Ny) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table rows must be 0..Ny");
+        if (t.ys > 0 && !tables_fit(c)) t.ys = 0;
         if (nread < 7 || (t.vec != 1 && t.vec != 2 && t.vec != 4) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
             (t.lb != 16 && t.lb != 32 && t.lb != 64) || (t.nch != 64 && t.nch != 128 && t.nch != 256) ||
             (t.nepi != 8 && t.nepi != 12 && t.nepi != 16) || t.tp < 0 || t.tp > 7)
@@ -1475,11 +1612,18 @@ TuneResult autotune(wt_ctx* c, float* H) {
         t.spectral_ms = t.expand_ms = 0.0;
         return t;
     }
+    // the process cache of timed results (the environment's fixed shapes above take precedence)
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(tune_key(c));
+        if (it != g_tune.end()) return it->second;
+    }
     cudaStream_t s = c->s;
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 4, 1e30, 1e30};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 4, 1e30, 1e30, 0};
+    c->tune_ys = 0;
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
@@ -1525,6 +1669,28 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_nb = best.nb;
     c->tune_lb = best.lb;
     alloc_fast32(c);
+    // the lateral tables (built once per context, at the FFT shapes chosen above): slabs of
+    // 1 .. 32 y rows x z-pass lines per block, against the per-basis passes' best time
+    if (tables_fit(c)) {
+        build_tables(c);
+        const int lb0 = best.lb;
+        for (int ys : {1, 2, 4, 8, 16, 32}) {
+            if (ys > g.Ny) break;
+            c->tune_ys = ys;
+            for (int lb : {16, 32, 64}) {
+                c->tune_lb = lb;
+                const float ms = time_min(s, 3, [&] { spectral_all(c, s); });
+                if (ms < best.spectral_ms) { best.spectral_ms = ms; best.ys = ys; best.lb = lb; }
+            }
+        }
+        c->tune_ys = best.ys;
+        c->tune_lb = best.ys ? best.lb : lb0;
+        if (!best.ys) {                      // not faster here: give the memory back
+            c->T32.release();
+            c->Rsl.release();
+            c->t32_ready = false;
+        }
+    }
     spectral_all(c, s);
     for (int vec : {4, 2, 1})
         for (int nepi : {8, 12, 16})
@@ -1544,8 +1710,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
     return best;
 }
 
-void tune_context(wt_ctx* c, float* H) {
-    const TuneResult t = autotune(c, H);
+void apply_tuning(wt_ctx* c, const TuneResult& t) {
     c->tune_nb = t.nb;
     c->tune_lb = t.lb;
     c->tune_nch = t.nch;
@@ -1553,14 +1718,19 @@ void tune_context(wt_ctx* c, float* H) {
     c->tune_vec = t.vec;
     c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);
     c->sp32.xdirect = t.xd;
-    c->tuned = true;
+    c->tune_ys = (t.ys > 0 && tables_fit(c)) ? t.ys : 0;
     alloc_fast32(c);
+    if (c->tune_ys) build_tables(c);         // the tables of this context (geometry only; kept)
+    c->tuned = true;
 }
 
+void tune_context(wt_ctx* c, float* H) { apply_tuning(c, autotune(c, H)); }
+
 BatchEntry entry_of(wt_ctx* c, const void* H) {
+    if (c->tune_ys) c->Rsl.alloc((size_t)32 * 3 * c->grid.Nz * c->grid.Nx * c->tune_ys);   // captured by address
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
-                      c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect,
-                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1) | ((int)c->sp32.xsm << 2)};
+                      c->T32.p, c->Rsl.p, c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect,
+                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1) | ((int)c->sp32.xsm << 2), c->tune_ys};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -1622,16 +1792,7 @@ void do_batch(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, cud
         ensure_spectral(c);
         const TuneKey k = tune_key(c);
         if (!shapes.count(k)) shapes[k] = autotune(c, static_cast<float*>(H[i]));
-        const TuneResult& t = shapes[k];
-        c->tune_nb = t.nb;
-        c->tune_lb = t.lb;
-        c->tune_nch = t.nch;
-        c->tune_nepi = t.nepi;
-        c->tune_vec = t.vec;
-        c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);
-        c->sp32.xdirect = t.xd;
-        c->tuned = true;
-        alloc_fast32(c);
+        apply_tuning(c, shapes[k]);
     }
     // one (time chunk, epilogue warps, store width) for the shared expansion launch: the one most
     // of the grid points asked for
@@ -1706,6 +1867,9 @@ wt_status wt_create(wt_ctx** out, const wt_grid* grid, int cuda_device) {
         c->uid = next_uid++;
         if (const char* e = std::getenv("WT_EXPAND")) c->use_tc = std::strcmp(e, "simt") != 0;
         c->grid = g;
+        c->info.Nx = g.Nx;
+        c->info.Ny = g.Ny;
+        c->info.Nz = g.Nz;
         try {
             WT_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
             WT_CUDA(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
@@ -1798,16 +1962,31 @@ wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tr, float
         if (tr->n_tracks < 0 || tr->n_steps < 1 || tr->n_out < 1 || !(tr->dt > 0.0))
             fail(WT_ERR_ARG, "bad track sizes or dt");
         if (tr->n_tracks == 0) return;
+        const wt_grid& g = ctx->grid;
+        // every buffer: device memory of the context's device, large enough for what the kernels touch
+        const size_t nts = (size_t)tr->n_tracks * tr->n_steps;
+        const size_t need[9] = {ctx->times.size() * 3 * (size_t)g.Nx * g.Ny * g.Nz * sizeof(float),
+                                (size_t)tr->n_tracks * tr->n_out * sizeof(float),
+                                nts * sizeof(float), nts * sizeof(float), nts * sizeof(float),
+                                nts * sizeof(float), nts * sizeof(float), nts * sizeof(float),
+                                (size_t)tr->n_tracks * sizeof(float)};
         const void* ptrs[9] = {H, i, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz, tr->q};
+        const char* names[9] = {"H", "i", "x", "y", "z", "vx", "vy", "vz", "q"};
         for (int k = 0; k < 9; ++k) {
             if (k == 8 && !tr->q) continue;
-            if (!ptrs[k] || !is_device_ptr(ptrs[k]))
-                fail(WT_ERR_ARG, "every buffer must be device memory (no staging without allocation)");
+            const std::string why = device_span_problem(ptrs[k], need[k], ctx->dev);
+            if (!why.empty())
+                fail(WT_ERR_ARG, std::string(names[k]) + ": " + why +
+                                     " (every buffer must be device memory of the context's device)");
         }
-        const wt_grid& g = ctx->grid;
-        eq1_noalloc_launch(static_cast<cudaStream_t>(stream), ctx->dev, H, g.Nx, g.Ny, g.Nz, ctx->d_times.p,
+        const cudaStream_t us = static_cast<cudaStream_t>(stream);
+        eq1_noalloc_launch(us, ctx->dev, H, g.Nx, g.Ny, g.Nz, ctx->d_times.p,
                            (int)ctx->times.size(), g.Lx, g.Ly, g.Lz, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz,
                            tr->q, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out, tr->dt, ctx->opts.v_w, i);
+        // the call reads the relaxation's time samples on the caller's stream: a later wt_relax
+        // waits for this event before it rewrites them (the event was created by wt_relax)
+        WT_CUDA(cudaEventRecord(ctx->ev_noalloc, us));
+        ctx->noalloc_pending = true;
     });
 }
 
@@ -1851,6 +2030,7 @@ wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out) {
         out->x_direct = ctx->sp_ready ? (int)ctx->sp32.xdirect : 0;
         out->two_pass = ctx->sp_ready ? (int)ctx->sp32.zsm | ((int)ctx->sp32.ysm << 1) | ((int)ctx->sp32.xsm << 2) : 0;
         out->store_vec = ctx->tune_vec;
+        out->table_rows = ctx->tune_ys;
     });
 }
 
@@ -2098,6 +2278,10 @@ void wt_destroy(wt_ctx* ctx) {
     if (s2) cudaStreamSynchronize(s2);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->ev_noalloc) {
+        cudaEventSynchronize(ctx->ev_noalloc);
+        cudaEventDestroy(ctx->ev_noalloc);
+    }
     delete ctx;
     if (s) cudaStreamDestroy(s);
     if (s2) cudaStreamDestroy(s2);

@@ -133,6 +133,16 @@ void trsm_lower_t(cudaStream_t s, const double* L, int n, int ldl, double* B, in
 // rounding-level directions would otherwise keep rotating).
 int jacobi_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err, int max_sweeps = 40,
                double abs_tol = 0.0);
+// Singular value decomposition of the rows of A [m][n] (row-major, destroyed)
+// by one-sided (Hestenes) Jacobi: on return the rows of A are mutually
+// orthogonal (row i = sigma_i u_i^T), V [m][m] holds the accumulated rotations
+// (A_in = V^T A_out) and sigma[m] the row norms (unsorted).  Returns the number
+// of sweeps; sets d_err (DERR_TIMEOUT) when max_sweeps do not converge.
+int onesided_jacobi_rows(cudaStream_t s, double* A, int m, int n, int lda, double* V, double* sigma, int* d_err,
+                         int max_sweeps = 30);
+// out[r][n] = scale[r] * A[idx[r]][:]  (idx, scale: device arrays of `rows`)
+void gather_rows_scaled(cudaStream_t s, const double* A, int n, int lda, const int* idx, const double* scale,
+                        int rows, double* out);
 // y = alpha * A x + beta * y  (A row-major M x N, or its transpose)
 void dgemv(cudaStream_t s, bool ta, int M, int N, double alpha, const double* A, int lda,
            const double* x, double beta, double* y);

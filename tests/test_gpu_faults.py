@@ -115,3 +115,30 @@ def test_stalled_expansion_times_out_and_recovers(P, torch):
         assert torch.equal(again, ref)
     finally:
         s.close()
+
+
+def test_truncated_time_basis_is_refused_by_the_fp32_paths(P, torch):
+    """WT_FAULT=rank_cap caps the time basis at rank 4, far short of what the charge history
+    needs: wt_relax still succeeds and reports the truncation, the FP32 field paths return
+    WT_ERR_ACCURACY, and the FP64 path is unaffected."""
+    from paper_2605_13987_gb300 import _binding as B
+    w = W.tiny_cell(nx=16, nz=32, n_t=24, radius=8 * UM)
+    s = P.Sensor(w.grid, w.columns)
+    try:
+        s.fit()
+        with fault("rank_cap"):
+            s.relax(w.times)
+        info = s.info()
+        assert info["rank"] == 4 and info["trunc_rel"] > 1e-6
+        with pytest.raises(P.WTError) as e:
+            s.extend("fp32")
+        assert e.value.code == B.WT_ERR_ACCURACY
+        H64 = s.extend("fp64")
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(H64).all())
+        s.relax(w.times)                      # without the cap: a full basis, FP32 works again
+        assert s.info()["trunc_rel"] <= 1e-7
+        s.extend("fp32")
+        torch.cuda.synchronize()
+    finally:
+        s.close()

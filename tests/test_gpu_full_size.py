@@ -24,8 +24,11 @@ def torch():
 
 
 def _sample(rng, w, n_t=4, n_side=8):
+    """The first and last time samples (1 ps, 10 ns) and n_t - 2 random ones; a random subgrid."""
     g = w.grid
-    ti = np.sort(rng.choice(len(w.times), n_t, replace=False))
+    nt = len(w.times)
+    mid = rng.choice(np.arange(1, nt - 1), n_t - 2, replace=False)
+    ti = np.sort(np.concatenate([[0, nt - 1], mid]))
     ix = np.sort(rng.choice(g.Nx, n_side, replace=False))
     iy = np.sort(rng.choice(g.Ny, n_side, replace=False))
     iz = np.sort(rng.choice(g.Nz, n_side, replace=False))
@@ -60,14 +63,32 @@ def test_c2_full_size(torch):
     sol = O.solve(w)
     ref = sol.H_subgrid(t_idx=samp[0], ix=samp[1], iy=samp[2], iz=samp[3])
     e64, e32 = rel_l2(got64, ref), rel_l2(got32, ref)
-    print("c2 full size: FP64", e64, "FP32", e32)
+    p32 = [rel_l2(got32[n], ref[n]) for n in range(len(ref))]
+    p64 = [rel_l2(got64[n], ref[n]) for n in range(len(ref))]
+    print("c2 full size: FP64", e64, "FP32", e32, "per time sample FP32", p32)
     assert e64 < TOL64 and e32 < TOL32
+    assert max(p32) < TOL32 and max(p64) < 100 * TOL64
+
+
+def _c3_pick():
+    """One sensor of the 64-geometry batch per grid size (64, 80, 96, 112, 128), plus the two
+    with the widest resistivity spreads (0.05 against 1.9 Ohm cm)."""
+    ws = W.c3_batch(seed=3)
+    pick = {}
+    for i, w in enumerate(ws):
+        pick.setdefault(w.grid.Nx, i)
+    spread = sorted(range(len(ws)), key=lambda i: -max(c.resistivity for c in ws[i].columns)
+                    / min(c.resistivity for c in ws[i].columns))[:2]
+    idx = sorted(set(pick.values()) | set(spread))
+    return [ws[i] for i in idx], idx
 
 
 def test_c3_sensors_through_the_batch(torch):
+    """Each picked sensor against the oracle, per time sample, from one batched launch."""
     import paper_2605_13987_gb300 as P
-    ws = W.c3_batch(seed=3)[:4]
-    sens = []
+    ws, idx = _c3_pick()
+    assert sorted({w.grid.Nx for w in ws}) == [64, 80, 96, 112, 128]
+    sens, got, samps = [], [], []
     try:
         for w in ws:
             s = P.Sensor(w.grid, w.columns)
@@ -76,14 +97,18 @@ def test_c3_sensors_through_the_batch(torch):
             sens.append(s)
         Hb = P.extend_batch(sens)
         torch.cuda.synchronize()
-        k = int(np.argmax([w.grid.Nx for w in ws]))
         rng = np.random.default_rng(22)
-        samp = _sample(rng, ws[k])
-        got = _take(Hb[k], *samp, torch)
+        for k, w in enumerate(ws):
+            samp = _sample(rng, w)
+            samps.append(samp)
+            got.append(_take(Hb[k], *samp, torch))
+        ranks = [s.info()["rank"] for s in sens]
     finally:
         for s in sens:
             s.close()
-    ref = O.solve(ws[k]).H_subgrid(t_idx=samp[0], ix=samp[1], iy=samp[2], iz=samp[3])
-    err = rel_l2(got, ref)
-    print("c3 sensor", k, ws[k].grid.Nx, "FP32", err)
-    assert err < TOL32
+    for k, w in enumerate(ws):
+        samp = samps[k]
+        ref = O.solve(w).H_subgrid(t_idx=samp[0], ix=samp[1], iy=samp[2], iz=samp[3])
+        per = [rel_l2(got[k][n], ref[n]) for n in range(len(ref))]
+        print("c3 sensor", idx[k], w.grid.Nx, "rank", ranks[k], "FP32", rel_l2(got[k], ref), "per sample", per)
+        assert rel_l2(got[k], ref) < TOL32 and max(per) < TOL32
