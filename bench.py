@@ -42,8 +42,8 @@ WORKLOADS = {
     "c1": "c1: single cell 55x55x100 um, grid 32x32x64, 2 columns x 64 sources, 64 time samples",
     "small": "small: single cell 55x55x100 um, grid 64x64x64, 2 columns x 64 sources, 512 time samples "
              "(profiling case: H = 1.6 GB > L2)",
-    "prof": "prof: c2's geometry and grid (128x128x256, 18 columns) with 16 time samples "
-            "(profiling case: the spectral kernels at c2 sizes, about 2.5 GB on the device)",
+    "prof": "prof: c2's geometry and grid (128x128x256, 18 columns) with 64 time samples "
+            "(profiling case: the spectral kernels at c2 sizes and rank, about 7 GB on the device)",
     "c4": "c4: 3x3 pixel cell at grid 96x96x192, radius 5 um, 256 time samples, 1e4 straight tracks of 100 "
           "steps; the Eq. 1 loss and its gradient (resistivities, radius, pitch)",
     "scan": "scan: Sec. 5's bias-diameter scan (6-14 um in 2 um steps) on the 3x3 pixel cell 165x165x500 um, "
@@ -64,7 +64,7 @@ def make_workload(name):
     if name == "prof":
         from dataclasses import replace
         w = W.workload("c2")
-        return replace(w, times=W.log_times(16))
+        return replace(w, times=W.log_times(64))
     return W.workload(name)
 
 

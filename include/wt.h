@@ -169,7 +169,7 @@ wt_status wt_relax(wt_ctx* ctx, const double* t, int n_t);
  * The first FP32 extension of a context (unless wt_batch_run came first)
  * runs the autotuner of wt_batch_run on it, writing trial results into H,
  * and returns only after that tuning; later calls reuse the choice.  The
- * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows]]]"
+ * environment variable WT_LAUNCH_SHAPES="nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows[,table_flags]]]]"
  * (the values of wt_get_tuning) fixes the shapes without tuning.
  * WT_FP32 returns WT_ERR_ACCURACY when the time basis is truncated beyond
  * its limit (see wt_relax). */
@@ -301,7 +301,7 @@ wt_status wt_eq1_loss_grad_profile(wt_ctx* ctx, const wt_tracks* tracks, const d
 wt_status wt_batch_run(wt_ctx* const* ctxs, int n, wt_precision prec, void* const* H, void* cuda_stream);
 
 /* Launch shapes the FP32 path of this context uses, set by the autotuner
- * (before the first extension: the defaults 1, 32, 256, 8, 0, 0, 0, 0, 4, 0). */
+ * (before the first extension: the defaults 1, 32, 256, 8, 0, 0, 0, 0, 4, 0, 0). */
 typedef struct {
     int nb;         /* charge vectors per spectral launch: 1, 2, 4 */
     int lb;         /* (x, y) lines per z-pass block: 16, 32, 64 */
@@ -309,8 +309,8 @@ typedef struct {
     int nepi;       /* expansion epilogue warps: 8, 12, 16 */
     int r_xy, r_z;  /* elements per lane of the lateral and z register FFTs */
     int x_direct;   /* 1: the x transforms store from registers (else staged) */
-    int two_pass;   /* two-pass shared-memory FFTs in use, a bit mask: 1 the z pass (Nz of 64, 128
-                       or 256; r_z then unused), 2 the y transforms (Ny of 64 or 128; r_xy then
+    int two_pass;   /* two-pass shared-memory FFTs in use, a bit mask: 1 the z pass (Nz of 64, 96,
+                       128, 160, 192, 224, 256 or 384; r_z then unused), 2 the y transforms (Ny of 64 or 128; r_xy then
                        sets the x transforms only), 4 the x transforms too (with 2, Nx = Ny;
                        r_xy and x_direct then unused) */
     int store_vec;  /* floats per expansion store: 4 (4 x 4 lane-quad transposes), 2 (2 x 2
@@ -320,6 +320,10 @@ typedef struct {
                        translated fundamental-solution chunks in spectral form, built once per
                        context, 12 B x n_columns x Nx x Ny x Nz), combined per basis vector in y
                        slabs of table_rows rows and followed by the z pass */
+    int table_flags; /* table path, a bit mask: 1 the combination of one slab overlaps the z pass
+                       of the previous one on a second stream (two slab buffers); 2 the z pass
+                       invalidates the L2 lines of the slab rows it has read, so that the slab
+                       (scratch) is not written back to DRAM */
 } wt_tuning;
 wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out);
 

@@ -41,8 +41,8 @@ def fit(P, S, tikhonov=0.0, want_cond=False):
         reg[:, :ns - 1] = np.sqrt(tikhonov * scale) * np.eye(ns - 1)
         A = np.vstack([A, reg])
         rhs = np.vstack([S, np.zeros((ns - 1, S.shape[1]))])
-    # X = A^+ rhs via QR: rhs^T Q, R  (Q is never formed)
-    QtR, R = sla.qr_multiply(A, rhs.T, mode="right")
+    # X = A^+ rhs via QR: rhs^T Q, R  (Q is never formed; A is a temporary and is factorised in place)
+    QtR, R = sla.qr_multiply(A, rhs.T, mode="right", overwrite_a=True)
     X = sla.solve_triangular(R, QtR.T, lower=False)
     F = B @ X[:ns - 1]
     out = {"F": F, "offset": X[ns - 1], "Cn": 0.5 * (F + F.T), "B": B}

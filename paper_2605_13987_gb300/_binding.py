@@ -55,7 +55,7 @@ class wt_shaper(C.Structure):
 
 class wt_tuning(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("nb", "lb", "nch", "nepi", "r_xy", "r_z", "x_direct", "two_pass",
-                                       "store_vec", "table_rows")]
+                                       "store_vec", "table_rows", "table_flags")]
 
 
 class wt_feature_opts(C.Structure):

@@ -73,8 +73,10 @@ struct Fast32 {
     // deposit and plane passes only: R [nb][3][Nz][Ny][Nx] (plane layout [y][x])
     void lateral(const float* Zc, int nb, float* rho, float* R, cudaStream_t s, int mode = 0) const;
     // z pass of rows y0 .. y0 + ys - 1: R [nb][3][Nz][ys][Nx] -> out[b * out_sb + c * out_sc + (x Ny + y) Nz + z]
+    // discard: with the two-pass z pass, invalidate the consumed rows of R in L2 (R is scratch;
+    // needs Nx ys a multiple of 32, R 128-byte aligned and lb >= 32, else ignored)
     void zlines(const float* R, int nb, int y0, int ys, float* out, size_t out_sb, size_t out_sc, cudaStream_t s,
-                int lb) const;
+                int lb, bool discard = false) const;
 };
 
 // R[b][a][kz][j] = sum_c Zc[b][c][kz] T[c][a][kz][off + j] for j < nl, b < r <= 32: the planes of the

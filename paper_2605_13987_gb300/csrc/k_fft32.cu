@@ -203,14 +203,15 @@ void Fast32::lateral(const float* Zc, int nb, float* rho, float* R, cudaStream_t
 }
 
 void Fast32::zlines(const float* R, int nb, int y0, int ys, float* out, size_t out_sb, size_t out_sc, cudaStream_t s,
-                    int lb) const {
+                    int lb, bool discard) const {
     if (lb != 16 && lb != 32 && lb != 64) fail(WT_ERR_ARG, "z-pass lines per block must be 16, 32 or 64");
     if (y0 < 0 || ys < 1 || y0 + ys > g.Ny) fail(WT_ERR_ARG, "z-pass rows out of range");
     const size_t nl = (size_t)g.Nx * ys;
     dim3 gz((unsigned)((nl + lb - 1) / lb), 3, nb);
     const C2<float>* tz = reinterpret_cast<const C2<float>*>(tw_z.p);
     const C2<float>* zz = reinterpret_cast<const C2<float>*>(zsh.p);
-    const ZLines zl{ys, y0};
+    const bool disc = discard && zsm && lb >= 32 && nl % 32 == 0 && reinterpret_cast<uintptr_t>(R) % 128 == 0;
+    const ZLines zl{ys, y0, disc ? 1 : 0};
     if (zsm) zpass2_launch(lb, gz, s, g, R, tz, zz, out, out_sb, out_sc, zl);
     else zpass_launch(rz, lb, gz, s, g, R, tz, zz, out, out_sb, out_sc, zl);
 }

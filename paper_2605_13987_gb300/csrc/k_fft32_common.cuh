@@ -39,6 +39,7 @@ inline size_t zpass_smem(const GridDev& g, int lb, int R) {
 // laid out [y - y0][x]; the outputs go to H's point order (x Ny + y) Nz + z of the full grid.
 struct ZLines {
     int ys, y0;
+    int discard;    // two-pass z pass: drop the staged rows' L2 lines once read (no write-back)
 };
 
 // Launchers (k_fft32_plane.cu, k_fft32_z.cu): dispatch on the register-FFT length.
@@ -50,7 +51,7 @@ void plane_launch(int r, bool xdirect, int ny2, dim3 grid, cudaStream_t s, const
 void zpass_allow(int r, size_t smem);
 void zpass_launch(int r, int lb, dim3 grid, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* twz,
                   const C2<float>* zsh, float* out, size_t out_sb, size_t out_sc, ZLines zl);
-// Two-pass shared-memory z FFT (k_fft32_z2.cu), Nz in {64, 128, 256}.
+// Two-pass shared-memory z FFT (k_fft32_z2.cu), Nz in {64, 96, 128, 160, 192, 224, 256, 384}.
 bool zpass2_supported(int nz);
 size_t zpass2_smem(int A, int B, int lb);
 void zpass2_allow(int nz);

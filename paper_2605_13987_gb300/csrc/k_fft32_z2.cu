@@ -1,12 +1,14 @@
 // FP32 z pass of the bulk extension, two-pass shared-memory form for
-// power-of-two Nz = A B (A <= B, A, B in {8, 16}): the same cosine and sine
-// series as the register-FFT z pass (k_fft32_z.cu, Makhoul's reordering of
-// the DCT-III with two real lines per complex FFT), with the N-point FFT
-// split as
+// Nz = A B with A in {8, 16} lanes per line pair and B built from the factors
+// 2, 3, 5, 7 (Nz = 64, 96, 128, 160, 192, 224, 256, 384): the same cosine
+// and sine series as the register-FFT z pass (k_fft32_z.cu, Makhoul's
+// reordering of the DCT-III with two real lines per complex FFT), with the
+// N-point FFT split as
 //   X[c + B d] = sum_a w_A^{a d} w_N^{a c} sum_b Y[a + A b] w_B^{b c}:
 // pass 1, lane a of a line's A lanes: one B-point DFT in registers, the
-// twiddles w_N^{a c}, the results to shared memory; pass 2: B / A A-point
-// DFTs per lane.  Register DFTs with compile-time twiddles; no shuffles.
+// twiddles w_N^{a c}, the results to shared memory; pass 2: the B columns'
+// A-point DFTs shared out over the A lanes (ceil(B / A) per lane).  Register
+// DFTs with compile-time twiddles; no shuffles.
 #include "k_fft32_common.cuh"
 
 namespace wt {
@@ -23,12 +25,16 @@ size_t zpass2_smem(int A, int B, int lb) {
     return ((size_t)(lb / 2) * zpass2_pitch(A, B) + 2 * (size_t)A * B) * sizeof(C2<float>);
 }
 
+// blocks per SM the kernel is compiled for: the larger register DFTs take more registers
+__host__ __device__ constexpr int zpass2_min_blocks(int A, int B) { return (B > 16 || (A == 16 && B > 16)) ? 2 : 3; }
+
 template <int A, int B, int LB>
-__global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const float* __restrict__ R,
+__global__ void __launch_bounds__(256, zpass2_min_blocks(A, B)) f32_zpass2_kernel(GridDev g, const float* __restrict__ R,
                                                             const C2<float>* __restrict__ twz,
                                                             const C2<float>* __restrict__ zsh, float* __restrict__ out,
                                                             size_t out_sb, size_t out_sc, ZLines zl) {
     constexpr int N = A * B, S = zpass2_pitch(A, B), G = 32 / A, NP = LB / 2;
+    constexpr int RC = (B + A - 1) / A;          // pass-2 columns per lane
     extern __shared__ unsigned char smem_raw[];
     const int nx = g.Nx, ny = g.Ny;
     const size_t nxy = (size_t)nx * zl.ys;      // staged lines: rows y0 .. y0 + ys - 1 of each plane
@@ -52,6 +58,20 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
         for (int m = m0; m < N; m += MS) dst[2 * m] = lin ? sp[(size_t)m * nxy] : 0.f;
     }
     __syncthreads();
+    if constexpr (LB >= 32) {
+        // the staged rows are scratch that only this block reads: invalidate their L2 lines so that
+        // the slab never goes back to DRAM (whole 128-byte lines inside the slab row only; the
+        // host enables this when every row starts on a 128-byte boundary)
+        if (zl.discard) {
+            constexpr int SEG = LB / 32;
+            const float* base = R + ((size_t)b * 3 + comp) * N * nxy + L0;
+            for (int e = threadIdx.x; e < N * SEG; e += blockDim.x) {
+                const int m = e / SEG, q = e - m * SEG;
+                if (L0 + (size_t)(q + 1) * 32 <= nxy)
+                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + (size_t)m * nxy + q * 32) : "memory");
+            }
+        }
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / A, gl = lane % A;
     const bool sine = comp == 2;
@@ -71,20 +91,21 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
             v[j] = cmul(C2<float>{p.x + q.y, p.y - q.x}, zs[m]);
         }
         __syncwarp();                             // every lane has read its inputs before the matrix overwrites them
-        reg_dft_c<B>(v);
+        reg_dft_k<B>(v);
 #pragma unroll
         for (int c = 1; c < B; ++c) v[c] = cmul(v[c], tl[c * A + gl]);
         if (act)
 #pragma unroll
             for (int c = 0; c < B; ++c) cf[gl * (B + 1) + c] = v[c];
         __syncwarp();
-        // pass 2: column c = gl + A r, A-point DFT over a -> X[c + B d]
-        C2<float> o[B];
+        // pass 2: column c = gl + A r (< B), A-point DFT over a -> X[c + B d]
+        C2<float> o[RC * A];
 #pragma unroll
-        for (int r = 0; r < B / A; ++r) {
+        for (int r = 0; r < RC; ++r) {
+            const bool col = act && gl + A * r < B;
             C2<float> u[A];
 #pragma unroll
-            for (int a = 0; a < A; ++a) u[a] = act ? cf[a * (B + 1) + gl + A * r] : C2<float>{0.f, 0.f};
+            for (int a = 0; a < A; ++a) u[a] = col ? cf[a * (B + 1) + gl + A * r] : C2<float>{0.f, 0.f};
             reg_dft_c<A>(u);
 #pragma unroll
             for (int d = 0; d < A; ++d) o[r * A + d] = u[d];
@@ -94,7 +115,8 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
         // odd z at N/2 + 8 + (z - 1)/2; the sine series takes (-1)^z / 2
         if (act)
 #pragma unroll
-            for (int r = 0; r < B / A; ++r)
+            for (int r = 0; r < RC; ++r) {
+                if (gl + A * r >= B) break;
 #pragma unroll
                 for (int d = 0; d < A; ++d) {
                     const int j = gl + A * r + B * d;
@@ -105,6 +127,7 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
                     }
                     cf[(2 * d < A) ? j : N / 2 + 8 + (N - 1 - j)] = y;
                 }
+            }
         __syncwarp();
         if (!act) continue;
         const size_t La = L0 + 2 * f, Lb = La + 1;
@@ -122,19 +145,33 @@ __global__ void __launch_bounds__(256, 3) f32_zpass2_kernel(GridDev g, const flo
     }
 }
 
-// Two-pass forms compiled in: (A, B) = (8, 8), (8, 16), (16, 16), i.e. Nz = 64, 128, 256.
-#define WT_FOR_EACH_Z2(X) X(8, 8) X(8, 16) X(16, 16)
+// Two-pass forms compiled in: (A, B) for Nz = 64, 96, 128, 160, 192, 224, 256, 384.
+#define WT_FOR_EACH_Z2(X) X(8, 8) X(8, 12) X(8, 16) X(8, 20) X(8, 24) X(16, 14) X(16, 16) X(16, 24)
 
-bool zpass2_supported(int nz) { return nz == 64 || nz == 128 || nz == 256; }
-static void z2_shape(int nz, int* A, int* B) {
-    *A = nz == 64 ? 8 : nz == 128 ? 8 : 16;
+static bool z2_shape(int nz, int* A, int* B) {
+    switch (nz) {
+        case 64: *A = 8; break;
+        case 96: *A = 8; break;
+        case 128: *A = 8; break;
+        case 160: *A = 8; break;
+        case 192: *A = 8; break;
+        case 224: *A = 16; break;
+        case 256: *A = 16; break;
+        case 384: *A = 16; break;
+        default: return false;
+    }
     *B = nz / *A;
+    return true;
+}
+bool zpass2_supported(int nz) {
+    int A, B;
+    return z2_shape(nz, &A, &B);
 }
 
 void zpass2_allow(int nz) {
-    if (!zpass2_supported(nz)) fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 128, 256}");
     int A, B;
-    z2_shape(nz, &A, &B);
+    if (!z2_shape(nz, &A, &B))
+        fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 96, 128, 160, 192, 224, 256, 384}");
     const size_t sz = zpass2_smem(A, B, 64);
 #define WT_CASE(AA, BB) \
     if (A == AA && B == BB) { \
@@ -148,9 +185,9 @@ void zpass2_allow(int nz) {
 
 void zpass2_launch(int lb, dim3 gz, cudaStream_t s, const GridDev& g, const float* R, const C2<float>* tz,
                    const C2<float>* zz, float* out, size_t out_sb, size_t out_sc, ZLines zl) {
-    if (!zpass2_supported(g.Nz)) fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 128, 256}");
     int A, B;
-    z2_shape(g.Nz, &A, &B);
+    if (!z2_shape(g.Nz, &A, &B))
+        fail(WT_ERR_UNSUPPORTED, "two-pass z FFT needs Nz in {64, 96, 128, 160, 192, 224, 256, 384}");
     const size_t sz = zpass2_smem(A, B, lb);
 #define WT_CASE(AA, BB) \
     if (A == AA && B == BB) { \

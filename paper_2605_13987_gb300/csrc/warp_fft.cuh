@@ -265,6 +265,95 @@ __device__ __forceinline__ void reg_dft_c(C2<float> (&v)[R]) {
     }
 }
 
+// cos and sin of 2 pi q / R for the compile-time twiddles of the mixed-radix register DFTs:
+// the angle reduced to [-pi, pi], then the Taylor series of cos and sin summed in double to far
+// below float precision (terms up to x^40 / 40!), and rounded once to float.
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 20; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k <= 20; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double turn_angle(int q, int R) {
+    q = ((q % R) + R) % R;
+    if (2 * q > R) q -= R;                      // q / R in (-1/2, 1/2]
+    return 2.0 * 3.14159265358979323846 * (double)q / (double)R;
+}
+
+// x w_R^M with w_R = exp(+2 pi i / R) for any R; quarter and half turns exact.
+template <int R, int M>
+__device__ __forceinline__ C2<float> twr(C2<float> x) {
+    constexpr int q = ((M % R) + R) % R;
+    if constexpr (q == 0) return x;
+    else if constexpr (4 * q == R) return {-x.y, x.x};
+    else if constexpr (2 * q == R) return {-x.x, -x.y};
+    else if constexpr (4 * q == 3 * R) return {x.y, -x.x};
+    else {
+        constexpr float c = (float)taylor_cos(turn_angle(q, R)), s = (float)taylor_sin(turn_angle(q, R));
+        return {x.x * c - x.y * s, x.x * s + x.y * c};
+    }
+}
+
+__host__ __device__ constexpr int smallest_factor(int R) {
+    return R % 4 == 0 && R > 4 ? 4 : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : R % 5 == 0 ? 5 : R % 7 == 0 ? 7 : R;
+}
+
+// R-point DFT in registers (exp(+i), natural order in and out) for R built from the factors
+// 2, 3, 4, 5, 7 (powers of two by reg_dft_c): R = P Q with P the first factor; Q-point DFTs over
+// x[j1 + P j2], twiddles w_R^{j1 k2}, P-point DFTs into X[k2 + Q k1]; a prime R directly.
+template <int R>
+__device__ __forceinline__ void reg_dft_k(C2<float> (&v)[R]) {
+    if constexpr (R == 1 || R == 2 || R == 4 || R == 8 || R == 16) {
+        reg_dft_c<R>(v);
+    } else if constexpr (smallest_factor(R) == R) {
+        C2<float> out[R];
+        static_for<0, R>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            C2<float> acc = v[0];
+            static_for<1, R>([&](auto J) {
+                constexpr int j = decltype(J)::value;
+                acc = cadd(acc, twr<R, j * k>(v[j]));
+            });
+            out[k] = acc;
+        });
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = out[k];
+    } else {
+        constexpr int P = smallest_factor(R), Q = R / P;
+        C2<float> y[P][Q];
+        static_for<0, P>([&](auto J1) {
+            constexpr int j1 = decltype(J1)::value;
+            C2<float> t[Q];
+#pragma unroll
+            for (int j2 = 0; j2 < Q; ++j2) t[j2] = v[j1 + P * j2];
+            reg_dft_k<Q>(t);
+            static_for<0, Q>([&](auto K2) {
+                constexpr int k2 = decltype(K2)::value;
+                y[j1][k2] = twr<R, j1 * k2>(t[k2]);
+            });
+        });
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            C2<float> t[P];
+#pragma unroll
+            for (int j1 = 0; j1 < P; ++j1) t[j1] = y[j1][k2];
+            reg_dft_k<P>(t);
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) v[k2 + Q * k1] = t[k1];
+        }
+    }
+}
+
 __device__ __forceinline__ int warp_fft_k2(int gl, int W) {
     const int lw = 31 - __clz(W);
     return lw ? (int)(__brev((unsigned)gl) >> (32 - lw)) : 0;

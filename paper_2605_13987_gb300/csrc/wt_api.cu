@@ -159,6 +159,9 @@ struct wt_ctx {
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
     int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_vec = 4;
     int tune_ys = 0;                 // > 0: basis fields from the lateral tables, y slabs of tune_ys rows
+    int tune_tf = 0;                 // table path flags: 1 slabs pipelined on two streams, 2 L2 discard
+    cudaStream_t s_aux = nullptr;    // second stream of the pipelined table path
+    cudaEvent_t ev_tc[2] = {nullptr, nullptr}, ev_tz[2] = {nullptr, nullptr}, ev_fork = nullptr;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
     // identity and state counter, for the captured graphs of wt_batch_run
     unsigned long long uid = 0, version = 0;
@@ -726,9 +729,16 @@ void do_relax(wt_ctx* c, const double* t, int nt) {
     c->mu.alloc(n1);
     DBuf<double> U;
     U.alloc((size_t)n1 * n1);
-    int sweeps = jacobi_eig(s, Y.p, n1, c->mu.p, U.p, c->d_err.p);
-    (void)sweeps;
-    if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver did not converge");
+    // modes: tridiagonalisation + divide and conquer; WT_EIGEN=jacobi selects the two-sided
+    // Jacobi solver instead (a cross-check)
+    const char* eig_env = std::getenv("WT_EIGEN");
+    if (eig_env && std::string(eig_env) == "jacobi") {
+        jacobi_eig(s, Y.p, n1, c->mu.p, U.p, c->d_err.p);
+        if (read_err(c)) fail(WT_ERR_TIMEOUT, "Jacobi eigensolver did not converge");
+    } else {
+        sym_eig(s, Y.p, n1, c->mu.p, U.p, c->d_err.p);
+        if (read_err(c)) fail(WT_ERR_TIMEOUT, "tridiagonal QL iteration did not converge");
+    }
     trsm_lower_t(s, Am.p, n1, n1, U.p, n1, n1);              // V = L^-T U
     Y.release(); Yt.release(); Sm.release();
     std::vector<double> hmu(n1);
@@ -843,16 +853,53 @@ void build_tables(wt_ctx* c) {
 
 // Basis fields of Zc [r][n_cols][Nz] from the lateral tables: per slab of ys y rows, the
 // combination of the tables' planes (into the L2-sized slab buffer) and the z pass.
+// Slab buffers of the table path: one, or two for the pipelined form.
+size_t slab_elems(const wt_ctx* c) { return (size_t)32 * 3 * c->grid.Nz * c->grid.Nx * c->tune_ys; }
+void alloc_slabs(wt_ctx* c) { c->Rsl.alloc(slab_elems(c) * ((c->tune_tf & 1) ? 2 : 1)); }
+
+// The second stream and the events of the pipelined table path (created once per context).
+void ensure_aux(wt_ctx* c) {
+    if (c->s_aux) return;
+    WT_CUDA(cudaStreamCreateWithFlags(&c->s_aux, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        WT_CUDA(cudaEventCreateWithFlags(&c->ev_tc[k], cudaEventDisableTiming));
+        WT_CUDA(cudaEventCreateWithFlags(&c->ev_tz[k], cudaEventDisableTiming));
+    }
+    WT_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+}
+
 void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz, nxy = (size_t)g.Nx * g.Ny;
     const int ncol = (int)c->cols.size(), ys = c->tune_ys;
-    c->Rsl.alloc((size_t)32 * 3 * g.Nz * g.Nx * ys);
-    for (int y0 = 0; y0 < g.Ny; y0 += ys) {
-        const int yn = std::min(ys, g.Ny - y0);
-        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p);
-        c->sp32.zlines(c->Rsl.p, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, s, c->tune_lb);
+    const bool pipe = c->tune_tf & 1, disc = c->tune_tf & 2;
+    alloc_slabs(c);
+    if (!pipe) {
+        for (int y0 = 0; y0 < g.Ny; y0 += ys) {
+            const int yn = std::min(ys, g.Ny - y0);
+            column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p);
+            c->sp32.zlines(c->Rsl.p, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, s, c->tune_lb, disc);
+        }
+        return;
     }
+    // combination of slab k + 1 (stream s) overlaps the z pass of slab k (second stream); two slab
+    // buffers, each reused once the z pass two slabs back has read it
+    ensure_aux(c);
+    const size_t se = slab_elems(c);
+    WT_CUDA(cudaEventRecord(c->ev_fork, s));
+    WT_CUDA(cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0));
+    int k = 0;
+    for (int y0 = 0; y0 < g.Ny; y0 += ys, ++k) {
+        const int yn = std::min(ys, g.Ny - y0), bi = k & 1;
+        float* R = c->Rsl.p + bi * se;
+        if (k >= 2) WT_CUDA(cudaStreamWaitEvent(s, c->ev_tz[bi], 0));
+        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, R);
+        WT_CUDA(cudaEventRecord(c->ev_tc[bi], s));
+        WT_CUDA(cudaStreamWaitEvent(c->s_aux, c->ev_tc[bi], 0));
+        c->sp32.zlines(R, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, c->s_aux, c->tune_lb, disc);
+        WT_CUDA(cudaEventRecord(c->ev_tz[bi], c->s_aux));
+    }
+    for (int q = 0; q < std::min(k, 2); ++q) WT_CUDA(cudaStreamWaitEvent(s, c->ev_tz[q], 0));
 }
 bool use_tables(const wt_ctx* c, int mode) { return mode == 0 && c->tune_ys > 0 && c->t32_ready; }
 
@@ -1497,11 +1544,11 @@ struct BatchEntry {
     unsigned long long uid, version;
     const void* H;
     const void *E, *Zc, *rho, *R, *Ub, *W, *T, *Rsl;
-    int nb, lb, rxy, rz, xd, tp, ys;
+    int nb, lb, rxy, rz, xd, tp, ys, tf;
     bool operator==(const BatchEntry& o) const {
         return c == o.c && uid == o.uid && version == o.version && H == o.H && E == o.E && Zc == o.Zc &&
                rho == o.rho && R == o.R && Ub == o.Ub && W == o.W && T == o.T && Rsl == o.Rsl && nb == o.nb &&
-               lb == o.lb && rxy == o.rxy && rz == o.rz && xd == o.xd && tp == o.tp && ys == o.ys;
+               lb == o.lb && rxy == o.rxy && rz == o.rz && xd == o.xd && tp == o.tp && ys == o.ys && tf == o.tf;
     }
 };
 
@@ -1525,6 +1572,7 @@ struct TuneResult {
     int nb, lb, nch, nepi, rxy, rz, xd, tp, vec;   // tp: two-pass FFTs, bits: 1 z pass, 2 y, 4 x transforms
     double spectral_ms, expand_ms;
     int ys;                                         // > 0: lateral tables, y slabs of ys rows
+    int tf;                                         // table path flags (pipelined slabs, L2 discard)
 };
 using TuneKey = std::tuple<int, int, int, int, int, int>;   // device, Nx, Ny, Nz, n_t, columns
 std::mutex g_tune_mu;
@@ -1591,15 +1639,17 @@ float time_min(cudaStream_t s, int reps, F&& f) {
 // width {4, 2, 1}.  Results are cached per (device, grid, n_t) for the process.
 TuneResult autotune(wt_ctx* c, float* H) {
     c->e32_stamp = 0;                       // trial shapes overwrite the basis fields
-    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows]]]" fixes
-    // the shapes without timing (reproducible profiling runs); the values are checked like tuned ones
+    // WT_LAUNCH_SHAPES = "nb,lb,nch,nepi,r_xy,r_z,x_direct[,two_pass[,store_vec[,table_rows[,table_flags]]]]"
+    // fixes the shapes without timing (reproducible profiling runs); the values are checked like tuned ones
     if (const char* env = std::getenv("WT_LAUNCH_SHAPES")) {
         TuneResult t{};
-        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi, &t.rxy,
-                                      &t.rz, &t.xd, &t.tp, &t.vec, &t.ys);
+        const int nread = std::sscanf(env, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d", &t.nb, &t.lb, &t.nch, &t.nepi,
+                                      &t.rxy, &t.rz, &t.xd, &t.tp, &t.vec, &t.ys, &t.tf);
         if (nread < 8) t.tp = 0;
         if (nread < 9) t.vec = 4;
         if (nread < 10) t.ys = 0;
+        if (nread < 11) t.tf = 0;
+        if (t.tf < 0 || t.tf > 3) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table flags must be 0..3");
         if (t.ys < 0 || t.ys > c->grid.Ny) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table rows must be 0..Ny");
         if (t.ys > 0 && !tables_fit(c)) t.ys = 0;
         if (nread < 7 || (t.vec != 1 && t.vec != 2 && t.vec != 4) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
@@ -1622,8 +1672,9 @@ TuneResult autotune(wt_ctx* c, float* H) {
     const wt_grid& g = c->grid;
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     const int ncol = (int)c->cols.size(), nt = (int)c->times.size();
-    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 4, 1e30, 1e30, 0};
+    TuneResult best{1, 32, 256, 8, c->sp32.rxy, c->sp32.rz, 0, 0, 4, 1e30, 1e30, 0, 0};
     c->tune_ys = 0;
+    c->tune_tf = 0;
     c->tune_nb = 1;
     c->tune_lb = 32;
     alloc_fast32(c);
@@ -1670,20 +1721,27 @@ TuneResult autotune(wt_ctx* c, float* H) {
     c->tune_lb = best.lb;
     alloc_fast32(c);
     // the lateral tables (built once per context, at the FFT shapes chosen above): slabs of
-    // 1 .. 32 y rows x z-pass lines per block, against the per-basis passes' best time
+    // 1 .. 32 y rows x z-pass lines per block x {one stream, slabs pipelined on two} x {slab kept,
+    // slab's L2 lines dropped after its z pass}, against the per-basis passes' best time
     if (tables_fit(c)) {
         build_tables(c);
         const int lb0 = best.lb;
         for (int ys : {1, 2, 4, 8, 16, 32}) {
             if (ys > g.Ny) break;
             c->tune_ys = ys;
-            for (int lb : {16, 32, 64}) {
-                c->tune_lb = lb;
-                const float ms = time_min(s, 3, [&] { spectral_all(c, s); });
-                if (ms < best.spectral_ms) { best.spectral_ms = ms; best.ys = ys; best.lb = lb; }
+            for (int tf = 0; tf < 4; ++tf) {
+                if ((tf & 2) && !(c->sp32.zsm && (g.Nx * ys) % 32 == 0)) continue;   // discard needs whole lines
+                c->tune_tf = tf;
+                for (int lb : {16, 32, 64}) {
+                    if ((tf & 2) && lb < 32) continue;
+                    c->tune_lb = lb;
+                    const float ms = time_min(s, 3, [&] { spectral_all(c, s); });
+                    if (ms < best.spectral_ms) { best.spectral_ms = ms; best.ys = ys; best.lb = lb; best.tf = tf; }
+                }
             }
         }
         c->tune_ys = best.ys;
+        c->tune_tf = best.ys ? best.tf : 0;
         c->tune_lb = best.ys ? best.lb : lb0;
         if (!best.ys) {                      // not faster here: give the memory back
             c->T32.release();
@@ -1719,6 +1777,7 @@ void apply_tuning(wt_ctx* c, const TuneResult& t) {
     c->sp32.set_radix(t.rxy, t.rz, t.tp & 1, t.tp & 2, t.tp & 4);
     c->sp32.xdirect = t.xd;
     c->tune_ys = (t.ys > 0 && tables_fit(c)) ? t.ys : 0;
+    c->tune_tf = c->tune_ys ? t.tf : 0;
     alloc_fast32(c);
     if (c->tune_ys) build_tables(c);         // the tables of this context (geometry only; kept)
     c->tuned = true;
@@ -1727,10 +1786,12 @@ void apply_tuning(wt_ctx* c, const TuneResult& t) {
 void tune_context(wt_ctx* c, float* H) { apply_tuning(c, autotune(c, H)); }
 
 BatchEntry entry_of(wt_ctx* c, const void* H) {
-    if (c->tune_ys) c->Rsl.alloc((size_t)32 * 3 * c->grid.Nz * c->grid.Nx * c->tune_ys);   // captured by address
+    if (c->tune_ys) alloc_slabs(c);   // captured by address
+    if (c->tune_ys && (c->tune_tf & 1)) ensure_aux(c);   // the second stream exists before any capture
     return BatchEntry{c, c->uid, c->version, H, c->E32.p, c->Zc32.p, c->rho32.p, c->R32.p, c->Ub.p, c->W32.p,
                       c->T32.p, c->Rsl.p, c->tune_nb, c->tune_lb, c->sp32.rxy, c->sp32.rz, (int)c->sp32.xdirect,
-                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1) | ((int)c->sp32.xsm << 2), c->tune_ys};
+                      (int)c->sp32.zsm | ((int)c->sp32.ysm << 1) | ((int)c->sp32.xsm << 2), c->tune_ys,
+                      c->tune_tf};
 }
 
 // Records the whole batch (column transforms, spectral passes of every
@@ -2031,6 +2092,7 @@ wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out) {
         out->two_pass = ctx->sp_ready ? (int)ctx->sp32.zsm | ((int)ctx->sp32.ysm << 1) | ((int)ctx->sp32.xsm << 2) : 0;
         out->store_vec = ctx->tune_vec;
         out->table_rows = ctx->tune_ys;
+        out->table_flags = ctx->tune_tf;
     });
 }
 
@@ -2278,6 +2340,15 @@ void wt_destroy(wt_ctx* ctx) {
     if (s2) cudaStreamSynchronize(s2);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->s_aux) {
+        cudaStreamSynchronize(ctx->s_aux);
+        for (int k = 0; k < 2; ++k) {
+            cudaEventDestroy(ctx->ev_tc[k]);
+            cudaEventDestroy(ctx->ev_tz[k]);
+        }
+        cudaEventDestroy(ctx->ev_fork);
+        cudaStreamDestroy(ctx->s_aux);
+    }
     if (ctx->ev_noalloc) {
         cudaEventSynchronize(ctx->ev_noalloc);
         cudaEventDestroy(ctx->ev_noalloc);

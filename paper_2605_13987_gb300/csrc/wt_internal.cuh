@@ -133,6 +133,11 @@ void trsm_lower_t(cudaStream_t s, const double* L, int n, int ldl, double* B, in
 // rounding-level directions would otherwise keep rotating).
 int jacobi_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err, int max_sweeps = 40,
                double abs_tol = 0.0);
+// Symmetric eigendecomposition by Householder tridiagonalisation, divide and conquer on the
+// tridiagonal matrix and blocked back-transformation: A (n x n row-major, destroyed) ->
+// eigenvalues w[n] (ascending), eigenvectors V (n x n, columns).  Sets d_err (DERR_TIMEOUT) if a
+// leaf's QL iteration does not converge.
+void sym_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err);
 // Singular value decomposition of the rows of A [m][n] (row-major, destroyed)
 // by one-sided (Hestenes) Jacobi: on return the rows of A are mutually
 // orthogonal (row i = sigma_i u_i^T), V [m][m] holds the accumulated rotations

@@ -94,3 +94,37 @@ def test_tables_serve_the_batch_bit_for_bit(torch, monkeypatch):
         monkeypatch.delenv("WT_LAUNCH_SHAPES", raising=False)
         for s in sens:
             s.close()
+
+
+@pytest.mark.parametrize("tf", [1, 2, 3])
+def test_pipelined_and_discarding_slabs_are_bit_equal(torch, monkeypatch, tf):
+    """Table flags (slabs pipelined on two streams, L2 lines of consumed slab rows dropped) change
+    only the schedule and the caching: the fields are bit-equal to the one-stream path, through
+    wt_extend and through a captured wt_batch_run."""
+    import paper_2605_13987_gb300 as P
+    w = W.workload("c1")                        # 32 x 32 x 64: two-pass z pass, 4-row slabs of 128 lines
+    _, tun, _ = _extend_with(P, w, None, monkeypatch, torch)
+    base = [tun["nb"], 64, tun["nch"], tun["nepi"], tun["r_xy"], tun["r_z"], tun["x_direct"],
+            tun["two_pass"] | 1, tun["store_vec"]]
+    Href, t0, _ = _extend_with(P, w, base + [4, 0], monkeypatch, torch)
+    Ht, tt, _ = _extend_with(P, w, base + [4, tf], monkeypatch, torch)
+    assert t0["table_flags"] == 0 and tt["table_flags"] == tf and tt["table_rows"] == 4
+    assert np.array_equal(Ht, Href)
+    monkeypatch.setenv("WT_LAUNCH_SHAPES", ",".join(str(v) for v in base + [4, tf]))
+    sens = []
+    try:
+        for seed in (1, 2):
+            s = P.Sensor(w.grid, w.columns)
+            s.fit()
+            s.relax(w.times)
+            sens.append(s)
+        Hb = P.extend_batch(sens)
+        Hb2 = P.extend_batch(sens)                # the captured graph replayed
+        torch.cuda.synchronize()
+        for a, b in zip(Hb, Hb2):
+            assert torch.equal(a, b)
+        assert np.array_equal(Hb[0].double().cpu().numpy(), Href)
+    finally:
+        monkeypatch.delenv("WT_LAUNCH_SHAPES", raising=False)
+        for s in sens:
+            s.close()

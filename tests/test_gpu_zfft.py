@@ -1,6 +1,7 @@
 """Every FFT variant of the FP32 path, forced through WT_LAUNCH_SHAPES:
 the z pass by the register FFT at each lane count and by the two-pass
-shared-memory FFT (Nz = 64, 128, 256), the y transforms of the plane pass
+shared-memory FFT (Nz = 64, 96, 128, 160, 192, 224, 256, 384: radix-2, 3, 5
+and 7 register DFTs), the y transforms of the plane pass
 by the register FFT and by the two-pass FFT (Ny = 64, 128) at 16 and 32
 lanes per x line, and two-pass x transforms on top, against the FP64 plain path of the same
 context (itself checked against the oracle, here for Nz = 64 and in
@@ -37,15 +38,15 @@ def _variants(nz):
         if nz % w == 0 and nz // w in (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 24):
             out.append((nz // w, 0))
         w //= 2
-    if nz in (64, 128, 256):
-        out.append((nz // 32, 1))
+    if nz in (64, 96, 128, 160, 192, 224, 256, 384):
+        out.append((out[0][0], 1))
     return out
 
 
-@pytest.mark.parametrize("nz", [64, 128, 256])
+@pytest.mark.parametrize("nz", [64, 96, 128, 160, 192, 224, 256, 384])
 def test_every_z_variant_matches_fp64(P, torch, monkeypatch, nz):
     # a time count of its own per length keeps the process-wide tuning cache out of the way
-    n_t = {64: 7, 128: 9, 256: 11}[nz]
+    n_t = {64: 7, 96: 8, 128: 9, 160: 10, 192: 13, 224: 14, 256: 11, 384: 15}[nz]
     w = W.tiny_cell(nx=8, nz=nz, n_t=n_t, radius=5 * UM)
     ref = O.solve(w).H_full() if nz == 64 else None
     H64 = None
