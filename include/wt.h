@@ -63,7 +63,11 @@ typedef enum {
 } wt_status;
 
 typedef enum { WT_FP32 = 0, WT_FP64 = 1 } wt_precision;
-typedef enum { WT_Z_MIRROR = 0, WT_Z_PERIODIC = 1 } wt_zbc;
+/* z boundary of the sensor box: a mirror (Neumann) plane at z = 0 and at z = Lz,
+ * the diamond slab between its two faces (the box is periodic in x and y, a
+ * tile of a pixel matrix).  A box periodic in z as well (a stack of sensors
+ * with no faces) is not part of this library. */
+typedef enum { WT_Z_MIRROR = 0 } wt_zbc;
 
 /* Sensor box and voxel grid.  Nx, Ny even; eps_r = relative permittivity
  * (5.7 for diamond; the columns take the same value). */
@@ -71,7 +75,7 @@ typedef struct {
     double Lx, Ly, Lz;
     int Nx, Ny, Nz;
     double eps_r;
-    int zbc;                     /* wt_zbc; only WT_Z_MIRROR in this build */
+    int zbc;                     /* wt_zbc: WT_Z_MIRROR (any other value gives WT_ERR_UNSUPPORTED) */
 } wt_grid;
 
 /* One graphitised column: axis at (x, y), spanning z0..z1, radius, and
@@ -436,6 +440,17 @@ wt_status wt_get_info(wt_ctx* ctx, wt_info* info);
  * launched. */
 wt_status wt_set_timing(wt_ctx* ctx, int enable);
 wt_status wt_get_timing(wt_ctx* ctx, double* ms3, int* n_launches);
+
+/* Stage timing of the last wt_eq1_loss_grad / wt_eq1_loss_grad_profile /
+ * wt_eq1_tangents call made with timing on (wt_set_timing), in ms of GPU
+ * time between CUDA events on the context's stream, summed over the
+ * parameters: ms6[0] base field, currents and loss; [1] the tables shared by
+ * the tangents (fit residual, modal factors, potentials, cosine tables);
+ * [2] fit tangents dC_n (derivative of the fit matrix, products, triangular
+ * solves); [3] resistive-line and modal tangents and the charge tangent
+ * dq(t); [4] time bases of the charge tangents; [5] tangent fields and
+ * currents (extensions and Eq. 1).  All zero when timing was off. */
+wt_status wt_get_grad_timing(wt_ctx* ctx, double* ms6);
 
 /* Message of the last failed call on ctx (or of a failed wt_create when
  * ctx is NULL); valid until the next call on ctx. */

@@ -19,7 +19,7 @@ WT_OK, WT_ERR_ARG, WT_ERR_GEOMETRY, WT_ERR_ILL_CONDITIONED, WT_ERR_NOT_SPD = 0, 
 WT_ERR_OOM, WT_ERR_CUDA, WT_ERR_TIMEOUT, WT_ERR_STATE, WT_ERR_NAN, WT_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
 WT_ERR_ACCURACY = 11
 WT_FP32, WT_FP64 = 0, 1
-WT_Z_MIRROR, WT_Z_PERIODIC = 0, 1
+WT_Z_MIRROR = 0
 STATUS_NAMES = {0: "WT_OK", 1: "WT_ERR_ARG", 2: "WT_ERR_GEOMETRY", 3: "WT_ERR_ILL_CONDITIONED",
                 4: "WT_ERR_NOT_SPD", 5: "WT_ERR_OOM", 6: "WT_ERR_CUDA", 7: "WT_ERR_TIMEOUT",
                 8: "WT_ERR_STATE", 9: "WT_ERR_NAN", 10: "WT_ERR_UNSUPPORTED", 11: "WT_ERR_ACCURACY"}
@@ -110,6 +110,7 @@ SIGNATURES = {
     "wt_get_info": (C.c_int, [C.c_void_p, C.POINTER(wt_info)]),
     "wt_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "wt_get_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "wt_get_grad_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "wt_last_error": (C.c_char_p, [C.c_void_p]),
     "wt_destroy": (None, [C.c_void_p]),
 }
@@ -171,8 +172,9 @@ def _ptr(x):
 def wt_create(grid, cuda_device=0):
     lib = load_library()
     ctx = C.c_void_p()
+    # any z boundary but the mirror reaches the library as an unknown code, which it rejects
     g = wt_grid(grid.Lx, grid.Ly, grid.Lz, grid.Nx, grid.Ny, grid.Nz, grid.eps_r,
-                WT_Z_MIRROR if getattr(grid, "zbc", "mirror") == "mirror" else WT_Z_PERIODIC)
+                WT_Z_MIRROR if getattr(grid, "zbc", "mirror") == "mirror" else -1)
     _check(lib.wt_create(C.byref(ctx), C.byref(g), int(cuda_device)), None)
     return ctx
 
@@ -439,6 +441,13 @@ def wt_get_timing(ctx):
     n = C.c_int(0)
     _check(load_library().wt_get_timing(ctx, ms, C.byref(n)), ctx)
     return list(ms), n.value
+
+
+def wt_get_grad_timing(ctx):
+    ms = (C.c_double * 6)()
+    _check(load_library().wt_get_grad_timing(ctx, ms), ctx)
+    keys = ("base", "shared", "fit_tangent", "modal_tangent", "tangent_basis", "tangent_fields")
+    return dict(zip(keys, list(ms)))
 
 
 def wt_destroy(ctx):

@@ -155,6 +155,7 @@ struct wt_ctx {
     bool noalloc_pending = false;
     bool ev_recorded = false;
     int last_launches = 0;
+    double grad_ms[6] = {0, 0, 0, 0, 0, 0};   // stages of the last timed loss derivative
     // launch shapes of the FP32 path (autotuned by wt_batch_run): charge vectors per spectral
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
     int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_vec = 4;
@@ -1326,6 +1327,36 @@ void kline_direction(const wt_ctx* c, const double* delta, std::vector<double>& 
 
 // I_out ([n_tracks][n_out]) and dI_out ([4][n_tracks][n_out]), device, optional: the currents and their
 // tangents (parameters 0..3 only).
+// CUDA events at the stage boundaries of one loss derivative (timing on): the time between a mark and
+// the previous one goes to the stage the later mark names.
+struct StageClock {
+    cudaStream_t s = nullptr;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> stage;
+    void mark(int k) {
+        if (!on) return;
+        cudaEvent_t e;
+        WT_CUDA(cudaEventCreate(&e));
+        WT_CUDA(cudaEventRecord(e, s));
+        ev.push_back(e);
+        stage.push_back(k);
+    }
+    void finish(double* ms, int n) {
+        if (!on || ev.empty()) return;
+        WT_CUDA(cudaEventSynchronize(ev.back()));
+        for (int k = 0; k < n; ++k) ms[k] = 0.0;
+        for (size_t i = 1; i < ev.size(); ++i) {
+            float t = 0.f;
+            WT_CUDA(cudaEventElapsedTime(&t, ev[i - 1], ev[i]));
+            if (stage[i] >= 0 && stage[i] < n) ms[stage[i]] += t;
+        }
+    }
+    ~StageClock() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, const double* delta = nullptr,
                   float* I_out = nullptr, float* dI_out = nullptr) {
     check_tracks(tr);
@@ -1346,6 +1377,11 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
     int launches = 0;
     clear_err(c);
     c->info.grad_trunc_rel = 0.0;
+    StageClock clock;
+    clock.s = s;
+    clock.on = c->timing;
+    for (double& v : c->grad_ms) v = 0.0;
+    clock.mark(-1);
     // base field and currents
     c->stage32.alloc((size_t)nt * 3 * npts);
     extend32_basis(c, c->Ub.p, c->rank, c->W32.p, nt, c->stage32.p, s, 0, &launches, false);
@@ -1356,6 +1392,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
     if (I_out) WT_CUDA(cudaMemcpyAsync(I_out, I.p, nI * sizeof(float), cudaMemcpyDeviceToDevice, s));
     *loss = dot_f32(s, I.p, I.p, nI, c->d_scr.p) / (double)nI;
     const double gscale = 2.0 / (double)nI;
+    clock.mark(0);
 
     // shared pieces: fit residual, modal factors, inverse gaps, potentials Phi(t)
     DBuf<int> sp, si;
@@ -1396,6 +1433,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
     dH.alloc((size_t)nt * 3 * npts);
     zeros.alloc((size_t)td.n_tracks * td.n_steps);
     zeros.zero(s);
+    clock.mark(1);
     DBuf<double> dCn, dKt, T, tmp, dP, Sh, Ah, Om, Mm, cm, dz, dQ, dQq, dgv, dqi;
     // parameters 0..3 (s_R, s_B, r, lambda), or 4: the node-resistivity direction delta
     const int p_first = delta ? 4 : 0, p_last = delta ? 4 : 3;
@@ -1432,6 +1470,7 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
             house_left(c, T.p, ns);                                          // dF
             dCn.alloc((size_t)ns * ns);
             symmetrize_avg(s, T.p, dCn.p, ns);
+            clock.mark(2);
         }
         // ---- resistive-line tangent: dK~
         if (has_dk) {
@@ -1508,12 +1547,14 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
         dgemm(s, false, false, ns, nt, ns, 1.0, c->Cn.p, ns, dQ.p, nt, 0.0, dQq.p, nt);
         if (has_dc) dgemm(s, false, false, ns, nt, ns, 1.0, dCn.p, ns, Phi.p, nt, 1.0, dQq.p, nt);
         check_finite(s, dQq.p, (size_t)ns * nt, c->d_err.p);
+        clock.mark(3);
         // field and current tangents
         DBuf<double> dUb;
         DBuf<float> dW;
         int dr = 0;
         double dtr = 0.0;
         compress_history(c, dQq.p, nt, dUb, dW, dr, dtr);
+        clock.mark(4);
         c->info.grad_trunc_rel = std::max(c->info.grad_trunc_rel, dtr);
         extend32_basis(c, dUb.p, dr, dW.p, nt, dH.p, s, 0, &launches, false);
         eq1_run(c, dH.p, false, td, dI.p, s);
@@ -1531,8 +1572,10 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
             if (dIo) add_f32(s, nI, dI.p, dIo);
         }
         grad[p - p_first] = gscale * acc;
+        clock.mark(5);
         if (read_err(c)) fail(WT_ERR_NAN, "non-finite or timed-out tangent");
     }
+    clock.finish(c->grad_ms, 6);
 }
 
 }  // namespace
@@ -2310,6 +2353,14 @@ wt_status wt_set_timing(wt_ctx* ctx, int enable) {
     if (!ctx) return WT_ERR_ARG;
     ctx->timing = enable != 0;
     return WT_OK;
+}
+
+wt_status wt_get_grad_timing(wt_ctx* ctx, double* ms6) {
+    if (!ctx) return WT_ERR_ARG;
+    return run(ctx, "wt_get_grad_timing", [&] {
+        if (!ms6) fail(WT_ERR_ARG, "NULL output");
+        for (int k = 0; k < 6; ++k) ms6[k] = ctx->grad_ms[k];
+    });
 }
 
 wt_status wt_get_timing(wt_ctx* ctx, double* ms3, int* n_launches) {

@@ -154,6 +154,9 @@ class Sensor:
     def timing(self):
         return B.wt_get_timing(self.ctx)
 
+    def grad_timing(self):
+        return B.wt_get_grad_timing(self.ctx)
+
     def close(self):
         if self.ctx:
             B.wt_destroy(self.ctx)

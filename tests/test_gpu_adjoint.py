@@ -216,3 +216,25 @@ def test_loss_error_paths(P, torch):
             s.loss_grad(t)
     finally:
         s.close()
+
+
+def test_gradient_stage_timing(P, torch):
+    """The library's CUDA-event split of one loss derivative: every stage timed, none negative,
+    zero again when timing is off."""
+    w, tr = _tiny()
+    s = _sensor(P, w)
+    try:
+        t = device_tracks(tr, torch)
+        s.set_timing(True)
+        L1, g1 = s.loss_grad(t)
+        st = s.grad_timing()
+        s.set_timing(False)
+        L2, g2 = s.loss_grad(t)
+        off = s.grad_timing()
+    finally:
+        s.close()
+    assert set(st) == {"base", "shared", "fit_tangent", "modal_tangent", "tangent_basis", "tangent_fields"}
+    assert all(v > 0.0 for v in st.values()), st
+    assert all(v == 0.0 for v in off.values()), off
+    # the loss reductions add block sums atomically: equal up to their order
+    assert abs(L1 - L2) <= 1e-12 * abs(L1) and np.allclose(g1, g2, rtol=1e-9, atol=0)

@@ -51,6 +51,18 @@ def test_null_handle_calls_fail_cleanly(lib):
     L.wt_destroy(None)
 
 
+def test_grid_checks_come_before_any_cuda_call(lib):
+    """wt_create rejects a non-mirror z boundary and odd lateral sizes on the host."""
+    from paper_2605_13987_gb300 import _binding as B
+    L = B.load_library()
+    ctx = ctypes.c_void_p()
+    g = B.wt_grid(55e-6, 55e-6, 100e-6, 8, 8, 16, 5.7, 1)
+    assert L.wt_create(ctypes.byref(ctx), ctypes.byref(g), 0) == B.WT_ERR_UNSUPPORTED
+    assert ctx.value is None
+    g = B.wt_grid(55e-6, 55e-6, 100e-6, 9, 8, 16, 5.7, B.WT_Z_MIRROR)
+    assert L.wt_create(ctypes.byref(ctx), ctypes.byref(g), 0) == B.WT_ERR_ARG
+
+
 def undocumented_prototypes(text):
     """Prototypes whose block of contiguous lines (typedefs, macros, other
     prototypes of a group) does not start right below a comment."""
