@@ -26,9 +26,9 @@ namespace wt {
 
 // One block of 128 threads per (line chunk, k_z, component); each thread takes VEC
 // consecutive lines and accumulates RB basis vectors in registers.  The block first stages
-// its table tile T[c][a][k_z][its lines] for every column in shared memory, all loads in
-// flight together (eight per thread at a time), so that the column loop runs on shared
-// memory; the z-transform coefficients Z[b][c][k_z] sit beside it as [c][RB].
+// its table tile T[c][a][k_z][its lines] for every column in shared memory by asynchronous
+// copies, all in flight together, so that the column loop runs on shared memory; the
+// z-transform coefficients Z[b][c][k_z] sit beside it as [c][RB].
 // T: [n_cols][3][Nz][nxy] (plane layout [y][x]); Zc: [nb][n_cols][Nz];
 // R: [r][3][Nz][nl], line j of the slab = line off + j of the plane.
 template <int RB, int VEC>
@@ -51,15 +51,20 @@ __global__ void __launch_bounds__(128) column_combine_kernel(const float* __rest
     const bool act = j < nl;                          // nl is a multiple of VEC
     const size_t cstride = (size_t)3 * Nz * nxy;
     const float* tp = T + ((size_t)comp * Nz + kz) * nxy + off + (act ? j : 0);
-    for (int c0 = 0; c0 < n_cols; c0 += 8) {
-        V q[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (act && c0 + u < n_cols) q[u] = *reinterpret_cast<const V*>(tp + (c0 + u) * cstride);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (act && c0 + u < n_cols) ts[(c0 + u) * 128 + threadIdx.x] = q[u];
-    }
+    // asynchronous copies straight into shared memory: every column's load in flight at once, no
+    // registers held for them
+    if (act)
+        for (int c = 0; c < n_cols; ++c) {
+            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ts + c * 128 + threadIdx.x));
+            const float* src = tp + c * cstride;
+            if constexpr (sizeof(V) == 16)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            else if constexpr (sizeof(V) == 8)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+        }
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (!act) return;
     float acc[RB][VEC];

@@ -40,7 +40,24 @@ __global__ void __launch_bounds__(256, RZ <= 8 ? 3 : 2) f32_zpass_kernel(GridDev
         tw[e] = twz[e];
         zs[zskew(e, RZ)] = zsh[e];          // read at m = j1 + RZ gl: the skew spreads the banks
     }
-    {   // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
+    if (nxy % 4 == 0) {
+        // thread t stages lines 4 (t % (LB / 4)) .. + 3 (two line pairs) of rows t / (LB / 4) + k:
+        // one 16-byte load per row, two 8-byte stores
+        constexpr int TPR = LB / 4, MS = 256 / TPR;
+        const int l4 = 4 * (threadIdx.x % TPR), m0 = threadIdx.x / TPR;
+        const bool lin = L0 + l4 < nxy;                  // nxy and L0 are multiples of 4: all four or none
+        const float4* sp = reinterpret_cast<const float4*>(R + ((size_t)b * 3 + comp) * nz * nxy + L0 + l4);
+        const size_t rs = nxy / 4;
+        C2<float>* d0 = cs + (size_t)(l4 >> 1) * S;
+        C2<float>* d1 = d0 + S;
+#pragma unroll 8
+        for (int m = m0; m < nz; m += MS) {
+            const float4 v = lin ? __ldg(sp + (size_t)m * rs) : make_float4(0.f, 0.f, 0.f, 0.f);
+            d0[zskew(m, RZ)] = C2<float>{v.x, v.y};
+            d1[zskew(m, RZ)] = C2<float>{v.z, v.w};
+        }
+    } else {
+        // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
         constexpr int MS = 256 / LB;
         const int l = threadIdx.x % LB, m0 = threadIdx.x / LB;
         const bool lin = L0 + l < nxy;

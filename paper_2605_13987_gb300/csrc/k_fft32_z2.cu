@@ -48,7 +48,25 @@ __global__ void __launch_bounds__(256, zpass2_min_blocks(A, B)) f32_zpass2_kerne
         const int c = e / A, a = e % A;
         tl[e] = twz[a * c];                                                 // a c < N
     }
-    {   // thread t stages line t % LB for rows t / LB + k (256 / LB); loads batched ahead of the stores
+    if (nxy % 4 == 0) {
+        // thread t stages lines 4 (t % (LB / 4)) .. + 3 of rows t / (LB / 4) + k (256 / (LB / 4)): one
+        // 16-byte load per row (four lines, two line pairs), two 8-byte stores into the pairs' rows;
+        // the loads of a batch are all in flight before the first store
+        constexpr int TPR = LB / 4, MS = 256 / TPR;
+        const int l4 = 4 * (threadIdx.x % TPR), m0 = threadIdx.x / TPR;
+        const bool lin = L0 + l4 < nxy;                  // nxy and L0 are multiples of 4: all four or none
+        const float4* sp = reinterpret_cast<const float4*>(R + ((size_t)b * 3 + comp) * N * nxy + L0 + l4);
+        const size_t rs = nxy / 4;
+        C2<float>* d0 = cs + (size_t)(l4 >> 1) * S;
+        C2<float>* d1 = d0 + S;
+#pragma unroll 8
+        for (int m = m0; m < N; m += MS) {
+            const float4 v = lin ? __ldg(sp + (size_t)m * rs) : make_float4(0.f, 0.f, 0.f, 0.f);
+            d0[m] = C2<float>{v.x, v.y};
+            d1[m] = C2<float>{v.z, v.w};
+        }
+    } else {
+        // thread t stages line t % LB for rows t / LB + k (256 / LB)
         constexpr int MS = 256 / LB;
         const int l = threadIdx.x % LB, m0 = threadIdx.x / LB;
         const bool lin = L0 + l < nxy;
@@ -134,10 +152,12 @@ __global__ void __launch_bounds__(256, zpass2_min_blocks(A, B)) f32_zpass2_kerne
         const size_t pa = ((La % nx) * ny + zl.y0 + La / nx) * (size_t)N;
         const size_t pb = ((Lb % nx) * ny + zl.y0 + Lb / nx) * (size_t)N;
         if (Lb < nxy) {
-            for (int z = gl; z < N; z += A) {     // one 64-bit read per lane feeds both lines
-                const C2<float> y = cf[(z & 1) ? N / 2 + 8 + (z >> 1) : (z >> 1)];
-                ob[pa + z] = y.x;
-                ob[pb + z] = y.y;
+            // lane takes z = 2 h and 2 h + 1: two 64-bit reads (the even and the odd half) feed one
+            // 8-byte store per line, each warp store a whole 128-byte line segment
+            for (int h = gl; h < N / 2; h += A) {
+                const C2<float> ev = cf[h], od = cf[N / 2 + 8 + h];
+                *reinterpret_cast<float2*>(ob + pa + 2 * h) = make_float2(ev.x, od.x);
+                *reinterpret_cast<float2*>(ob + pb + 2 * h) = make_float2(ev.y, od.y);
             }
         } else if (La < nxy) {
             for (int z = gl; z < N; z += A) ob[pa + z] = cf[(z & 1) ? N / 2 + 8 + (z >> 1) : (z >> 1)].x;

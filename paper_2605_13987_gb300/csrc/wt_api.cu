@@ -586,8 +586,15 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
     V.alloc((size_t)nt * nt);
     sig.alloc(nt);
     clear_err(c);
-    onesided_jacobi_rows(s, A.p, nt, ns, ns, V.p, sig.p, c->d_err.p);
-    if (read_err(c)) fail(WT_ERR_TIMEOUT, "one-sided Jacobi (time basis) did not converge");
+    double coupling = 0.0;
+    const int sweeps = onesided_jacobi_rows(s, A.p, nt, ns, ns, V.p, sig.p, c->d_err.p, 40, &coupling);
+    if (read_err(c)) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg,
+                      "one-sided Jacobi (time basis) did not converge: %d sweeps, relative coupling %.3e still rotated",
+                      sweeps, coupling);
+        fail(WT_ERR_TIMEOUT, msg);
+    }
     std::vector<double> hs(nt), hv((size_t)nt * nt);
     sig.download(hs.data(), nt, s);
     V.download(hv.data(), (size_t)nt * nt, s);
