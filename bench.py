@@ -44,6 +44,8 @@ WORKLOADS = {
              "(profiling case: H = 1.6 GB > L2)",
     "prof": "prof: c2's geometry and grid (128x128x256, 18 columns) with 64 time samples "
             "(profiling case: the spectral kernels at c2 sizes and rank, about 7 GB on the device)",
+    "prof256": "prof256: the 3x3 pixel cell at grid 96x96x192 (c4's geometry) with 256 time samples, extension "
+               "only (profiling case: the expansion at the 5x5 cell's time count, H 5.4 GB)",
     "c4": "c4: 3x3 pixel cell at grid 96x96x192, radius 5 um, 256 time samples, 1e4 straight tracks of 100 "
           "steps; the Eq. 1 loss and its gradient (resistivities, radius, pitch)",
     "scan": "scan: Sec. 5's bias-diameter scan (6-14 um in 2 um steps) on the 3x3 pixel cell 165x165x500 um, "
@@ -65,6 +67,9 @@ def make_workload(name):
         from dataclasses import replace
         w = W.workload("c2")
         return replace(w, times=W.log_times(64))
+    if name == "prof256":
+        from dataclasses import replace
+        return replace(W.workload("c4", n_tracks=1), tracks=None)
     return W.workload(name)
 
 

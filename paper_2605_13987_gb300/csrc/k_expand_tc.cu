@@ -30,8 +30,10 @@
 // until the MMAs of the previous job have completed and rewrites the
 // coefficient tiles in shared memory.
 //
-// Warp roles: warp 0 producer (TMA issue + hi/lo conversion), warp 1 TMEM
-// owner + MMA issuer, warps 2-9 epilogue.  Every mbarrier wait gives up
+// Warp roles: two producer warps (warp 0 and the last warp; each loads its
+// half of the 128-point slice by TMA and splits it into hi/lo, with its own
+// TMA barriers, so neither waits on the other), warp 1 TMEM owner + MMA
+// issuer, warps 2 .. 1 + NEPI epilogue.  Every mbarrier wait gives up
 // after ~2 s (globaltimer), sets the device error word and lets the CTA
 // unwind: the producer waits (bounded) for the TMA loads it still has in
 // flight and the MMA thread drains its own MMAs before tensor memory is
@@ -180,7 +182,8 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int RAW_BYTES = KR * BM * 4;   // one raw FP32 slice [32 basis][128 points]
+constexpr int RAW_BYTES = KR * BM * 4;   // one raw FP32 slice [32 basis][128 points], two halves
+constexpr int HALF = BM / 2;             // points per producer warp
 
 // 4 x 4 transposes within lane quads: on entry lane 4g + i holds v[4b + j] =
 // D[point 4g + i][time 4b + j]; on return v[4b + j] = D[point 4g + j][time 4b + i],
@@ -203,7 +206,7 @@ __device__ __forceinline__ void quad_transpose(float (&v)[32], int lane) {
 struct Smem {
     // tiles first (1024-byte aligned base):
     // B_hi[nt_pad x 128 B], B_lo[...], A[2 stages][hi, lo], raw[2][32][128] FP32
-    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2], drain, b_free;
+    unsigned long long a_full[2], a_empty[2], acc_full[2], acc_empty[2], raw_full[2][2], drain, b_free;
     unsigned tmem_base;
     int abort_flag;
 };
@@ -256,7 +259,7 @@ __device__ __forceinline__ void pair_transpose(float (&v)[32], int lane) {
 }
 
 template <int NEPI, int VEC>
-__global__ void __launch_bounds__(64 + 32 * NEPI, 1)
+__global__ void __launch_bounds__(96 + 32 * NEPI, 1)
     expand_tc_kernel(const __grid_constant__ Jobs J, int nt_pad_max, int n_units, int nch, int stall,
                      int* __restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -265,16 +268,17 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     unsigned char* b_hi = base;
     unsigned char* b_lo = b_hi + (size_t)nt_pad_max * 128;
     unsigned char* a_tiles = b_lo + (size_t)nt_pad_max * 128;      // [stage][hi|lo] x TILE_BYTES
-    float* raw = reinterpret_cast<float*>(a_tiles + 4 * TILE_BYTES);  // [2][KR][BM]
+    float* raw = reinterpret_cast<float*>(a_tiles + 4 * TILE_BYTES);  // [2 stages][2 halves][KR][HALF]
     Smem* S = reinterpret_cast<Smem*>(reinterpret_cast<unsigned char*>(raw) + 2 * RAW_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int job0 = job_of(J, blockIdx.x, 0);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&S->a_full[i], 32);
+            mbar_init(&S->a_full[i], 64);            // both producer warps
             mbar_init(&S->a_empty[i], 1);
-            mbar_init(&S->raw_full[i], 1);
+            mbar_init(&S->raw_full[i][0], 1);
+            mbar_init(&S->raw_full[i][1], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S->acc_full[i], 1);
@@ -300,8 +304,10 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
     constexpr int nbuf = 2, bstride = TMEM_COLS / 2;
     volatile int* abort_flag = &S->abort_flag;
 
-    if (warp == 0) {
-        // ---------------- producer: TMA loads of raw E slices, hi/lo conversion into swizzled A tiles
+    if (warp == 0 || warp == 2 + NEPI) {
+        // ---------------- producers: TMA loads of raw E half slices, hi/lo conversion into swizzled A tiles
+        const int h = warp == 0 ? 0 : 1;             // points h HALF .. h HALF + HALF - 1 of each unit
+        float* rawh = raw + h * KR * HALF;           // stage st at rawh + st * KR * BM
         int issued = 0;          // raw loads issued (unit k of this CTA goes to buffer k & 1)
         if (lane == 0)
             for (int jl = job0; issued < 2; ++issued) {
@@ -309,8 +315,9 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 if (u >= n_units) break;
                 jl = job_of(J, u, jl);
                 const int v = u - unit0_of(J, jl);
-                mbar_expect_tx(&S->raw_full[issued], RAW_BYTES);
-                tma_load_2d(raw + issued * KR * BM, &J.emap[jl], (v / 3) * BM, (v % 3) * KR, &S->raw_full[issued]);
+                mbar_expect_tx(&S->raw_full[issued][h], RAW_BYTES / 2);
+                tma_load_2d(rawh + issued * KR * BM, &J.emap[jl], (v / 3) * BM + h * HALF, (v % 3) * KR,
+                            &S->raw_full[issued][h]);
             }
         issued = __shfl_sync(0xffffffffu, issued, 0);
         int i = 0, cur = job0, jnext = job0, n_changes = 0;
@@ -321,24 +328,25 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
                 // new job: wait until the MMAs of the previous one are done, then its coefficients
                 if (!mbar_wait(&S->b_free, n_changes & 1, abort_flag, d_err)) break;
                 ++n_changes;
-                load_coeffs(J.W[j], J.nt[j], pad32(J.nt[j]), b_hi, b_lo, lane, 32);
+                load_coeffs(J.W[j], J.nt[j], pad32(J.nt[j]), b_hi, b_lo, h * 32 + lane, 64);
                 cur = j;
             }
             if (!mbar_wait(&S->a_empty[st], ((i >> 1) & 1) ^ 1, abort_flag, d_err)) break;
-            if (!mbar_wait(&S->raw_full[st], (i >> 1) & 1, abort_flag, d_err)) break;
+            if (!mbar_wait(&S->raw_full[st][h], (i >> 1) & 1, abort_flag, d_err)) break;
             unsigned char* ah = a_tiles + (size_t)(2 * st) * TILE_BYTES;
             unsigned char* al = ah + TILE_BYTES;
-            const float* rb = raw + st * KR * BM;
+            const float* rb = rawh + st * KR * BM;               // [KR][HALF]
             const int rk = J.r[cur];
 #pragma unroll
-            for (int rr = 0; rr < BM / 32; ++rr) {
-                const int row = lane + 32 * rr;                   // lane = grid point
+            for (int rr = 0; rr < HALF / 32; ++rr) {
+                const int hr = lane + 32 * rr;                    // lane = grid point of this half
+                const int row = h * HALF + hr;
 #pragma unroll
                 for (int c = 0; c < KR / 4; ++c) {
                     unsigned hi[4], lo[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float x = (4 * c + j) < rk ? rb[(4 * c + j) * BM + row] : 0.f;
+                        const float x = (4 * c + j) < rk ? rb[(4 * c + j) * HALF + hr] : 0.f;
                         hi[j] = to_tf32(x);
                         lo[j] = to_tf32(x - __uint_as_float(hi[j]));
                     }
@@ -357,14 +365,15 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
             if (u2 < n_units) jnext = job_of(J, u2, max(jnext, cur));
             if (lane == 0 && u2 < n_units) {
                 const int v2 = u2 - unit0_of(J, jnext);
-                mbar_expect_tx(&S->raw_full[st], RAW_BYTES);
-                tma_load_2d(raw + st * KR * BM, &J.emap[jnext], (v2 / 3) * BM, (v2 % 3) * KR, &S->raw_full[st]);
+                mbar_expect_tx(&S->raw_full[st][h], RAW_BYTES / 2);
+                tma_load_2d(rawh + st * KR * BM, &J.emap[jnext], (v2 / 3) * BM + h * HALF, (v2 % 3) * KR,
+                            &S->raw_full[st][h]);
             }
             if (u + 2 * gridDim.x < n_units) ++issued;
             mbar_arrive(&S->a_full[st]);
         }
         // loads still in flight after an abort: wait for them (bounded) before the CTA exits
-        for (int k = i; k < issued; ++k) mbar_wait_drain(&S->raw_full[k & 1], (k >> 1) & 1, d_err);
+        for (int k = i; k < issued; ++k) mbar_wait_drain(&S->raw_full[k & 1][h], (k >> 1) & 1, d_err);
     } else if (warp == 1) {
         // ---------------- MMA issuer (lane 0)
         int i = 0, g = 0, cur = job0;
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(64 + 32 * NEPI, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: TMEM -> H; warps 2..9, quadrant warp & 3, column slice (warp - 2) / 4
+        // ---------------- epilogue: TMEM -> H; warps 2 .. 1 + NEPI, quadrant warp & 3, column slice (warp - 2) / 4
         const int q = warp & 3;
         const int slice = (warp - 2) >> 2;
         constexpr int NSL = NEPI / 4;
@@ -510,10 +519,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 static void encode_basis_map(CUtensorMap* m, const float* E, size_t npts) {
-    // E viewed as 96 rows (component x basis index) of npts points; one box = 32 rows x 128 points
+    // E viewed as 96 rows (component x basis index) of npts points; one box = 32 rows x 64 points
+    // (half a unit: each producer warp loads its own half)
     cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)3 * tc::KR};
     cuuint64_t strides[1] = {(cuuint64_t)npts * sizeof(float)};
-    cuuint32_t box[2] = {tc::BM, tc::KR};
+    cuuint32_t box[2] = {tc::HALF, tc::KR};
     cuuint32_t es[2] = {1, 1};
     CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(E), dims, strides, box,
                                       es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -530,13 +540,13 @@ static void launch_expand(int nepi, int grid, size_t sh, cudaStream_t s, const t
                           int nch, int stall, int* d_err) {
     if (nepi == 8) {
         allow_dyn_smem(tc::expand_tc_kernel<8, VEC>, sh);
-        tc::expand_tc_kernel<8, VEC><<<grid, 64 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+        tc::expand_tc_kernel<8, VEC><<<grid, 96 + 32 * 8, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     } else if (nepi == 12) {
         allow_dyn_smem(tc::expand_tc_kernel<12, VEC>, sh);
-        tc::expand_tc_kernel<12, VEC><<<grid, 64 + 32 * 12, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+        tc::expand_tc_kernel<12, VEC><<<grid, 96 + 32 * 12, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     } else {
         allow_dyn_smem(tc::expand_tc_kernel<16, VEC>, sh);
-        tc::expand_tc_kernel<16, VEC><<<grid, 64 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
+        tc::expand_tc_kernel<16, VEC><<<grid, 96 + 32 * 16, sh, s>>>(J, nt_pad_max, units, nch, stall, d_err);
     }
 }
 
