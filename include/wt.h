@@ -327,7 +327,8 @@ typedef struct {
     int table_flags; /* table path, a bit mask: 1 the combination of one slab overlaps the z pass
                        of the previous one on a second stream (two slab buffers); 2 the z pass
                        invalidates the L2 lines of the slab rows it has read, so that the slab
-                       (scratch) is not written back to DRAM */
+                       (scratch) is not written back to DRAM; 4 the combination takes one line per
+                       thread (fewer registers, more resident warps) instead of vectors of lines */
 } wt_tuning;
 wt_status wt_get_tuning(wt_ctx* ctx, wt_tuning* out);
 

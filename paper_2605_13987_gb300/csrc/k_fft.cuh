@@ -82,6 +82,6 @@ struct Fast32 {
 // R[b][a][kz][j] = sum_c Zc[b][c][kz] T[c][a][kz][off + j] for j < nl, b < r <= 32: the planes of the
 // per-column lateral tables T [n_cols][3][Nz][nxy] combined by the basis vectors' column z-transforms.
 void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
-                    size_t off, int nl, float* R);
+                    size_t off, int nl, float* R, bool one_line = false);
 
 }  // namespace wt

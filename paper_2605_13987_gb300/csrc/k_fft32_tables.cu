@@ -109,13 +109,14 @@ static void combine_launch(cudaStream_t s, const float* T, const float* Zc, int 
 }
 
 void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
-                    size_t off, int nl, float* R) {
+                    size_t off, int nl, float* R, bool one_line) {
     if (r < 1 || r > 32) fail(WT_ERR_ARG, "column combination: rank must be 1..32");
     if (n_cols < 1 || n_cols > 96) fail(WT_ERR_UNSUPPORTED, "the lateral tables take 1 to 96 columns");
     // vectors of VEC lines when every line chunk starts aligned to them
     const uintptr_t al = reinterpret_cast<uintptr_t>(T) | reinterpret_cast<uintptr_t>(R);
-    const bool v4 = (off % 4 == 0) && (nl % 4 == 0) && (nxy % 4 == 0) && (al % 16 == 0);
-    const bool v2 = (off % 2 == 0) && (nl % 2 == 0) && (nxy % 2 == 0) && (al % 8 == 0);
+    // (one_line: one line per thread, fewer registers and more resident warps)
+    const bool v4 = !one_line && (off % 4 == 0) && (nl % 4 == 0) && (nxy % 4 == 0) && (al % 16 == 0);
+    const bool v2 = !one_line && (off % 2 == 0) && (nl % 2 == 0) && (nxy % 2 == 0) && (al % 8 == 0);
     if (r <= 8) {
         if (v4) combine_launch<8, 4>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);
         else combine_launch<8, 1>(s, T, Zc, r, n_cols, Nz, nxy, off, nl, R);

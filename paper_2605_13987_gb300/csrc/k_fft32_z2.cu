@@ -25,8 +25,9 @@ size_t zpass2_smem(int A, int B, int lb) {
     return ((size_t)(lb / 2) * zpass2_pitch(A, B) + 2 * (size_t)A * B) * sizeof(C2<float>);
 }
 
-// blocks per SM the kernel is compiled for: the larger register DFTs take more registers
-__host__ __device__ constexpr int zpass2_min_blocks(int A, int B) { return (B > 16 || (A == 16 && B > 16)) ? 2 : 3; }
+// blocks per SM the kernel is compiled for (register budget): four for DFTs up to 16 points (64
+// registers, no spills; shared memory allows four at 32 lines per block), two for the larger ones
+__host__ __device__ constexpr int zpass2_min_blocks(int A, int B) { return B > 16 ? 2 : 4; }
 
 template <int A, int B, int LB>
 __global__ void __launch_bounds__(256, zpass2_min_blocks(A, B)) f32_zpass2_kernel(GridDev g, const float* __restrict__ R,

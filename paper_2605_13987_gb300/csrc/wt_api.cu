@@ -160,7 +160,8 @@ struct wt_ctx {
     // launch, (x, y) lines per z-pass block, time samples per expansion accumulator chunk
     int tune_nb = 1, tune_lb = 32, tune_nch = 256, tune_nepi = 8, tune_vec = 4;
     int tune_ys = 0;                 // > 0: basis fields from the lateral tables, y slabs of tune_ys rows
-    int tune_tf = 0;                 // table path flags: 1 slabs pipelined on two streams, 2 L2 discard
+    int tune_tf = 0;                 // table path flags: 1 slabs pipelined on two streams, 2 L2 discard,
+                                     // 4 one line per thread in the combination
     cudaStream_t s_aux = nullptr;    // second stream of the pipelined table path
     cudaEvent_t ev_tc[2] = {nullptr, nullptr}, ev_tz[2] = {nullptr, nullptr}, ev_fork = nullptr;
     bool tuned = false;              // launch shapes chosen (first FP32 extension or batch)
@@ -885,7 +886,7 @@ void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
     if (!pipe) {
         for (int y0 = 0; y0 < g.Ny; y0 += ys) {
             const int yn = std::min(ys, g.Ny - y0);
-            column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p);
+            column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p, c->tune_tf & 4);
             c->sp32.zlines(c->Rsl.p, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, s, c->tune_lb, disc);
         }
         return;
@@ -901,7 +902,7 @@ void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
         const int yn = std::min(ys, g.Ny - y0), bi = k & 1;
         float* R = c->Rsl.p + bi * se;
         if (k >= 2) WT_CUDA(cudaStreamWaitEvent(s, c->ev_tz[bi], 0));
-        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, R);
+        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, R, c->tune_tf & 4);
         WT_CUDA(cudaEventRecord(c->ev_tc[bi], s));
         WT_CUDA(cudaStreamWaitEvent(c->s_aux, c->ev_tc[bi], 0));
         c->sp32.zlines(R, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, c->s_aux, c->tune_lb, disc);
@@ -1699,7 +1700,7 @@ TuneResult autotune(wt_ctx* c, float* H) {
         if (nread < 9) t.vec = 4;
         if (nread < 10) t.ys = 0;
         if (nread < 11) t.tf = 0;
-        if (t.tf < 0 || t.tf > 3) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table flags must be 0..3");
+        if (t.tf < 0 || t.tf > 7) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table flags must be 0..7");
         if (t.ys < 0 || t.ys > c->grid.Ny) fail(WT_ERR_ARG, "WT_LAUNCH_SHAPES: table rows must be 0..Ny");
         if (t.ys > 0 && !tables_fit(c)) t.ys = 0;
         if (nread < 7 || (t.vec != 1 && t.vec != 2 && t.vec != 4) || (t.nb != 1 && t.nb != 2 && t.nb != 4) ||
@@ -1772,14 +1773,15 @@ TuneResult autotune(wt_ctx* c, float* H) {
     alloc_fast32(c);
     // the lateral tables (built once per context, at the FFT shapes chosen above): slabs of
     // 1 .. 32 y rows x z-pass lines per block x {one stream, slabs pipelined on two} x {slab kept,
-    // slab's L2 lines dropped after its z pass}, against the per-basis passes' best time
+    // slab's L2 lines dropped after its z pass} x {vectors of lines, one line per thread in the
+    // combination}, against the per-basis passes' best time
     if (tables_fit(c)) {
         build_tables(c);
         const int lb0 = best.lb;
         for (int ys : {1, 2, 4, 8, 16, 32}) {
             if (ys > g.Ny) break;
             c->tune_ys = ys;
-            for (int tf = 0; tf < 4; ++tf) {
+            for (int tf = 0; tf < 8; ++tf) {
                 if ((tf & 2) && !(c->sp32.zsm && (g.Nx * ys) % 32 == 0)) continue;   // discard needs whole lines
                 c->tune_tf = tf;
                 for (int lb : {16, 32, 64}) {

@@ -96,7 +96,7 @@ def test_tables_serve_the_batch_bit_for_bit(torch, monkeypatch):
             s.close()
 
 
-@pytest.mark.parametrize("tf", [1, 2, 3])
+@pytest.mark.parametrize("tf", [1, 2, 3, 4, 7])
 def test_pipelined_and_discarding_slabs_are_bit_equal(torch, monkeypatch, tf):
     """Table flags (slabs pipelined on two streams, L2 lines of consumed slab rows dropped) change
     only the schedule and the caching: the fields are bit-equal to the one-stream path, through
