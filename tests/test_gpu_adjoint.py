@@ -122,11 +122,11 @@ def test_readout_resistivity_dominates_bias(P, torch):
 
 
 def test_adjoint_workload_gradient_vs_fd_of_fp64_loss(P, torch):
-    """3x3 cell at grid 96x96x192, 256 time samples: the hand-written
-    gradient against central differences of the library's FP64 loss (plain
-    FP64 field and Eq. 1) on re-fitted perturbed designs."""
+    """3x3 cell at grid 96x96x192, 256 time samples, 1e4 tracks: the
+    hand-written gradient against central differences of the library's FP64
+    loss (plain FP64 field and Eq. 1) on re-fitted perturbed designs."""
     from paper_2605_13987_gb300.autograd import design_at
-    w = W.workload("c4", n_tracks=1000)
+    w = W.workload("c4")                         # the configuration's 1e4 tracks of 100 steps
     tr = device_tracks(w.tracks, torch)
     base = np.array([1.0, 1.0, 0.0, 1.0])
     sen = _sensor(P, w)
