@@ -142,6 +142,81 @@ __global__ void trd_tail_kernel(const double* A, int n, double* d, double* e, do
     tau[n - 1] = 0.0;
 }
 
+// Small matrices (n <= kSmallTrd) in one block: the same four steps per column on a copy of A in
+// shared memory (rows of pitch n), then A (reflectors in its rows), d, e, tau written back.
+constexpr int kSmallTrd = 96;
+__global__ void __launch_bounds__(1024) trd_small_kernel(double* A, int n, double* d, double* e, double* tau) {
+    extern __shared__ double sm[];
+    double* a = sm;                       // [n][n]
+    double* v = a + (size_t)n * n;        // [n]
+    double* p = v + n;                    // [n]
+    __shared__ double red[33];
+    __shared__ double par[3];             // tau, beta, scale
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) a[i] = A[i];
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        double* row = a + (size_t)k * n + k + 1;
+        double ss = 0.0;
+        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) ss = fma(row[i], row[i], ss);
+        ss = block_sum(ss, red);
+        if (threadIdx.x == 0) {
+            const double x0 = row[0];
+            double t = 0.0, beta = x0, scale = 0.0;
+            if (ss > 0.0) {
+                beta = -copysign(sqrt(fma(x0, x0, ss)), x0);
+                t = (beta - x0) / beta;
+                scale = 1.0 / (x0 - beta);
+            }
+            par[0] = t;
+            par[1] = beta;
+            par[2] = scale;
+            d[k] = a[(size_t)k * n + k];
+            e[k] = beta;
+            tau[k] = t;
+        }
+        __syncthreads();
+        const double t = par[0], scale = par[2];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double vi = i == 0 ? 1.0 : row[i] * scale;
+            v[i] = vi;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = v[i];
+        // p = tau A22 v, one thread per row
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double* r = a + (size_t)(k + 1 + i) * n + k + 1;
+            double acc = 0.0;
+            for (int j = 0; j < m; ++j) acc = fma(r[j], v[j], acc);
+            p[i] = t * acc;
+        }
+        __syncthreads();
+        double sv = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) sv = fma(p[i], v[i], sv);
+        sv = block_sum(sv, red);
+        const double al = 0.5 * t * sv;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = fma(-al, v[i], p[i]);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int i = idx / m, j = idx % m;
+            double* x = a + (size_t)(k + 1 + i) * n + k + 1 + j;
+            *x = __dsub_rn(*x, __dadd_rn(__dmul_rn(v[i], p[j]), __dmul_rn(p[i], v[j])));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (n >= 2) {
+            d[n - 2] = a[(size_t)(n - 2) * n + n - 2];
+            e[n - 2] = a[(size_t)(n - 2) * n + n - 1];
+            tau[n - 2] = 0.0;
+        }
+        d[n - 1] = a[(size_t)(n - 1) * n + n - 1];
+        e[n - 1] = 0.0;
+        tau[n - 1] = 0.0;
+    }
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) A[i] = a[i];
+}
+
 // ------------------------------------------------------- divide and conquer
 // Take |rho| off the diagonal entries on both sides of every split (one thread, in order).
 __global__ void dc_split_kernel(double* d, const double* e, const int* splits, int n_splits) {
@@ -428,7 +503,9 @@ __global__ void __launch_bounds__(128) dc_secular_kernel(const DcNode* __restric
         if (w <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) break;
         double tn = t - f / fp;
         if (!(tn > lo && tn < hi) || (fabs(tn - t) > 0.5 * w && it > 2)) tn = 0.5 * (lo + hi);
-        if (tn == t) break;
+        // converged: the step is at the rounding level of tau (Newton may otherwise alternate
+        // between neighbouring values until the iteration limit)
+        if (fabs(tn - t) <= 2.0 * kEps * fabs(t)) { t = tn; break; }
         t = tn;
     }
     W.org[l + j] = org;
@@ -584,15 +661,21 @@ void sym_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err)
     tau.alloc(n);
     vk.alloc(n);
     p.alloc(n);
-    // 1. tridiagonalisation
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        trd_house_kernel<<<1, 1024, 0, s>>>(A, n, k, vk.p, d.p, e.p, tau.p);
-        trd_symv_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, n, k, vk.p, tau.p, p.p);
-        trd_w_kernel<<<1, 1024, 0, s>>>(n, k, vk.p, tau.p, p.p);
-        trd_syr2_kernel<<<dim3((m + 255) / 256, (m + 3) / 4), 256, 0, s>>>(A, n, k, vk.p, p.p);
+    // 1. tridiagonalisation (small matrices in one block)
+    if (n <= kSmallTrd) {
+        const size_t sh = ((size_t)n * n + 2 * (size_t)n) * sizeof(double);
+        allow_dyn_smem(trd_small_kernel, sh);
+        trd_small_kernel<<<1, 1024, sh, s>>>(A, n, d.p, e.p, tau.p);
+    } else {
+        for (int k = 0; k + 2 < n; ++k) {
+            const int m = n - k - 1;
+            trd_house_kernel<<<1, 1024, 0, s>>>(A, n, k, vk.p, d.p, e.p, tau.p);
+            trd_symv_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, n, k, vk.p, tau.p, p.p);
+            trd_w_kernel<<<1, 1024, 0, s>>>(n, k, vk.p, tau.p, p.p);
+            trd_syr2_kernel<<<dim3((m + 255) / 256, (m + 3) / 4), 256, 0, s>>>(A, n, k, vk.p, p.p);
+        }
+        trd_tail_kernel<<<1, 32, 0, s>>>(A, n, d.p, e.p, tau.p);
     }
-    trd_tail_kernel<<<1, 32, 0, s>>>(A, n, d.p, e.p, tau.p);
     WT_LAUNCH("tridiagonalisation");
     vk.release();
     p.release();
