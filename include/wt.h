@@ -151,7 +151,10 @@ wt_status wt_fit(wt_ctx* ctx, const wt_fit_opts* opts, double* cond_estimate_out
 /* Relaxation in time (Abstract: third-order quasi-static PDE; Sec. 3
  * forward-Euler iteration, here its exact limit), FP64 on the GPU:
  * C_n dphi/dt = K phi + b with the resistive lines of Sec. 5, solved by
- * the generalised symmetric eigenproblem on the neutral subspace; the node
+ * the generalised symmetric eigenproblem on the neutral subspace (Cholesky
+ * reduction, Householder tridiagonalisation, divide and conquer; the
+ * environment variable WT_EIGEN=jacobi selects a two-sided Jacobi solver
+ * instead, a cross-check; wt_get_modes returns the rates ascending); the node
  * charges q(t_n) at the n_t host times t[] (seconds, increasing, > 0), and
  * the rank-r time basis used by the FP32 path: the singular value
  * decomposition of the charge history [q(t_0) ... q(t_{n_t-1})] (one-sided

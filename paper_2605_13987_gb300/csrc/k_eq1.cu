@@ -6,13 +6,16 @@
 // last grid planes); between time samples: linear in t, W(0) = 0, held after
 // the last sample.  One block per track: the dot products W(x_m', t_n) . v_m'
 // at the time samples are staged in shared memory for a chunk of steps, then
-// every output time accumulates its lags in FP64.
+// every output time accumulates its lags: the FP64 field in FP64; the FP32
+// field as current increments, FP32 within a chunk and FP64 across chunks.
 #include "wt_internal.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 namespace wt {
 
@@ -27,6 +30,39 @@ struct Eq1Lag64 {
 };
 
 constexpr int EQ1_MC = 16;   // track steps per chunk
+
+// Current increments of one chunk of track steps (FP32 field): for output m,
+//   D(m) = Q(tau_m) - Q(tau_{m-1}) = sum_j [g_j(m - m'_j) - g_j(m - m'_j - 1)] dt,
+// g_j(L) = W(x_j, (L + 1/2) dt) . v_j (linear in time between the staged samples f[j][n],
+// g_j(-1) = 0), summed in FP32 over the chunk's steps (at most EQ1_MC terms, each a difference of
+// neighbouring lags, so nothing large cancels) and carried across chunks in FP64: one FP64
+// addition per output and chunk instead of FP64 products per lag (GB300's FP64 rate is low).
+__device__ __forceinline__ float eq1_interp(const float* __restrict__ fj, int nt, Eq1Lag lg) {
+    return fmaf(lg.w0, fj[lg.n], lg.w1 * fj[min(lg.n + 1, nt - 1)]);
+}
+__device__ __forceinline__ void eq1_increments(const float* __restrict__ f, int nt, int mc, int c0, int n_out,
+                                               const Eq1Lag* __restrict__ lags, double* __restrict__ D) {
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+        const int jmax = min(mc - 1, m - c0);
+        if (jmax < 0) continue;
+        // step j sees lag L = m - c0 - j; the entry of lag L - 1 is the next step's entry of lag L
+        int L = m - c0;
+        Eq1Lag hi = lags[L];
+        float d = 0.f;
+        for (int j = 0; j <= jmax; ++j, --L) {
+            const float* fj = f + j * nt;
+            const float g_hi = eq1_interp(fj, nt, hi);
+            if (L == 0) {
+                d += g_hi;
+                break;
+            }
+            const Eq1Lag lo = lags[L - 1];
+            d += g_hi - eq1_interp(fj, nt, lo);
+            hi = lo;
+        }
+        D[m] += (double)d;
+    }
+}
 
 // T: field type; L: lag table entry; TO: current type
 template <class T, class L, class TO>
@@ -80,20 +116,27 @@ __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int N
             f[j * nt + n] = acc;
         }
         __syncthreads();
-        for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
-            double q = 0.0;
-            const int jmax = min(mc - 1, m - c0);
-            for (int j = 0; j <= jmax; ++j) {
-                const L lg = lags[m - (c0 + j)];
-                q += (double)lg.w0 * (double)f[j * nt + lg.n] + (double)lg.w1 * (double)f[j * nt + min(lg.n + 1, nt - 1)];
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 field: increments D(m) = Q(tau_m) - Q(tau_{m-1}) over dt, accumulated in Q
+            eq1_increments(f, nt, mc, c0, n_out, lags, Q);
+        } else {
+            for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+                double q = 0.0;
+                const int jmax = min(mc - 1, m - c0);
+                for (int j = 0; j <= jmax; ++j) {
+                    const L lg = lags[m - (c0 + j)];
+                    q += (double)lg.w0 * (double)f[j * nt + lg.n] +
+                         (double)lg.w1 * (double)f[j * nt + min(lg.n + 1, nt - 1)];
+                }
+                Q[m] += q * dt;
             }
-            Q[m] += q * dt;
         }
     }
     __syncthreads();
     const float qc = qtrack ? qtrack[tr] : qconst;
     for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
-        const double dq = Q[m] - (m ? Q[m - 1] : 0.0);
+        // FP32 field: Q holds the increments already (the dt of Q and of the derivative cancel)
+        const double dq = std::is_same<T, float>::value ? Q[m] * dt : Q[m] - (m ? Q[m - 1] : 0.0);
         out[(size_t)tr * n_out + m] = (TO)(-(double)qc * inv_vw * dq / dt);
     }
 }
@@ -131,8 +174,10 @@ void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int n
 // W(x_j, t_n) . v_j = sum_m W[t_n][m] (E_m(x_j) . v_j), the interpolation being linear, so per
 // track step the r basis fields are interpolated once instead of the field at every time
 // sample (r x 24 gathers from E instead of n_t x 24 from H).  Lags, accumulation and currents
-// as in eq1_kernel.
-__global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict__ E, int r,
+// as in eq1_kernel.  The basis fields are read point-major, Ep[p][c][32] (eq1_point_major): one
+// warp per track step, a lane per basis field, so that each of the 24 corner-component reads is
+// one 128-byte line, and the two z neighbours of a corner are adjacent lines.
+__global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict__ Ep, int r,
                                                         const float* __restrict__ W32, int Nx, int Ny, int Nz,
                                                         int nt, float inv_hx, float inv_hy, float inv_hz,
                                                         const float* __restrict__ X, const float* __restrict__ Y,
@@ -142,13 +187,13 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
                                                         int n_out, double dt, double inv_vw,
                                                         const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Wt = reinterpret_cast<float*>(smem_raw);                          // [r][nt]
-    float* sv = Wt + (size_t)r * nt;                                         // [EQ1_MC][32]
-    float* f = sv + EQ1_MC * 32;                                             // [EQ1_MC][nt]
+    float* sv = reinterpret_cast<float*>(smem_raw);                          // [32][EQ1_MC] (basis-major)
+    float* Wt = sv + 32 * EQ1_MC;                                            // [r][nt]
+    float* f = Wt + (size_t)r * nt;                                          // [EQ1_MC][nt]
     double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * nt + EQ1_MC * 32 + (size_t)EQ1_MC * nt) *
                                                         sizeof(float) + 15) & ~(size_t)15));   // [n_out]
     const int tr = blockIdx.x;
-    const size_t npts = (size_t)Nx * Ny * Nz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < r * nt; e += blockDim.x) {
         const int m = e / nt, n = e - m * nt;
         Wt[e] = W32[(size_t)n * 32 + m];
@@ -157,8 +202,7 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
     for (int c0 = 0; c0 < n_steps; c0 += EQ1_MC) {
         const int mc = min(EQ1_MC, n_steps - c0);
         __syncthreads();
-        for (int e = threadIdx.x; e < mc * r; e += blockDim.x) {
-            const int j = e / r, m = e - j * r;
+        for (int j = warp; j < mc; j += nwarps) {
             const size_t s = (size_t)tr * n_steps + c0 + j;
             const float vx = VX[s], vy = VY[s], vz = VZ[s];
             float acc = 0.f;
@@ -171,49 +215,98 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
                 const float wx = fx - flx, wy = fy - fly, wz = fz - (float)k0;
                 const int i0 = ((int)flx % Nx + Nx) % Nx, j0 = ((int)fly % Ny + Ny) % Ny;
                 const int i1 = (i0 + 1) % Nx, j1 = (j0 + 1) % Ny;
-                const size_t a00 = ((size_t)i0 * Ny + j0) * Nz + k0, a01 = ((size_t)i0 * Ny + j1) * Nz + k0;
-                const size_t a10 = ((size_t)i1 * Ny + j0) * Nz + k0, a11 = ((size_t)i1 * Ny + j1) * Nz + k0;
+                // 96 floats per point; the z neighbour is the next point
+                const float* p00 = Ep + (((size_t)i0 * Ny + j0) * Nz + k0) * 96 + lane;
+                const float* p01 = Ep + (((size_t)i0 * Ny + j1) * Nz + k0) * 96 + lane;
+                const float* p10 = Ep + (((size_t)i1 * Ny + j0) * Nz + k0) * 96 + lane;
+                const float* p11 = Ep + (((size_t)i1 * Ny + j1) * Nz + k0) * 96 + lane;
                 float w[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float* h = E + ((size_t)c * 32 + m) * npts;
-                    const float v00 = (1.f - wz) * h[a00] + wz * h[a00 + 1];
-                    const float v01 = (1.f - wz) * h[a01] + wz * h[a01 + 1];
-                    const float v10 = (1.f - wz) * h[a10] + wz * h[a10 + 1];
-                    const float v11 = (1.f - wz) * h[a11] + wz * h[a11 + 1];
+                    const int o = 32 * c;
+                    const float v00 = (1.f - wz) * __ldg(p00 + o) + wz * __ldg(p00 + 96 + o);
+                    const float v01 = (1.f - wz) * __ldg(p01 + o) + wz * __ldg(p01 + 96 + o);
+                    const float v10 = (1.f - wz) * __ldg(p10 + o) + wz * __ldg(p10 + 96 + o);
+                    const float v11 = (1.f - wz) * __ldg(p11 + o) + wz * __ldg(p11 + 96 + o);
                     w[c] = (1.f - wx) * ((1.f - wy) * v00 + wy * v01) + wx * ((1.f - wy) * v10 + wy * v11);
                 }
                 acc = w[0] * vx + w[1] * vy + w[2] * vz;
             }
-            sv[j * 32 + m] = acc;
+            sv[lane * EQ1_MC + j] = lane < r ? acc : 0.f;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < mc * nt; e += blockDim.x) {
-            const int j = e / nt, n = e - j * nt;
-            float acc = 0.f;
-            for (int m = 0; m < r; ++m) acc = fmaf(Wt[m * nt + n], sv[j * 32 + m], acc);
-            f[j * nt + n] = acc;
-        }
-        __syncthreads();
-        for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
-            double q = 0.0;
-            const int jmax = min(mc - 1, m - c0);
-            for (int j = 0; j <= jmax; ++j) {
-                const Eq1Lag lg = lags[m - (c0 + j)];
-                q += (double)lg.w0 * (double)f[j * nt + lg.n] + (double)lg.w1 * (double)f[j * nt + min(lg.n + 1, nt - 1)];
+        // f[j][n] = sum_m W[t_n][m] sv[m][j]: four time samples (nq apart, so that a warp reads
+        // consecutive words of Wt) by four steps per thread
+        const int nq = (nt + 3) >> 2, ng = (mc + 3) >> 2;
+        for (int e = threadIdx.x; e < nq * ng; e += blockDim.x) {
+            const int n0 = e % nq, j0 = 4 * (e / nq);
+            float acc[4][4] = {};
+            for (int m = 0; m < r; ++m) {
+                const float4 s4 = *reinterpret_cast<const float4*>(sv + m * EQ1_MC + j0);
+                const float* wr = Wt + (size_t)m * nt;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int n = n0 + i * nq;
+                    const float wv = n < nt ? wr[n] : 0.f;
+                    acc[i][0] = fmaf(wv, s4.x, acc[i][0]);
+                    acc[i][1] = fmaf(wv, s4.y, acc[i][1]);
+                    acc[i][2] = fmaf(wv, s4.z, acc[i][2]);
+                    acc[i][3] = fmaf(wv, s4.w, acc[i][3]);
+                }
             }
-            Q[m] += q * dt;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int n = n0 + i * nq;
+                if (n >= nt) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q < mc) f[(j0 + q) * nt + n] = acc[i][q];
+            }
         }
+        __syncthreads();
+        eq1_increments(f, nt, mc, c0, n_out, lags, Q);
     }
     __syncthreads();
     const float qc = qtrack ? qtrack[tr] : qconst;
-    for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
-        const double dq = Q[m] - (m ? Q[m - 1] : 0.0);
-        out[(size_t)tr * n_out + m] = (float)(-(double)qc * inv_vw * dq / dt);
+    for (int m = threadIdx.x; m < n_out; m += blockDim.x)
+        out[(size_t)tr * n_out + m] = (float)(-(double)qc * inv_vw * Q[m]);
+}
+
+// Point-major copy of the basis fields for eq1_basis_kernel: Ep[p][c][m] = E[c][m][p] for m < r, 0 for
+// r <= m < 32 (E: [3][32][npts], rows m >= r need not be written).  A block moves a tile of 32 points x
+// 96 rows through shared memory: coalesced 128-byte row reads, one contiguous 12 KB write.
+__global__ void __launch_bounds__(256) eq1_point_major_kernel(const float* __restrict__ E, int r, size_t npts,
+                                                              float* __restrict__ Ep) {
+    __shared__ float tile[96][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t ntiles = (npts + 31) / 32;
+    for (size_t tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const size_t p0 = tb * 32;
+        const size_t p = p0 + lane;
+        for (int row = warp; row < 96; row += 8) {
+            const int m = row & 31;
+            tile[row][lane] = (m < r && p < npts) ? __ldg(E + (size_t)row * npts + p) : 0.f;
+        }
+        __syncthreads();
+        const int np = (int)min((size_t)32, npts - p0);
+        float* o = Ep + p0 * 96;
+        for (int e = threadIdx.x; e < np * 96; e += 256) o[e] = tile[e % 96][e / 96];
+        __syncthreads();
     }
 }
 
-void eq1_basis_launch(cudaStream_t s, const float* E, int r, const float* W32, int Nx, int Ny, int Nz, int nt,
+void eq1_point_major(cudaStream_t s, const float* E, int r, size_t npts, float* Ep) {
+    if (npts == 0) return;
+    int dev = 0, num_sms = 0;
+    WT_CUDA(cudaGetDevice(&dev));
+    WT_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t ntiles = (npts + 31) / 32;
+    const int grid = (int)std::min<size_t>(ntiles, (size_t)num_sms * 8);
+    eq1_point_major_kernel<<<grid, 256, 0, s>>>(E, r, npts, Ep);
+    WT_LAUNCH("eq1_point_major");
+}
+
+void eq1_basis_launch(cudaStream_t s, const float* Ep, int r, const float* W32, int Nx, int Ny, int Nz, int nt,
                       double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
                       const float* vx, const float* vy, const float* vz, const float* q, float qconst, int n_tracks,
                       int n_steps, int n_out, double dt, double v_w, const void* lags, float* out) {
@@ -223,7 +316,7 @@ void eq1_basis_launch(cudaStream_t s, const float* E, int r, const float* W32, i
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
     allow_dyn_smem(eq1_basis_kernel, sh);
     if (n_tracks > 0)
-        eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(E, r, W32, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly),
+        eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(Ep, r, W32, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly),
                                                    (float)(Nz / Lz), x, y, z, vx, vy, vz, q, qconst, n_steps, n_out,
                                                    dt, 1.0 / v_w, static_cast<const Eq1Lag*>(lags), out);
     WT_LAUNCH("eq1_basis");

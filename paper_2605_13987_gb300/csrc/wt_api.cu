@@ -66,6 +66,7 @@ size_t eq1_lag64_size();
 void eq1_pack_lag64(void*, int, double, double);
 double dot_f64(cudaStream_t, const double*, const double*, size_t, double*);
 void shape_launch(cudaStream_t, const float*, int, int, double, double, int, double, double, const float*, float*);
+void eq1_point_major(cudaStream_t, const float*, int, size_t, float*);
 void eq1_basis_launch(cudaStream_t, const float*, int, const float*, int, int, int, int, double, double, double,
                       const float*, const float*, const float*, const float*, const float*, const float*,
                       const float*, float, int, int, int, double, double, const void*, float*);
@@ -132,6 +133,7 @@ struct wt_ctx {
     Spectral<double> sp64;
     bool sp_ready = false;
     DBuf<float> Zc32, rho32, R32, E32;
+    DBuf<float> Ep32;                // point-major copy of E32 for Eq. 1 from the rank-r form
     // per-column lateral tables of the FP32 path ([n_cols][3][Nz][Ny][Nx], geometry only; built once)
     // and the slab buffer of the combined planes ([32][3][Nz][ys][Nx])
     DBuf<float> T32, Rsl;
@@ -1215,7 +1217,10 @@ void eq1_basis_run(wt_ctx* c, const float* E, int r, const float* W32, const Tra
     const int nt = (int)c->times.size();
     DBuf<unsigned char> dlag;
     build_lags(c, t.dt, t.n_out, dlag, s, false);
-    eq1_basis_launch(s, E, r, W32, g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
+    const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
+    c->Ep32.alloc(npts * 96);
+    eq1_point_major(s, E, r, npts, c->Ep32.p);
+    eq1_basis_launch(s, c->Ep32.p, r, W32, g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
                      vz_override ? vz_override : t.vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt,
                      c->opts.v_w, dlag.p, out);
     WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
