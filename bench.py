@@ -46,6 +46,9 @@ WORKLOADS = {
             "(profiling case: the spectral kernels at c2 sizes and rank, about 7 GB on the device)",
     "prof256": "prof256: the 3x3 pixel cell at grid 96x96x192 (c4's geometry) with 256 time samples, extension "
                "only (profiling case: the expansion at the 5x5 cell's time count, H 5.4 GB)",
+    "prof_eq1": "prof_eq1: the 3x3 pixel cell at grid 96x96x192 (c4's geometry) with 256 time samples, Eq. 1 "
+                "from the rank-r form against 2e4 drift tracks of 200 steps (the 5x5 cell's track recipe) "
+                "(profiling case: basis fields 0.68 GB)",
     "c4": "c4: 3x3 pixel cell at grid 96x96x192, radius 5 um, 256 time samples, 1e4 straight tracks of 100 "
           "steps; the Eq. 1 loss and its gradient (resistivities, radius, pitch)",
     "scan": "scan: Sec. 5's bias-diameter scan (6-14 um in 2 um steps) on the 3x3 pixel cell 165x165x500 um, "
@@ -70,6 +73,12 @@ def make_workload(name):
     if name == "prof256":
         from dataclasses import replace
         return replace(W.workload("c4", n_tracks=1), tracks=None)
+    if name == "prof_eq1":
+        import numpy as np
+        from dataclasses import replace
+        w = W.workload("c4", n_tracks=1)
+        tr = W.configs.drift_tracks(w.grid, w.columns, 20_000, 200, 1.5e-12, np.random.default_rng(7))
+        return replace(w, tracks=tr)
     return W.workload(name)
 
 
@@ -540,9 +549,53 @@ def run_large(args):
                 "stage_ms": {"extension": ext_ms, "eq1": eq1_ms}, "extension_stage_ms": ext_stages,
                 "extension_frac_of_hbm_roof": 12.0 * ps / (ext_ms / 1e3) / 1e9 / peaks()[0],
                 "checks": checks, "tuning": sen.tuning(), "clocks": clk.summary(local), "setup_s": setup,
-                "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond},
+                "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond,
+                          "fit_correction": info["fit_correction"], "fit_refined": info["fit_refined"]},
                 "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
         print(json.dumps(line), flush=True)
+    sen.close()
+    return 0
+
+
+def run_eq1_prof(args):
+    """Eq. 1 from the rank-r form alone (wt_eq1_direct) on the prof_eq1 workload: a profiling case
+    for the Eq. 1 kernels at the 5x5 cell's track recipe, with basis fields a tenth of its size."""
+    import numpy as np
+    import torch
+    import paper_2605_13987_gb300 as P
+
+    rank, local, world = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load_library()
+    w = make_workload("prof_eq1")
+    tr = w.tracks
+    sen = P.Sensor(w.grid, w.columns, device=local)
+    sen.fit()
+    sen.relax(w.times)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    tracks = dict(n_tracks=tr.n_tracks, n_steps=tr.n_steps, n_out=tr.n_out, dt=tr.dt, charge=1.0,
+                  x=d(tr.x), y=d(tr.y), z=d(tr.z), vx=d(tr.vx), vy=d(tr.vy), vz=d(tr.vz), q=d(tr.charge))
+    cur = torch.empty((tr.n_tracks, tr.n_out), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sen.eq1_direct(tracks, out=cur)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStart()
+    for k in range(args.steps):
+        ev[2 * k].record(stream)
+        sen.eq1_direct(tracks, out=cur)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStop()
+    ms = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
+    if rank == 0:
+        print(json.dumps({"workload": WORKLOADS["prof_eq1"], "eq1_ms": ms, "tracks": tr.n_tracks,
+                          "steps_per_track": tr.n_steps, "n_out": tr.n_out, "rank": sen.info()["rank"],
+                          "finite": bool(torch.isfinite(cur).all())}), flush=True)
     sen.close()
     return 0
 
@@ -788,7 +841,8 @@ def run_ours(args):
             "clocks": clk.summary(local),
             "setup_s": setup,
             "setup": {"fit_s": info["fit_seconds"], "relax_s": info["relax_seconds"], "cond_estimate": cond,
-                      "boundary_residual": info["boundary_residual"], "trunc_rel": info["trunc_rel"]},
+                      "boundary_residual": info["boundary_residual"], "trunc_rel": info["trunc_rel"],
+                      "fit_correction": info["fit_correction"], "fit_refined": info["fit_refined"]},
         }
         print(json.dumps(line), flush=True)
     sen.close()
@@ -827,6 +881,8 @@ def main():
         return run_scan_bench(args)
     if args.workload == "c5":
         return run_large(args)
+    if args.workload == "prof_eq1":
+        return run_eq1_prof(args)
     return run_ours(args)
 
 

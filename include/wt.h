@@ -94,12 +94,18 @@ typedef struct {
 /* Boundary fit: n_h * n_sources collocation heights times n_az azimuths
  * (az0 + 2 pi a / n_az) per column, on the column surface.  tikhonov >= 0
  * is a relative ridge weight (0 = plain least squares).  v_w = weighting
- * potential (Eq. 1: 1 V). */
+ * potential (Eq. 1: 1 V).  refine: the least-squares solve is Cholesky on
+ * the normal equations, corrected by one step of the semi-normal equations
+ * (the residual taken in the collocation space) either always (1) or (0,
+ * the default) only when the correction, probed on eight random
+ * combinations of the right-hand sides, exceeds 1e-11 of the solution
+ * (wt_info.fit_correction, wt_info.fit_refined). */
 typedef struct {
     int n_az, n_h;
     double tikhonov;
     double v_w;
     double az0;
+    int refine;
 } wt_fit_opts;
 
 /* Carrier tracks for Eq. 1, [track][step] float32 arrays, positions in m,
@@ -128,6 +134,9 @@ typedef struct {
     double grad_trunc_rel;       /* largest relative truncation of the charge tangents in the
                                     last wt_eq1_loss_grad (rank-32 time bases) */
     int Nx, Ny, Nz;              /* the context's grid (H holds n_t x 3 x Nx x Ny x Nz values) */
+    double fit_correction;       /* relative size of the semi-normal-equations correction of the fit
+                                    (the full one when applied, else the probe's estimate) */
+    int fit_refined;             /* 1 when the fit applied the correction */
 } wt_info;
 
 /* Create a context on CUDA device `cuda_device` for the given grid.

@@ -39,7 +39,7 @@ class wt_column(C.Structure):
 
 class wt_fit_opts(C.Structure):
     _fields_ = [("n_az", C.c_int), ("n_h", C.c_int), ("tikhonov", C.c_double),
-                ("v_w", C.c_double), ("az0", C.c_double)]
+                ("v_w", C.c_double), ("az0", C.c_double), ("refine", C.c_int)]
 
 
 class wt_tracks(C.Structure):
@@ -71,7 +71,8 @@ class wt_info(C.Structure):
                 ("rank", C.c_int), ("cond_estimate", C.c_double), ("boundary_residual", C.c_double),
                 ("asymmetry", C.c_double), ("trunc_rel", C.c_double), ("mu_min", C.c_double),
                 ("mu_max", C.c_double), ("fit_seconds", C.c_double), ("relax_seconds", C.c_double),
-                ("grad_trunc_rel", C.c_double), ("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int)]
+                ("grad_trunc_rel", C.c_double), ("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int),
+                ("fit_correction", C.c_double), ("fit_refined", C.c_int)]
 
 
 # name -> (restype, argtypes); the ABI of include/wt.h
@@ -187,9 +188,9 @@ def wt_add_columns(ctx, columns):
     _check(lib.wt_add_columns(ctx, arr, len(columns)), ctx)
 
 
-def wt_fit(ctx, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0):
+def wt_fit(ctx, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0, refine=0):
     lib = load_library()
-    o = wt_fit_opts(int(n_az), int(n_h), float(tikhonov), float(v_w), float(az0))
+    o = wt_fit_opts(int(n_az), int(n_h), float(tikhonov), float(v_w), float(az0), int(refine))
     cond = C.c_double(0.0)
     _check(lib.wt_fit(ctx, C.byref(o), C.byref(cond)), ctx)
     return cond.value

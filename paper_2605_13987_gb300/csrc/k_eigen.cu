@@ -453,27 +453,31 @@ __global__ void __launch_bounds__(256) dc_prep_kernel(const DcNode* __restrict__
     W.node_r[blockIdx.x] = r;
 }
 
-// f(tau) = 1 + r sum_i zeta_i^2 / ((delta_i - delta_org) - tau) and its derivative.
+// f(tau) = 1 + r sum_i zeta_i^2 / ((delta_i - delta_org) - tau) and its derivative, summed by the
+// 32 lanes of a warp (lane k takes the poles k, k + 32, ...).  The xor butterfly gives every lane
+// the same bits, so the iteration that uses them stays uniform across the warp.
 __device__ __forceinline__ void secular_f(const double* __restrict__ delta, const double* __restrict__ zeta, int kp,
                                           double dorg, double r, double tau, double* f, double* fp) {
     double s = 0.0, sp = 0.0;
-    for (int i = 0; i < kp; ++i) {
+    for (int i = threadIdx.x & 31; i < kp; i += 32) {
         const double q = 1.0 / ((delta[i] - dorg) - tau);
         const double z2 = zeta[i] * zeta[i];
         s = fma(z2, q, s);
         sp = fma(z2 * q, q, sp);
     }
+    s = warp_sum(s);
+    sp = warp_sum(sp);
     *f = fma(r, s, 1.0);
     *fp = r * sp;
 }
 
-// One thread per root: bracket between the poles, Newton steps kept inside the bracket, else
-// bisection; stops when the bracket is at the rounding level of tau.
-__global__ void __launch_bounds__(128) dc_secular_kernel(const DcNode* __restrict__ nodes, DcWork W) {
+// One warp per root (eight per block): bracket between the poles, Newton steps kept inside the
+// bracket, else bisection; stops when the bracket is at the rounding level of tau.
+__global__ void __launch_bounds__(256) dc_secular_kernel(const DcNode* __restrict__ nodes, DcWork W) {
     const DcNode nd = nodes[blockIdx.y];
     const int l = nd.l, kp = W.node_kp[blockIdx.y];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= kp) return;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= kp) return;                 // whole warps leave together
     const double r = W.node_r[blockIdx.y];
     const double* delta = W.delta + l;
     const double* zeta = W.zeta + l;
@@ -487,7 +491,8 @@ __global__ void __launch_bounds__(128) dc_secular_kernel(const DcNode* __restric
         else { org = j + 1; lo = -0.5 * gap; hi = 0.0; }
     } else {
         double zz = 0.0;
-        for (int i = 0; i < kp; ++i) zz = fma(zeta[i], zeta[i], zz);
+        for (int i = threadIdx.x & 31; i < kp; i += 32) zz = fma(zeta[i], zeta[i], zz);
+        zz = warp_sum(zz);
         org = j;
         lo = 0.0;
         hi = r * zz;
@@ -508,9 +513,11 @@ __global__ void __launch_bounds__(128) dc_secular_kernel(const DcNode* __restric
         if (fabs(tn - t) <= 2.0 * kEps * fabs(t)) { t = tn; break; }
         t = tn;
     }
-    W.org[l + j] = org;
-    W.tau[l + j] = t;
-    W.root[l + j] = dorg + t;
+    if ((threadIdx.x & 31) == 0) {
+        W.org[l + j] = org;
+        W.tau[l + j] = t;
+        W.root[l + j] = dorg + t;
+    }
 }
 
 // Loewner's formula: zh_i^2 = (lambda_last - delta_i) / r  prod_{j < i} (lambda_j - delta_i) / (delta_j - delta_i)
@@ -764,7 +771,7 @@ void sym_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err)
             for (const DcNode& nd : nodes) kmax = std::max(kmax, nd.r - nd.l);
             dc_prep_kernel<<<nn_, 256, 0, s>>>(dnodes.p, e.p, la, qa, n, Wk, zbuf.p);
             WT_LAUNCH("dc_prep");
-            dc_secular_kernel<<<dim3((kmax + 127) / 128, nn_), 128, 0, s>>>(dnodes.p, Wk);
+            dc_secular_kernel<<<dim3((kmax + 7) / 8, nn_), 256, 0, s>>>(dnodes.p, Wk);
             WT_LAUNCH("dc_secular");
             dc_loewner_kernel<<<dim3((kmax + 127) / 128, nn_), 128, 0, s>>>(dnodes.p, Wk);
             WT_LAUNCH("dc_loewner");

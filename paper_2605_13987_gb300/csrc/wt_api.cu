@@ -45,11 +45,11 @@ void sample_contract(cudaStream_t, const double*, const double*, const double*, 
                      double*);
 void eq1_launch(cudaStream_t, const float*, int, int, int, int, double, double, double, const float*, const float*,
                 const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
-                double, const void*, float*);
+                double, const void*, int, float*);
 size_t eq1_lag_size();
 void eq1_launch64(cudaStream_t, const double*, int, int, int, int, double, double, double, const float*, const float*,
                   const float*, const float*, const float*, const float*, const float*, float, int, int, int, double,
-                  double, const void*, double*);
+                  double, const void*, int, double*);
 void green_lateral_deriv(cudaStream_t, const double*, const double*, int, int, int, int, double, double, double, double,
                          int, double*);
 void modal_inv_gap(cudaStream_t, const double*, int, double*);
@@ -60,7 +60,7 @@ void add_row_const(cudaStream_t, double*, int, int, const double*);
 double dot_f32(cudaStream_t, const float*, const float*, size_t, double*);
 void eq1_noalloc_launch(cudaStream_t, int, const float*, int, int, int, const double*, int, double, double, double,
                         const float*, const float*, const float*, const float*, const float*, const float*,
-                        const float*, float, int, int, int, double, double, float*);
+                        const float*, float, int, int, int, double, double, int, float*);
 void eq1_pack_lag(void*, int, float, float);
 size_t eq1_lag64_size();
 void eq1_pack_lag64(void*, int, double, double);
@@ -69,7 +69,7 @@ void shape_launch(cudaStream_t, const float*, int, int, double, double, int, dou
 void eq1_point_major(cudaStream_t, const float*, int, size_t, float*);
 void eq1_basis_launch(cudaStream_t, const float*, int, const float*, int, int, int, int, double, double, double,
                       const float*, const float*, const float*, const float*, const float*, const float*,
-                      const float*, float, int, int, int, double, double, const void*, float*);
+                      const float*, float, int, int, int, double, double, const void*, int, float*);
 void features_launch(cudaStream_t, const float*, int, int, double, double, float, float, float, const float*, int,
                      double*, double*);
 void add_f32(cudaStream_t, size_t, const float*, float*);
@@ -478,7 +478,41 @@ void do_fit(wt_ctx* c) {
     copy_block(s, R.p, ns, Y.p, ns, ns, ns);
     trsm_lower(s, G.p, ns, ns, Y.p, ns, ns);
     trsm_lower_t(s, G.p, ns, ns, Y.p, ns, ns);
-    {
+    // Corrected semi-normal equations: dY = G^-1 A_s^T (S - A_s Y).  Its two products cost
+    // 4 nc ns^2 flops, most of the fit; dY is linear in the right-hand sides, so its action on
+    // eight random +-1 combinations Z (dY Z, from S Z and Y Z at 8/ns of the cost) estimates
+    // ||dY|| / ||Y||, and the full step runs only when that exceeds kRefineSkip, a tenth of the
+    // FP64 path's accuracy bound (1e-10): the normal equations alone err by about cond(A_s)^2 eps.
+    constexpr double kRefineSkip = 1e-11;
+    bool refine = c->opts.refine == 1;
+    double correction = 0.0;
+    if (!refine) {
+        constexpr int kp = 8;
+        std::vector<double> hz((size_t)ns * kp), hsz((size_t)nc * kp, 0.0);
+        unsigned long long st = 0x9E3779B97F4A7C15ull;            // fixed seed: reproducible fits
+        for (double& v : hz) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            v = (st >> 63) ? 1.0 : -1.0;
+        }
+        for (int j = 0; j < ns; ++j)
+            for (int e = c->s_ptr[j]; e < c->s_ptr[j + 1]; ++e)
+                for (int k = 0; k < kp; ++k) hsz[(size_t)c->s_idx[e] * kp + k] += c->s_w[e] * hz[(size_t)j * kp + k];
+        DBuf<double> Z, Yz, Rz, Cz;
+        Z.upload(hz.data(), hz.size(), s);
+        Rz.upload(hsz.data(), hsz.size(), s);                    // S Z
+        Yz.alloc((size_t)ns * kp);
+        Cz.alloc((size_t)ns * kp);
+        dgemm(s, false, false, ns, kp, ns, 1.0, Y.p, ns, Z.p, kp, 0.0, Yz.p, kp);
+        dgemm(s, false, false, nc, kp, ns, -1.0, P.p, ns, Yz.p, kp, 1.0, Rz.p, kp);
+        dgemm(s, true, false, ns, kp, nc, 1.0, P.p, ns, Rz.p, kp, 0.0, Cz.p, kp);
+        trsm_lower(s, G.p, ns, ns, Cz.p, kp, kp);
+        trsm_lower_t(s, G.p, ns, ns, Cz.p, kp, kp);
+        const double ny = dnrm2(s, Yz.p, (size_t)ns * kp, c->d_scr.p);
+        const double nd = dnrm2(s, Cz.p, (size_t)ns * kp, c->d_scr.p);
+        correction = ny > 0.0 ? nd / ny : INFINITY;
+        refine = !(correction <= kRefineSkip);
+    }
+    if (refine) {
         DBuf<double> Res;
         Res.alloc((size_t)nc * ns);
         dgemm(s, false, false, nc, ns, ns, -1.0, P.p, ns, Y.p, ns, 0.0, Res.p, ns);
@@ -486,8 +520,12 @@ void do_fit(wt_ctx* c) {
         dgemm(s, true, false, ns, ns, nc, 1.0, P.p, ns, Res.p, ns, 0.0, R.p, ns);
         trsm_lower(s, G.p, ns, ns, R.p, ns, ns);
         trsm_lower_t(s, G.p, ns, ns, R.p, ns, ns);
+        const double ny = dnrm2(s, Y.p, (size_t)ns * ns, c->d_scr.p);
+        correction = ny > 0.0 ? dnrm2(s, R.p, (size_t)ns * ns, c->d_scr.p) / ny : INFINITY;
         axpy(s, (size_t)ns * ns, 1.0, R.p, Y.p);
     }
+    c->info.fit_correction = correction;
+    c->info.fit_refined = refine ? 1 : 0;
     // DC boundary residual || A_s (Y phi) - S phi || / || S phi ||
     {
         DBuf<double> dphi, yphi, r;
@@ -1120,8 +1158,11 @@ void do_sample(wt_ctx* c, const double* xyz, int n, const double* t, int nt, dou
 
 // Lag table of Eq. 1: (k + 1/2) dt -> bracketing samples and weights (linear
 // in t; 0 at t = 0; held after the last sample).
-void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cudaStream_t s, bool f64 = false) {
+// Returns the count of time samples the table reads (samples n0 and n0 + 1 of every lag; n0 grows
+// with the lag), so that the kernels stage no sample beyond it.
+int build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cudaStream_t s, bool f64 = false) {
     const int nt = (int)c->times.size();
+    int n0_max = 0;
     const size_t esz = f64 ? eq1_lag64_size() : eq1_lag_size();
     std::vector<unsigned char> lag(esz * (size_t)n_out);
     const std::vector<double>& ts = c->times;
@@ -1139,8 +1180,20 @@ void build_lags(wt_ctx* c, double dt, int n_out, DBuf<unsigned char>& dlag, cuda
         }
         if (f64) eq1_pack_lag64(lag.data() + esz * k, n0, w0, w1);
         else eq1_pack_lag(lag.data() + esz * k, n0, (float)w0, (float)w1);
+        n0_max = std::max(n0_max, n0);
     }
     dlag.upload(lag.data(), lag.size(), s);
+    return std::min(nt, n0_max + 2);
+}
+// The same count for a table built on the device by the same rule (the allocation-free call),
+// from the longest lag, with one sample of margin.
+int lag_samples_used(const std::vector<double>& ts, double dt, int n_out) {
+    const int nt = (int)ts.size();
+    const double L = (n_out - 0.5) * dt;
+    int n0 = 0;
+    if (L >= ts.back()) n0 = nt - 1;
+    else if (L > ts.front()) n0 = (int)(std::upper_bound(ts.begin(), ts.end(), L) - ts.begin()) - 1;
+    return std::min(nt, n0 + 3);
 }
 
 struct TrackDev {
@@ -1175,15 +1228,15 @@ void eq1_run(wt_ctx* c, const void* H, bool h64, const TrackDev& t, void* out, c
     const wt_grid& g = c->grid;
     const int nt = (int)c->times.size();
     DBuf<unsigned char> dlag;
-    build_lags(c, t.dt, t.n_out, dlag, s, h64);
+    const int nu = build_lags(c, t.dt, t.n_out, dlag, s, h64);
     const float* vz = vz_override ? vz_override : t.vz;
     if (h64)
         eq1_launch64(s, static_cast<const double*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx,
-                     t.vy, vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p,
+                     t.vy, vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, nu,
                      static_cast<double*>(out));
     else
         eq1_launch(s, static_cast<const float*>(H), g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
-                   vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p,
+                   vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt, c->opts.v_w, dlag.p, nu,
                    static_cast<float*>(out));
     WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
 }
@@ -1216,13 +1269,13 @@ void eq1_basis_run(wt_ctx* c, const float* E, int r, const float* W32, const Tra
     const wt_grid& g = c->grid;
     const int nt = (int)c->times.size();
     DBuf<unsigned char> dlag;
-    build_lags(c, t.dt, t.n_out, dlag, s, false);
+    const int nu = build_lags(c, t.dt, t.n_out, dlag, s, false);
     const size_t npts = (size_t)g.Nx * g.Ny * g.Nz;
     c->Ep32.alloc(npts * 96);
     eq1_point_major(s, E, r, npts, c->Ep32.p);
     eq1_basis_launch(s, c->Ep32.p, r, W32, g.Nx, g.Ny, g.Nz, nt, g.Lx, g.Ly, g.Lz, t.x, t.y, t.z, t.vx, t.vy,
                      vz_override ? vz_override : t.vz, t.q, t.qconst, t.n_tracks, t.n_steps, t.n_out, t.dt,
-                     c->opts.v_w, dlag.p, out);
+                     c->opts.v_w, dlag.p, nu, out);
     WT_CUDA(cudaStreamSynchronize(s));   // the lag table is freed on return
 }
 
@@ -2020,9 +2073,10 @@ wt_status wt_fit(wt_ctx* ctx, const wt_fit_opts* opts, double* cond_out) {
     if (!ctx) return WT_ERR_ARG;
     return run(ctx, "wt_fit", [&] {
         if (ctx->stage != 0) fail(WT_ERR_STATE, "wt_fit already called");
-        wt_fit_opts o{4, 2, 0.0, 1.0, 0.0};
+        wt_fit_opts o{4, 2, 0.0, 1.0, 0.0, 0};
         if (opts) o = *opts;
-        if (o.n_az < 1 || o.n_h < 1 || !(o.tikhonov >= 0) || !(o.v_w != 0) || !std::isfinite(o.az0))
+        if (o.n_az < 1 || o.n_h < 1 || !(o.tikhonov >= 0) || !(o.v_w != 0) || !std::isfinite(o.az0) ||
+            (o.refine != 0 && o.refine != 1))
             fail(WT_ERR_ARG, "bad fit options");
         ctx->opts = o;
         do_fit(ctx);
@@ -2100,7 +2154,8 @@ wt_status wt_eq1_noalloc(wt_ctx* ctx, const float* H, const wt_tracks* tr, float
         const cudaStream_t us = static_cast<cudaStream_t>(stream);
         eq1_noalloc_launch(us, ctx->dev, H, g.Nx, g.Ny, g.Nz, ctx->d_times.p,
                            (int)ctx->times.size(), g.Lx, g.Ly, g.Lz, tr->x, tr->y, tr->z, tr->vx, tr->vy, tr->vz,
-                           tr->q, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out, tr->dt, ctx->opts.v_w, i);
+                           tr->q, (float)tr->charge, tr->n_tracks, tr->n_steps, tr->n_out, tr->dt, ctx->opts.v_w,
+                           lag_samples_used(ctx->times, tr->dt, tr->n_out), i);
         // the call reads the relaxation's time samples on the caller's stream: a later wt_relax
         // waits for this event before it rewrites them (the event was created by wt_relax)
         WT_CUDA(cudaEventRecord(ctx->ev_noalloc, us));

@@ -34,8 +34,8 @@ class Sensor:
         self.n_sources = sum(int(c.n_sources) for c in self.columns)
         self.times = None
 
-    def fit(self, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0):
-        return B.wt_fit(self.ctx, n_az, n_h, tikhonov, v_w, az0)
+    def fit(self, n_az=4, n_h=2, tikhonov=0.0, v_w=1.0, az0=0.0, refine=0):
+        return B.wt_fit(self.ctx, n_az, n_h, tikhonov, v_w, az0, refine)
 
     def relax(self, times):
         self.times = np.asarray(times, dtype=np.float64)
