@@ -80,8 +80,11 @@ struct Fast32 {
 };
 
 // R[b][a][kz][j] = sum_c Zc[b][c][kz] T[c][a][kz][off + j] for j < nl, b < r <= 32: the planes of the
-// per-column lateral tables T [n_cols][3][Nz][nxy] combined by the basis vectors' column z-transforms.
-void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
+// per-column lateral tables T [n_cols][3][Nz][nxy] combined by the basis vectors' column z-transforms,
+// read as ZcT [Nz][n_cols][32] (combine_coeffs).
+void column_combine(cudaStream_t s, const float* T, const float* ZcT, int r, int n_cols, int Nz, size_t nxy,
                     size_t off, int nl, float* R, bool one_line = false);
+// ZcT[kz][c][b] = Zc[b][c][kz] for b < r, 0 for r <= b < 32 (Zc: [r][n_cols][Nz]).
+void combine_coeffs(cudaStream_t s, const float* Zc, int r, int n_cols, int Nz, float* ZcT);
 
 }  // namespace wt

@@ -24,68 +24,99 @@
 
 namespace wt {
 
+// Coefficients of the combination in the order a block reads them: ZcT[k_z][c][b] (32 per column,
+// zero for b >= r) from the column transforms Zc[b][c][k_z].
+__global__ void combine_coeffs_kernel(const float* __restrict__ Zc, int r, int n_cols, int Nz,
+                                      float* __restrict__ ZcT) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)Nz * n_cols * 32) return;
+    const int b = (int)(e % 32);
+    const size_t q = e / 32;
+    const int c = (int)(q % n_cols), kz = (int)(q / n_cols);
+    ZcT[e] = b < r ? Zc[((size_t)b * n_cols + c) * Nz + kz] : 0.f;
+}
+
+constexpr int kCombineCC = 8;      // columns per asynchronous copy group
+constexpr int kCombineStages = 3;  // copy groups in flight
+
 // One block of 128 threads per (line chunk, k_z, component); each thread takes VEC
-// consecutive lines and accumulates RB basis vectors in registers.  The block first stages
-// its table tile T[c][a][k_z][its lines] for every column in shared memory by asynchronous
-// copies, all in flight together, so that the column loop runs on shared memory; the
-// z-transform coefficients Z[b][c][k_z] sit beside it as [c][RB].
-// T: [n_cols][3][Nz][nxy] (plane layout [y][x]); Zc: [nb][n_cols][Nz];
+// consecutive lines and accumulates RB basis vectors in registers.  A thread's table values
+// T[c][a][k_z][its lines] arrive by asynchronous copies in groups of kCombineCC columns,
+// kCombineStages groups in flight, into shared memory that only this thread reads back, so
+// the column loop overlaps the copies of later columns and needs no barrier; the coefficients
+// ZcT[k_z][c][0..RB) are staged once per block, contiguous, as [c][RB].
+// T: [n_cols][3][Nz][nxy] (plane layout [y][x]); ZcT: [Nz][n_cols][32];
 // R: [r][3][Nz][nl], line j of the slab = line off + j of the plane.
 template <int RB, int VEC>
 __global__ void __launch_bounds__(128) column_combine_kernel(const float* __restrict__ T,
-                                                             const float* __restrict__ Zc, int r, int n_cols,
+                                                             const float* __restrict__ ZcT, int r, int n_cols,
                                                              int Nz, size_t nxy, size_t off, int nl,
                                                              float* __restrict__ R) {
     using V = typename std::conditional<VEC == 4, float4, typename std::conditional<VEC == 2, float2, float>::type>::type;
     constexpr int LPB = 128 * VEC;                    // lines per block
+    constexpr int CC = kCombineCC, NS = kCombineStages;
     extern __shared__ __align__(16) float smem[];
     float* zs = smem;                                 // [n_cols][RB]
-    V* ts = reinterpret_cast<V*>(smem + n_cols * RB); // [n_cols][128] vectors of VEC lines
+    V* ts = reinterpret_cast<V*>(smem + n_cols * RB); // [NS][CC][128] vectors of VEC lines
     const int kz = blockIdx.y, comp = blockIdx.z;
-    for (int e = threadIdx.x; e < n_cols * RB; e += blockDim.x) {
-        const int c = e / RB, b = e % RB;
-        zs[e] = b < r ? Zc[((size_t)b * n_cols + c) * Nz + kz] : 0.f;
-    }
+    const float* zrow = ZcT + (size_t)kz * n_cols * 32;
+    for (int e = threadIdx.x; e < n_cols * RB; e += blockDim.x) zs[e] = zrow[(e / RB) * 32 + e % RB];
     const int j0 = blockIdx.x * LPB;
     const int j = j0 + threadIdx.x * VEC;
     const bool act = j < nl;                          // nl is a multiple of VEC
     const size_t cstride = (size_t)3 * Nz * nxy;
     const float* tp = T + ((size_t)comp * Nz + kz) * nxy + off + (act ? j : 0);
-    // asynchronous copies straight into shared memory: every column's load in flight at once, no
-    // registers held for them
-    if (act)
-        for (int c = 0; c < n_cols; ++c) {
-            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ts + c * 128 + threadIdx.x));
-            const float* src = tp + c * cstride;
-            if constexpr (sizeof(V) == 16)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-            else if constexpr (sizeof(V) == 8)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    const int ngroups = (n_cols + CC - 1) / CC;
+    // group g: columns g CC .. into stage g % NS; every thread commits one (possibly empty) group
+    // per call so that the group counts stay uniform
+    auto issue = [&](int g) {
+        if (act && g < ngroups) {
+            V* dst0 = ts + (size_t)(g % NS) * CC * 128 + threadIdx.x;
+            const int c1 = min(n_cols, (g + 1) * CC);
+            for (int c = g * CC; c < c1; ++c) {
+                const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(dst0 + (c - g * CC) * 128));
+                const float* src = tp + c * cstride;
+                if constexpr (sizeof(V) == 16)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                else if constexpr (sizeof(V) == 8)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+            }
         }
-    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    if (!act) return;
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int g = 0; g < NS - 1; ++g) issue(g);
+    __syncthreads();                                  // zs staged
     float acc[RB][VEC];
 #pragma unroll
     for (int b = 0; b < RB; ++b)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[b][v] = 0.f;
-    for (int c = 0; c < n_cols; ++c) {
-        const V q = ts[c * 128 + threadIdx.x];
-        const float* t = reinterpret_cast<const float*>(&q);
-        const float4* z4 = reinterpret_cast<const float4*>(zs + c * RB);
+    for (int g = 0; g < ngroups; ++g) {
+        issue(g + NS - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");   // group g has landed
+        if (!act) continue;
+        const V* tg = ts + (size_t)(g % NS) * CC * 128 + threadIdx.x;
+        const int c1 = min(n_cols, (g + 1) * CC);
+        for (int c = g * CC; c < c1; ++c) {
+            const V q = tg[(c - g * CC) * 128];
+            const float* t = reinterpret_cast<const float*>(&q);
+            const float4* z4 = reinterpret_cast<const float4*>(zs + c * RB);
 #pragma unroll
-        for (int b4 = 0; b4 < RB / 4; ++b4) {
-            const float4 z = z4[b4];
-            const float zz[4] = {z.x, z.y, z.z, z.w};
+            for (int b4 = 0; b4 < RB / 4; ++b4) {
+                const float4 z = z4[b4];
+                const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[4 * b4 + i][v] = fmaf(zz[i], t[v], acc[4 * b4 + i][v]);
+                    for (int v = 0; v < VEC; ++v) acc[4 * b4 + i][v] = fmaf(zz[i], t[v], acc[4 * b4 + i][v]);
+            }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!act) return;
     float* rp = R + ((size_t)comp * Nz + kz) * nl + j;
     const size_t bstride = (size_t)3 * Nz * nl;
 #pragma unroll
@@ -102,10 +133,17 @@ __global__ void __launch_bounds__(128) column_combine_kernel(const float* __rest
 template <int RB, int VEC>
 static void combine_launch(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,
                            size_t off, int nl, float* R) {
-    const size_t sh = (size_t)n_cols * (RB + 128 * VEC) * sizeof(float);
+    const size_t sh = ((size_t)n_cols * RB + (size_t)kCombineStages * kCombineCC * 128 * VEC) * sizeof(float);
     allow_dyn_smem(column_combine_kernel<RB, VEC>, sh);
     dim3 gd((unsigned)((nl + 128 * VEC - 1) / (128 * VEC)), (unsigned)Nz, 3);
     column_combine_kernel<RB, VEC><<<gd, 128, sh, s>>>(T, Zc, r, n_cols, Nz, nxy, off, nl, R);
+}
+
+void combine_coeffs(cudaStream_t s, const float* Zc, int r, int n_cols, int Nz, float* ZcT) {
+    const size_t n = (size_t)Nz * n_cols * 32;
+    if (!n) return;
+    combine_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Zc, r, n_cols, Nz, ZcT);
+    WT_LAUNCH("combine_coeffs");
 }
 
 void column_combine(cudaStream_t s, const float* T, const float* Zc, int r, int n_cols, int Nz, size_t nxy,

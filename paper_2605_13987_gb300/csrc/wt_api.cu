@@ -134,6 +134,7 @@ struct wt_ctx {
     bool sp_ready = false;
     DBuf<float> Zc32, rho32, R32, E32;
     DBuf<float> Ep32;                // point-major copy of E32 for Eq. 1 from the rank-r form
+    DBuf<float> ZcT32;               // column transforms as the table combination reads them
     // per-column lateral tables of the FP32 path ([n_cols][3][Nz][Ny][Nx], geometry only; built once)
     // and the slab buffer of the combined planes ([32][3][Nz][ys][Nx])
     DBuf<float> T32, Rsl;
@@ -904,7 +905,10 @@ void build_tables(wt_ctx* c) {
 // combination of the tables' planes (into the L2-sized slab buffer) and the z pass.
 // Slab buffers of the table path: one, or two for the pipelined form.
 size_t slab_elems(const wt_ctx* c) { return (size_t)32 * 3 * c->grid.Nz * c->grid.Nx * c->tune_ys; }
-void alloc_slabs(wt_ctx* c) { c->Rsl.alloc(slab_elems(c) * ((c->tune_tf & 1) ? 2 : 1)); }
+void alloc_slabs(wt_ctx* c) {
+    c->Rsl.alloc(slab_elems(c) * ((c->tune_tf & 1) ? 2 : 1));
+    c->ZcT32.alloc((size_t)c->grid.Nz * c->cols.size() * 32);
+}
 
 // The second stream and the events of the pipelined table path (created once per context).
 void ensure_aux(wt_ctx* c) {
@@ -923,10 +927,12 @@ void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
     const int ncol = (int)c->cols.size(), ys = c->tune_ys;
     const bool pipe = c->tune_tf & 1, disc = c->tune_tf & 2;
     alloc_slabs(c);
+    combine_coeffs(s, Zc, r, ncol, g.Nz, c->ZcT32.p);
     if (!pipe) {
         for (int y0 = 0; y0 < g.Ny; y0 += ys) {
             const int yn = std::min(ys, g.Ny - y0);
-            column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p, c->tune_tf & 4);
+            column_combine(s, c->T32.p, c->ZcT32.p, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, c->Rsl.p,
+                           c->tune_tf & 4);
             c->sp32.zlines(c->Rsl.p, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, s, c->tune_lb, disc);
         }
         return;
@@ -942,7 +948,7 @@ void spectral_tables(wt_ctx* c, const float* Zc, int r, cudaStream_t s) {
         const int yn = std::min(ys, g.Ny - y0), bi = k & 1;
         float* R = c->Rsl.p + bi * se;
         if (k >= 2) WT_CUDA(cudaStreamWaitEvent(s, c->ev_tz[bi], 0));
-        column_combine(s, c->T32.p, Zc, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, R, c->tune_tf & 4);
+        column_combine(s, c->T32.p, c->ZcT32.p, r, ncol, g.Nz, nxy, (size_t)y0 * g.Nx, g.Nx * yn, R, c->tune_tf & 4);
         WT_CUDA(cudaEventRecord(c->ev_tc[bi], s));
         WT_CUDA(cudaStreamWaitEvent(c->s_aux, c->ev_tc[bi], 0));
         c->sp32.zlines(R, r, y0, yn, c->E32.p, npts, (size_t)32 * npts, c->s_aux, c->tune_lb, disc);
@@ -972,7 +978,7 @@ void basis_fields32(wt_ctx* c, const double* Ub, int r, cudaStream_t s, int mode
     if (timing) WT_CUDA(cudaEventRecord(c->ev[1], s));
     if (use_tables(c, mode)) {
         spectral_tables(c, c->Zc32.p, r, s);
-        *launches += 2 * ((g.Ny + c->tune_ys - 1) / c->tune_ys);
+        *launches += 1 + 2 * ((g.Ny + c->tune_ys - 1) / c->tune_ys);
     } else {
         for (int m0 = 0; m0 < r; m0 += nb) {
             const int b = std::min(nb, r - m0);
