@@ -46,6 +46,8 @@ WORKLOADS = {
             "(profiling case: the spectral kernels at c2 sizes and rank, about 7 GB on the device)",
     "prof256": "prof256: the 3x3 pixel cell at grid 96x96x192 (c4's geometry) with 256 time samples, extension "
                "only (profiling case: the expansion at the 5x5 cell's time count, H 5.4 GB)",
+    "prof5": "prof5: the 5x5 pixel cell (50 columns, 275x275x500 um) at grid 96x96x192 with 64 sources per "
+             "column and 64 time samples (profiling case: the 50-column table path, about 4 GB on the device)",
     "prof_eq1": "prof_eq1: the 3x3 pixel cell at grid 96x96x192 (c4's geometry) with 256 time samples, Eq. 1 "
                 "from the rank-r form against 2e4 drift tracks of 200 steps (the 5x5 cell's track recipe) "
                 "(profiling case: basis fields 0.68 GB)",
@@ -73,6 +75,13 @@ def make_workload(name):
     if name == "prof256":
         from dataclasses import replace
         return replace(W.workload("c4", n_tracks=1), tracks=None)
+    if name == "prof5":
+        import numpy as np
+        from workloads import configs as WC
+        grid, cols = WC.pixel_matrix(5, 55 * WC.UM, 500 * WC.UM, 96, 192, 6 * WC.UM, 0.1 * WC.OHM_CM,
+                                     1.0 * WC.OHM_CM, 64, np.random.default_rng(5))
+        return WC.Workload("prof5", grid, cols, WC.FitSpec(), W.log_times(64), seed=5,
+                           notes="5x5 pixels at grid 96x96x192, 64 sources per column")
     if name == "prof_eq1":
         import numpy as np
         from dataclasses import replace

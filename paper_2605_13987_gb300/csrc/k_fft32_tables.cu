@@ -38,6 +38,7 @@ __global__ void combine_coeffs_kernel(const float* __restrict__ Zc, int r, int n
 
 constexpr int kCombineCC = 8;      // columns per asynchronous copy group
 constexpr int kCombineStages = 3;  // copy groups in flight
+constexpr int kCombineMinBlocks = 5;   // resident blocks per SM the register budget allows
 
 // One block of 128 threads per (line chunk, k_z, component); each thread takes VEC
 // consecutive lines and accumulates RB basis vectors in registers.  A thread's table values
@@ -48,7 +49,7 @@ constexpr int kCombineStages = 3;  // copy groups in flight
 // T: [n_cols][3][Nz][nxy] (plane layout [y][x]); ZcT: [Nz][n_cols][32];
 // R: [r][3][Nz][nl], line j of the slab = line off + j of the plane.
 template <int RB, int VEC>
-__global__ void __launch_bounds__(128) column_combine_kernel(const float* __restrict__ T,
+__global__ void __launch_bounds__(128, kCombineMinBlocks) column_combine_kernel(const float* __restrict__ T,
                                                              const float* __restrict__ ZcT, int r, int n_cols,
                                                              int Nz, size_t nxy, size_t off, int nl,
                                                              float* __restrict__ R) {
@@ -99,11 +100,11 @@ __global__ void __launch_bounds__(128) column_combine_kernel(const float* __rest
         asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");   // group g has landed
         if (!act) continue;
         const V* tg = ts + (size_t)(g % NS) * CC * 128 + threadIdx.x;
-        const int c1 = min(n_cols, (g + 1) * CC);
-        for (int c = g * CC; c < c1; ++c) {
-            const V q = tg[(c - g * CC) * 128];
+        const float* zg = zs + g * CC * RB;
+        // one column: RB x VEC FMAs from one table vector and RB broadcast coefficients
+        auto column = [&](const V q, const float* zc) {
             const float* t = reinterpret_cast<const float*>(&q);
-            const float4* z4 = reinterpret_cast<const float4*>(zs + c * RB);
+            const float4* z4 = reinterpret_cast<const float4*>(zc);
 #pragma unroll
             for (int b4 = 0; b4 < RB / 4; ++b4) {
                 const float4 z = z4[b4];
@@ -113,6 +114,12 @@ __global__ void __launch_bounds__(128) column_combine_kernel(const float* __rest
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) acc[4 * b4 + i][v] = fmaf(zz[i], t[v], acc[4 * b4 + i][v]);
             }
+        };
+        if ((g + 1) * CC <= n_cols) {
+#pragma unroll
+            for (int cc = 0; cc < CC; ++cc) column(tg[cc * 128], zg + cc * RB);   // a full group, unrolled
+        } else {
+            for (int cc = 0; cc < n_cols - g * CC; ++cc) column(tg[cc * 128], zg + cc * RB);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
