@@ -631,6 +631,7 @@ __global__ void __launch_bounds__(256) osj_round_kernel(double* __restrict__ A, 
         ap[k] = c * x - sn * y;
         aq[k] = sn * x + c * y;
     }
+    if (!V) return;                               // rotations not accumulated
     double* vp = V + (size_t)p * ldv;
     double* vq = V + (size_t)q * ldv;
     for (int k = threadIdx.x; k < m_real; k += blockDim.x) {
@@ -660,8 +661,10 @@ __global__ void __launch_bounds__(256) row_norms_kernel(const double* __restrict
 int onesided_jacobi_rows(cudaStream_t s, double* A, int m, int n, int lda, double* V, double* sigma, int* d_err,
                          int max_sweeps, double* coupling_out) {
     const int mp = m + (m & 1);                  // even circle; an odd m has one idle row per round
-    eye_kernel<<<((size_t)m * m + 255) / 256, 256, 0, s>>>(V, m, m);
-    WT_LAUNCH("eye");
+    if (V) {                                     // V = NULL: the rotations are not accumulated
+        eye_kernel<<<((size_t)m * m + 255) / 256, 256, 0, s>>>(V, m, m);
+        WT_LAUNCH("eye");
+    }
     DBuf<unsigned long long> cnt;
     cnt.alloc(2);                                // rotations, largest relative coupling (its bits)
     constexpr double kAcceptCoupling = 1e-10;
@@ -708,6 +711,158 @@ int onesided_jacobi_rows(cudaStream_t s, double* A, int m, int n, int lda, doubl
     }
     WT_CUDA(cudaStreamSynchronize(s));
     return sweeps;
+}
+
+// ------------------------------------------------------------------------
+// Householder QR with column pivoting of a tall matrix whose columns are the rows of a
+// row-major array (column j = M + j ld, ns entries; ns >= nt columns): M P = Q1 R.  Only R is
+// kept (the reflectors are not needed afterwards).  Step k: the column of largest remaining
+// norm is swapped into place and its reflector formed (one block), then every trailing column
+// takes the reflector and recomputes its remaining norm exactly (one block per column), so no
+// norm downdating can go stale.
+
+// sum over the block (blockDim.x a multiple of 32, at most 1024); every thread gets the result
+__device__ double qr_block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = l < nw ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (l == 0) sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+__global__ void __launch_bounds__(256) qrcp_norms_kernel(const double* __restrict__ M, int ns, int ld,
+                                                         double* __restrict__ nrm) {
+    __shared__ double sh[33];
+    const double* a = M + (size_t)blockIdx.x * ld;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) ss = fma(a[i], a[i], ss);
+    ss = qr_block_sum(ss, sh);
+    if (threadIdx.x == 0) nrm[blockIdx.x] = ss;
+}
+
+// pivot (largest remaining squared norm, the lowest index among equals), swap, reflector
+// v = x - beta e_k with beta = -sign(x_k) ||x||, tau = 2 / v.v; column k becomes beta e_k
+__global__ void __launch_bounds__(512) qrcp_pivot_kernel(double* __restrict__ M, int ns, int nt, int ld, int k,
+                                                         double* __restrict__ nrm, int* __restrict__ piv,
+                                                         double* __restrict__ v, double* __restrict__ tau) {
+    __shared__ double sh[33];
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    __shared__ int sp;
+    double best = -1.0;
+    int bj = nt;
+    for (int j = k + threadIdx.x; j < nt; j += blockDim.x)
+        if (nrm[j] > best) { best = nrm[j]; bj = j; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { bv[w] = best; bi[w] = bj; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = bv[0];
+        int j = bi[0];
+        for (int q = 1; q < nw; ++q)
+            if (bv[q] > b || (bv[q] == b && bi[q] < j)) { b = bv[q]; j = bi[q]; }
+        sp = (j < nt) ? j : k;
+    }
+    __syncthreads();
+    const int p = sp;
+    double* x = M + (size_t)k * ld;
+    if (p != k) {
+        double* y = M + (size_t)p * ld;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            const double t = x[i];
+            x[i] = y[i];
+            y[i] = t;
+        }
+        if (threadIdx.x == 0) {
+            const double t = nrm[k];
+            nrm[k] = nrm[p];
+            nrm[p] = t;
+            const int q = piv[k];
+            piv[k] = piv[p];
+            piv[p] = q;
+        }
+    }
+    __syncthreads();
+    double ss = 0.0;
+    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) ss = fma(x[i], x[i], ss);
+    ss = qr_block_sum(ss, sh);
+    const double x0 = x[k];
+    const double alpha = sqrt(ss);
+    const double beta = alpha > 0.0 ? -copysign(alpha, x0) : 0.0;
+    const double vn = 2.0 * alpha * (alpha + fabs(x0));          // (x - beta e_k).(x - beta e_k)
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) v[i] = i < k ? 0.0 : (i == k ? x0 - beta : x[i]);
+    __syncthreads();
+    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) x[i] = i == k ? beta : 0.0;
+    if (threadIdx.x == 0) {
+        *tau = vn > 0.0 ? 2.0 / vn : 0.0;
+        nrm[k] = 0.0;
+    }
+}
+
+// columns j > k: a -= tau (v.a) v, then their squared norms below row k
+__global__ void __launch_bounds__(256) qrcp_apply_kernel(double* __restrict__ M, int ns, int ld, int k,
+                                                         const double* __restrict__ v, const double* __restrict__ tau,
+                                                         double* __restrict__ nrm) {
+    __shared__ double sh[33];
+    const int j = k + 1 + blockIdx.x;
+    double* a = M + (size_t)j * ld;
+    double d = 0.0;
+    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) d = fma(v[i], a[i], d);
+    d = qr_block_sum(d, sh);
+    const double t = *tau * d;
+    double ss = 0.0;
+    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) {
+        const double y = fma(-t, v[i], a[i]);
+        a[i] = y;
+        if (i > k) ss = fma(y, y, ss);
+    }
+    ss = qr_block_sum(ss, sh);
+    if (threadIdx.x == 0) nrm[j] = ss;
+}
+
+// R[i][j] = M[j][i] for i, j < nt (upper triangular after the factorisation)
+__global__ void qrcp_extract_kernel(const double* __restrict__ M, int nt, int ld, double* __restrict__ R) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)nt * nt) return;
+    const int i = (int)(e / nt), j = (int)(e % nt);
+    R[e] = i <= j ? M[(size_t)j * ld + i] : 0.0;
+}
+
+void qrcp_r(cudaStream_t s, double* M, int ns, int nt, int ld, double* R, int* piv) {
+    if (nt < 1) return;
+    if (ns < nt) fail(WT_ERR_ARG, "column-pivoted QR: needs at least as many rows as columns");
+    DBuf<double> v, nrm, tau;
+    v.alloc(ns);
+    nrm.alloc(nt);
+    tau.alloc(1);
+    std::vector<int> h(nt);
+    for (int j = 0; j < nt; ++j) h[j] = j;
+    WT_CUDA(cudaMemcpyAsync(piv, h.data(), nt * sizeof(int), cudaMemcpyHostToDevice, s));
+    qrcp_norms_kernel<<<nt, 256, 0, s>>>(M, ns, ld, nrm.p);
+    WT_LAUNCH("qrcp norms");
+    for (int k = 0; k < nt; ++k) {
+        qrcp_pivot_kernel<<<1, 512, 0, s>>>(M, ns, nt, ld, k, nrm.p, piv, v.p, tau.p);
+        if (k + 1 < nt) qrcp_apply_kernel<<<nt - k - 1, 256, 0, s>>>(M, ns, ld, k, v.p, tau.p, nrm.p);
+    }
+    WT_LAUNCH("qrcp steps");
+    qrcp_extract_kernel<<<(unsigned)(((size_t)nt * nt + 255) / 256), 256, 0, s>>>(M, nt, ld, R);
+    WT_LAUNCH("qrcp extract");
+    WT_CUDA(cudaStreamSynchronize(s));      // the host pivot array and the work buffers go out of scope
 }
 
 __global__ void gather_rows_scaled_kernel(const double* __restrict__ A, int n, int lda, const int* __restrict__ idx,

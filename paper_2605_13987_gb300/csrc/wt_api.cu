@@ -604,9 +604,14 @@ void charges_at(wt_ctx* c, const double* d_t, int nt, double* Q) {
 }
 
 // Time basis of a charge history Q [ns][nt] for the FP32 path: the singular
-// value decomposition Q = sum_i sigma_i u_i v_i^T by one-sided Jacobi on the
-// rows of Q^T (no Gram matrix: the small singular values keep their relative
-// accuracy), then the smallest rank r <= 32 whose truncation error in every
+// value decomposition Q = sum_i sigma_i u_i v_i^T by one-sided Jacobi (no Gram
+// matrix: the small singular values keep their relative accuracy).  When
+// ns >= nt the Jacobi runs on the rows of R from a column-pivoted QR,
+// Q P = Q1 R (Drmac and Veselic's preconditioning: rows of length nt instead
+// of ns, and a few sweeps instead of twenty for the nearly parallel samples of
+// a relaxation): rotated to orthogonal rows S_k = sigma_k w_k^T, R's rows give
+// v_k[P_i] = w_k[i], and u_k = Q v_k / sigma_k.  Otherwise it runs on the rows
+// of Q^T directly.  Then the smallest rank r <= 32 whose truncation error in every
 // time sample, ||q(t_n) - sum_{i<r} sigma_i u_i v_i[n]|| / ||q(t_n)||, is at
 // most kTruncTarget (the FP32 rounding level).  The error is exact from the
 // decomposition: the squared tail sum_{i>=r} (sigma_i v_i[n])^2, summed from
@@ -622,14 +627,24 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
                       double& trunc_out) {
     cudaStream_t s = c->s;
     const int ns = c->ns;
-    DBuf<double> A, V, sig;
+    const bool pre = ns >= nt;                    // column-pivoted QR first
+    DBuf<double> A, V, sig, Rm;
+    DBuf<int> dpiv;
     A.alloc((size_t)nt * ns);
-    transpose(s, Q, ns, nt, A.p);                 // rows = time samples
-    V.alloc((size_t)nt * nt);
+    transpose(s, Q, ns, nt, A.p);                 // rows = time samples (the columns of Q)
     sig.alloc(nt);
+    if (pre) {
+        Rm.alloc((size_t)nt * nt);
+        dpiv.alloc(nt);
+        qrcp_r(s, A.p, ns, nt, ns, Rm.p, dpiv.p);
+        A.release();
+    } else {
+        V.alloc((size_t)nt * nt);
+    }
     clear_err(c);
     double coupling = 0.0;
-    const int sweeps = onesided_jacobi_rows(s, A.p, nt, ns, ns, V.p, sig.p, c->d_err.p, 40, &coupling);
+    const int sweeps = pre ? onesided_jacobi_rows(s, Rm.p, nt, nt, nt, nullptr, sig.p, c->d_err.p, 40, &coupling)
+                           : onesided_jacobi_rows(s, A.p, nt, ns, ns, V.p, sig.p, c->d_err.p, 40, &coupling);
     if (read_err(c)) {
         char msg[160];
         std::snprintf(msg, sizeof msg,
@@ -639,8 +654,21 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
     }
     std::vector<double> hs(nt), hv((size_t)nt * nt);
     sig.download(hs.data(), nt, s);
-    V.download(hv.data(), (size_t)nt * nt, s);
-    WT_CUDA(cudaStreamSynchronize(s));
+    if (pre) {
+        // hv[k][P_i] = S[k][i] / sigma_k: the coefficient of u_k in sample P_i over sigma_k
+        std::vector<double> hS((size_t)nt * nt);
+        std::vector<int> hp(nt);
+        Rm.download(hS.data(), hS.size(), s);
+        dpiv.download(hp.data(), nt, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < nt; ++k) {
+            const double inv = hs[k] > 0.0 ? 1.0 / hs[k] : 0.0;
+            for (int i = 0; i < nt; ++i) hv[(size_t)k * nt + hp[i]] = hS[(size_t)k * nt + i] * inv;
+        }
+    } else {
+        V.download(hv.data(), (size_t)nt * nt, s);
+        WT_CUDA(cudaStreamSynchronize(s));
+    }
     std::vector<int> ord(nt);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hs[a] > hs[b]; });
@@ -683,10 +711,21 @@ void compress_history(wt_ctx* c, const double* Q, int nt, DBuf<double>& Ub, DBuf
     }
     DBuf<int> didx;
     DBuf<double> dscale, dcoef;
-    didx.upload(idx.data(), r, s);
-    dscale.upload(scale.data(), r, s);
     Ub.alloc((size_t)r * ns);
-    gather_rows_scaled(s, A.p, ns, ns, didx.p, dscale.p, r, Ub.p);
+    if (pre) {
+        // u_m = Q v_m / sigma_m: Ub [r][ns] = (V_r / sigma) Q^T
+        std::vector<double> vr((size_t)r * nt);
+        for (int m = 0; m < r; ++m)
+            for (int n = 0; n < nt; ++n) vr[(size_t)m * nt + n] = hv[(size_t)idx[m] * nt + n] * scale[m];
+        DBuf<double> dvr;
+        dvr.upload(vr.data(), vr.size(), s);
+        dgemm(s, false, true, r, ns, nt, 1.0, dvr.p, nt, Q, nt, 0.0, Ub.p, ns);
+        WT_CUDA(cudaStreamSynchronize(s));
+    } else {
+        didx.upload(idx.data(), r, s);
+        dscale.upload(scale.data(), r, s);
+        gather_rows_scaled(s, A.p, ns, ns, didx.p, dscale.p, r, Ub.p);
+    }
     dcoef.upload(coef.data(), coef.size(), s);
     W32.alloc(coef.size());
     to_float(s, dcoef.p, coef.size(), 1.0, W32.p);

@@ -141,11 +141,15 @@ void sym_eig(cudaStream_t s, double* A, int n, double* w, double* V, int* d_err)
 // Singular value decomposition of the rows of A [m][n] (row-major, destroyed)
 // by one-sided (Hestenes) Jacobi: on return the rows of A are mutually
 // orthogonal (row i = sigma_i u_i^T), V [m][m] holds the accumulated rotations
-// (A_in = V^T A_out) and sigma[m] the row norms (unsorted).  Returns the number
+// (A_in = V^T A_out; V = NULL: not accumulated) and sigma[m] the row norms (unsorted).  Returns the number
 // of sweeps; sets d_err (DERR_TIMEOUT) when max_sweeps do not converge (unless the largest
 // relative coupling still rotated in the last sweep is below 1e-10; coupling_out returns it).
 int onesided_jacobi_rows(cudaStream_t s, double* A, int m, int n, int lda, double* V, double* sigma, int* d_err,
                          int max_sweeps = 40, double* coupling_out = nullptr);
+// Householder QR with column pivoting, M P = Q1 R, of the ns x nt matrix whose column j is row j of
+// the row-major array M [nt][ld] (ns >= nt; M is destroyed): R [nt][nt] row-major upper triangular,
+// piv[i] (device) = the column of M that became column i.  Only R and P are formed.
+void qrcp_r(cudaStream_t s, double* M, int ns, int nt, int ld, double* R, int* piv);
 // out[r][n] = scale[r] * A[idx[r]][:]  (idx, scale: device arrays of `rows`)
 void gather_rows_scaled(cudaStream_t s, const double* A, int n, int lda, const int* idx, const double* scale,
                         int rows, double* out);
