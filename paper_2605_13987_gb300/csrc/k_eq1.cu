@@ -66,7 +66,8 @@ __device__ __forceinline__ void eq1_increments(const float* __restrict__ f, int 
 
 // T: field type; L: lag table entry; TO: current type
 template <class T, class L, class TO>
-__global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int Nx, int Ny, int Nz, int nt,
+// nu: time samples the lag table reads (samples n >= nu are never staged)
+__global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int Nx, int Ny, int Nz, int nt, int nu,
                                                   T inv_hx, T inv_hy, T inv_hz,
                                                   const float* __restrict__ X, const float* __restrict__ Y,
                                                   const float* __restrict__ Z, const float* __restrict__ VX,
@@ -83,8 +84,8 @@ __global__ void __launch_bounds__(256) eq1_kernel(const T* __restrict__ H, int N
     for (int c0 = 0; c0 < n_steps; c0 += EQ1_MC) {
         const int mc = min(EQ1_MC, n_steps - c0);
         __syncthreads();
-        for (int e = threadIdx.x; e < mc * nt; e += blockDim.x) {
-            const int j = e / nt, n = e % nt;
+        for (int e = threadIdx.x; e < mc * nu; e += blockDim.x) {
+            const int j = e / nu, n = e % nu;
             const size_t s = (size_t)tr * n_steps + c0 + j;
             const T vx = VX[s], vy = VY[s], vz = VZ[s];
             T acc = 0;
@@ -145,11 +146,12 @@ template <class T, class L, class TO>
 static void eq1_launch_t(cudaStream_t s, const T* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                          const float* x, const float* y, const float* z, const float* vx, const float* vy,
                          const float* vz, const float* q, float qconst, int n_tracks, int n_steps, int n_out,
-                         double dt, double v_w, const void* lags, TO* out) {
+                         double dt, double v_w, const void* lags, int nu, TO* out) {
+    if (nu < 1 || nu > nt) fail(WT_ERR_ARG, "eq1: bad count of time samples in use");
     size_t sh = (((size_t)EQ1_MC * nt * sizeof(T) + 15) & ~(size_t)15) + (size_t)n_out * sizeof(double);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
     allow_dyn_smem(eq1_kernel<T, L, TO>, sh);
-    eq1_kernel<T, L, TO><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y,
+    eq1_kernel<T, L, TO><<<n_tracks, 256, sh, s>>>(H, Nx, Ny, Nz, nt, nu, (T)(Nx / Lx), (T)(Ny / Ly), (T)(Nz / Lz), x, y,
                                                    z, vx, vy, vz, q, qconst, n_steps, n_out, dt, 1.0 / v_w,
                                                    static_cast<const L*>(lags), out);
     WT_LAUNCH("eq1");
@@ -157,17 +159,17 @@ static void eq1_launch_t(cudaStream_t s, const T* H, int Nx, int Ny, int Nz, int
 void eq1_launch(cudaStream_t s, const float* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                 const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
                 const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
-                const void* lags, float* out) {
+                const void* lags, int nu, float* out) {
     eq1_launch_t<float, Eq1Lag, float>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks,
-                                       n_steps, n_out, dt, v_w, lags, out);
+                                       n_steps, n_out, dt, v_w, lags, nu, out);
 }
 // FP64 field (plain path): interpolation, time weights and currents in FP64 (lags: FP64 table).
 void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int nt, double Lx, double Ly, double Lz,
                   const float* x, const float* y, const float* z, const float* vx, const float* vy, const float* vz,
                   const float* q, float qconst, int n_tracks, int n_steps, int n_out, double dt, double v_w,
-                  const void* lags, double* out) {
+                  const void* lags, int nu, double* out) {
     eq1_launch_t<double, Eq1Lag64, double>(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst,
-                                           n_tracks, n_steps, n_out, dt, v_w, lags, out);
+                                           n_tracks, n_steps, n_out, dt, v_w, lags, nu, out);
 }
 // Eq. 1 straight from the rank-r form of the FP32 field, H[t][c][p] = sum_m W[t][m] E[c][m][p]
 // (the representation the tensor-core expansion writes out): the staged dot products are
@@ -179,7 +181,8 @@ void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int n
 // one 128-byte line, and the two z neighbours of a corner are adjacent lines.
 __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict__ Ep, int r,
                                                         const float* __restrict__ W32, int Nx, int Ny, int Nz,
-                                                        int nt, float inv_hx, float inv_hy, float inv_hz,
+                                                        int nt, int nu, float inv_hx, float inv_hy,
+                                                        float inv_hz,
                                                         const float* __restrict__ X, const float* __restrict__ Y,
                                                         const float* __restrict__ Z, const float* __restrict__ VX,
                                                         const float* __restrict__ VY, const float* __restrict__ VZ,
@@ -188,15 +191,16 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
                                                         const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* sv = reinterpret_cast<float*>(smem_raw);                          // [32][EQ1_MC] (basis-major)
-    float* Wt = sv + 32 * EQ1_MC;                                            // [r][nt]
-    float* f = Wt + (size_t)r * nt;                                          // [EQ1_MC][nt]
-    double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * nt + EQ1_MC * 32 + (size_t)EQ1_MC * nt) *
+    float* Wt = sv + 32 * EQ1_MC;                                            // [r][ldw]
+    const int nq = (nu + 3) >> 2, ldw = 4 * nq;                              // Wt row: nu samples, zero-padded
+    float* f = Wt + (size_t)r * ldw;                                         // [EQ1_MC][nt]
+    double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nt) *
                                                         sizeof(float) + 15) & ~(size_t)15));   // [n_out]
     const int tr = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int e = threadIdx.x; e < r * nt; e += blockDim.x) {
-        const int m = e / nt, n = e - m * nt;
-        Wt[e] = W32[(size_t)n * 32 + m];
+    for (int e = threadIdx.x; e < r * ldw; e += blockDim.x) {
+        const int m = e / ldw, n = e - m * ldw;
+        Wt[e] = n < nu ? W32[(size_t)n * 32 + m] : 0.f;
     }
     for (int m = threadIdx.x; m < n_out; m += blockDim.x) Q[m] = 0.0;
     for (int c0 = 0; c0 < n_steps; c0 += EQ1_MC) {
@@ -237,17 +241,17 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
         __syncthreads();
         // f[j][n] = sum_m W[t_n][m] sv[m][j]: four time samples (nq apart, so that a warp reads
         // consecutive words of Wt) by four steps per thread
-        const int nq = (nt + 3) >> 2, ng = (mc + 3) >> 2;
+        const int ng = (mc + 3) >> 2;
         for (int e = threadIdx.x; e < nq * ng; e += blockDim.x) {
             const int n0 = e % nq, j0 = 4 * (e / nq);
             float acc[4][4] = {};
             for (int m = 0; m < r; ++m) {
                 const float4 s4 = *reinterpret_cast<const float4*>(sv + m * EQ1_MC + j0);
-                const float* wr = Wt + (size_t)m * nt;
+                const float* wr = Wt + (size_t)m * ldw;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int n = n0 + i * nq;
-                    const float wv = n < nt ? wr[n] : 0.f;
+                    const float wv = wr[n];
                     acc[i][0] = fmaf(wv, s4.x, acc[i][0]);
                     acc[i][1] = fmaf(wv, s4.y, acc[i][1]);
                     acc[i][2] = fmaf(wv, s4.z, acc[i][2]);
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int n = n0 + i * nq;
-                if (n >= nt) continue;
+                if (n >= nu) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (j0 + q < mc) f[(j0 + q) * nt + n] = acc[i][q];
@@ -309,14 +313,16 @@ void eq1_point_major(cudaStream_t s, const float* E, int r, size_t npts, float* 
 void eq1_basis_launch(cudaStream_t s, const float* Ep, int r, const float* W32, int Nx, int Ny, int Nz, int nt,
                       double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
                       const float* vx, const float* vy, const float* vz, const float* q, float qconst, int n_tracks,
-                      int n_steps, int n_out, double dt, double v_w, const void* lags, float* out) {
+                      int n_steps, int n_out, double dt, double v_w, const void* lags, int nu, float* out) {
     if (r < 1 || r > 32) fail(WT_ERR_ARG, "eq1: basis rank out of range");
-    const size_t sh = ((((size_t)r * nt + EQ1_MC * 32 + (size_t)EQ1_MC * nt) * sizeof(float) + 15) & ~(size_t)15) +
+    if (nu < 1 || nu > nt) fail(WT_ERR_ARG, "eq1: bad count of time samples in use");
+    const size_t ldw = 4 * (size_t)((nu + 3) / 4);
+    const size_t sh = ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nt) * sizeof(float) + 15) & ~(size_t)15) +
                       (size_t)n_out * sizeof(double);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
     allow_dyn_smem(eq1_basis_kernel, sh);
     if (n_tracks > 0)
-        eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(Ep, r, W32, Nx, Ny, Nz, nt, (float)(Nx / Lx), (float)(Ny / Ly),
+        eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(Ep, r, W32, Nx, Ny, Nz, nt, nu, (float)(Nx / Lx), (float)(Ny / Ly),
                                                    (float)(Nz / Lz), x, y, z, vx, vy, vz, q, qconst, n_steps, n_out,
                                                    dt, 1.0 / v_w, static_cast<const Eq1Lag*>(lags), out);
     WT_LAUNCH("eq1_basis");
@@ -403,7 +409,7 @@ unsigned long long current_context_id() {
 void eq1_noalloc_launch(cudaStream_t s, int device, const float* H, int Nx, int Ny, int Nz, const double* d_times,
                         int nt, double Lx, double Ly, double Lz, const float* x, const float* y, const float* z,
                         const float* vx, const float* vy, const float* vz, const float* q, float qconst,
-                        int n_tracks, int n_steps, int n_out, double dt, double v_w, float* out) {
+                        int n_tracks, int n_steps, int n_out, double dt, double v_w, int nu, float* out) {
     if (n_out > kEq1NoAllocMaxOut)
         fail(WT_ERR_ARG, "n_out " + std::to_string(n_out) + " exceeds the allocation-free limit of " +
                              std::to_string(kEq1NoAllocMaxOut));
@@ -428,7 +434,7 @@ void eq1_noalloc_launch(cudaStream_t s, int device, const float* H, int Nx, int 
     eq1_lag_table_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(d_times, nt, dt, n_out, lags);
     WT_LAUNCH("eq1_lag_table");
     eq1_launch(s, H, Nx, Ny, Nz, nt, Lx, Ly, Lz, x, y, z, vx, vy, vz, q, qconst, n_tracks, n_steps, n_out, dt, v_w,
-               lags, out);
+               lags, nu, out);
 }
 
 }  // namespace wt
