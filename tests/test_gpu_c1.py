@@ -11,7 +11,7 @@ from tests.gpu_common import rel_l2, device_tracks
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10      # FP64 plain path and FP64 setup stages
-TOL32 = 1e-5       # FP32 fast path (spec bound)
+TOL32 = 1e-5       # FP32 fast path: the accuracy target of the FP32 field against the FP64 oracle
 
 
 @pytest.fixture(scope="module")
