@@ -40,9 +40,11 @@ constexpr int EQ1_MC = 16;   // track steps per chunk
 __device__ __forceinline__ float eq1_interp(const float* __restrict__ fj, int nt, Eq1Lag lg) {
     return fmaf(lg.w0, fj[lg.n], lg.w1 * fj[min(lg.n + 1, nt - 1)]);
 }
+// f: [mc][nt] (nt: the row stride, also the clamp of sample n + 1); outputs m < c0 take nothing
+// from this chunk, so the threads start at c0.
 __device__ __forceinline__ void eq1_increments(const float* __restrict__ f, int nt, int mc, int c0, int n_out,
                                                const Eq1Lag* __restrict__ lags, double* __restrict__ D) {
-    for (int m = threadIdx.x; m < n_out; m += blockDim.x) {
+    for (int m = c0 + threadIdx.x; m < n_out; m += blockDim.x) {
         const int jmax = min(mc - 1, m - c0);
         if (jmax < 0) continue;
         // step j sees lag L = m - c0 - j; the entry of lag L - 1 is the next step's entry of lag L
@@ -179,6 +181,39 @@ void eq1_launch64(cudaStream_t s, const double* H, int Nx, int Ny, int Nz, int n
 // as in eq1_kernel.  The basis fields are read point-major, Ep[p][c][32] (eq1_point_major): one
 // warp per track step, a lane per basis field, so that each of the 24 corner-component reads is
 // one 128-byte line, and the two z neighbours of a corner are adjacent lines.
+// f[j][n] = sum_m W[t_n][m] sv[m][j] for n < nu, j < mc: NB time samples (nq apart, so that a warp
+// reads consecutive words of Wt) by four steps per thread; Wt rows hold NB nq >= nu samples, the
+// ones past nu zero.
+template <int NB>
+__device__ __forceinline__ void eq1_stage_product(const float* __restrict__ sv, const float* __restrict__ Wt, int r,
+                                                  int nq, int nu, int mc, float* __restrict__ f) {
+    const int ng = (mc + 3) >> 2, ldw = NB * nq;
+    for (int e = threadIdx.x; e < nq * ng; e += blockDim.x) {
+        const int n0 = e % nq, j0 = 4 * (e / nq);
+        float acc[NB][4] = {};
+        for (int m = 0; m < r; ++m) {
+            const float4 s4 = *reinterpret_cast<const float4*>(sv + m * EQ1_MC + j0);
+            const float* wr = Wt + (size_t)m * ldw + n0;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const float wv = wr[i * nq];
+                acc[i][0] = fmaf(wv, s4.x, acc[i][0]);
+                acc[i][1] = fmaf(wv, s4.y, acc[i][1]);
+                acc[i][2] = fmaf(wv, s4.z, acc[i][2]);
+                acc[i][3] = fmaf(wv, s4.w, acc[i][3]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int n = n0 + i * nq;
+            if (n >= nu) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < mc) f[(j0 + q) * nu + n] = acc[i][q];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict__ Ep, int r,
                                                         const float* __restrict__ W32, int Nx, int Ny, int Nz,
                                                         int nt, int nu, float inv_hx, float inv_hy,
@@ -187,15 +222,20 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
                                                         const float* __restrict__ Z, const float* __restrict__ VX,
                                                         const float* __restrict__ VY, const float* __restrict__ VZ,
                                                         const float* __restrict__ qtrack, float qconst, int n_steps,
-                                                        int n_out, double dt, double inv_vw,
-                                                        const Eq1Lag* __restrict__ lags, float* __restrict__ out) {
+                                                        int n_out, double dt, double inv_vw, int nb,
+                                                        bool stage_lags, const Eq1Lag* __restrict__ lags,
+                                                        float* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* sv = reinterpret_cast<float*>(smem_raw);                          // [32][EQ1_MC] (basis-major)
     float* Wt = sv + 32 * EQ1_MC;                                            // [r][ldw]
-    const int nq = (nu + 3) >> 2, ldw = 4 * nq;                              // Wt row: nu samples, zero-padded
-    float* f = Wt + (size_t)r * ldw;                                         // [EQ1_MC][nt]
-    double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nt) *
+    const int nq = (nu + nb - 1) / nb, ldw = nb * nq;                        // Wt row: nu samples, zero-padded
+    float* f = Wt + (size_t)r * ldw;                                         // [EQ1_MC][nu]
+    double* Q = reinterpret_cast<double*>(smem_raw + ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nu) *
                                                         sizeof(float) + 15) & ~(size_t)15));   // [n_out]
+    Eq1Lag* ls = reinterpret_cast<Eq1Lag*>(Q + n_out);                       // [n_out] when staged
+    if (stage_lags)
+        for (int m = threadIdx.x; m < n_out; m += blockDim.x) ls[m] = lags[m];
+    const Eq1Lag* lg = stage_lags ? ls : lags;
     const int tr = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < r * ldw; e += blockDim.x) {
@@ -239,36 +279,14 @@ __global__ void __launch_bounds__(256) eq1_basis_kernel(const float* __restrict_
             sv[lane * EQ1_MC + j] = lane < r ? acc : 0.f;
         }
         __syncthreads();
-        // f[j][n] = sum_m W[t_n][m] sv[m][j]: four time samples (nq apart, so that a warp reads
-        // consecutive words of Wt) by four steps per thread
-        const int ng = (mc + 3) >> 2;
-        for (int e = threadIdx.x; e < nq * ng; e += blockDim.x) {
-            const int n0 = e % nq, j0 = 4 * (e / nq);
-            float acc[4][4] = {};
-            for (int m = 0; m < r; ++m) {
-                const float4 s4 = *reinterpret_cast<const float4*>(sv + m * EQ1_MC + j0);
-                const float* wr = Wt + (size_t)m * ldw;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int n = n0 + i * nq;
-                    const float wv = wr[n];
-                    acc[i][0] = fmaf(wv, s4.x, acc[i][0]);
-                    acc[i][1] = fmaf(wv, s4.y, acc[i][1]);
-                    acc[i][2] = fmaf(wv, s4.z, acc[i][2]);
-                    acc[i][3] = fmaf(wv, s4.w, acc[i][3]);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int n = n0 + i * nq;
-                if (n >= nu) continue;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j0 + q < mc) f[(j0 + q) * nt + n] = acc[i][q];
-            }
+        switch (nb) {
+            case 1: eq1_stage_product<1>(sv, Wt, r, nq, nu, mc, f); break;
+            case 2: eq1_stage_product<2>(sv, Wt, r, nq, nu, mc, f); break;
+            case 3: eq1_stage_product<3>(sv, Wt, r, nq, nu, mc, f); break;
+            default: eq1_stage_product<4>(sv, Wt, r, nq, nu, mc, f); break;
         }
         __syncthreads();
-        eq1_increments(f, nt, mc, c0, n_out, lags, Q);
+        eq1_increments(f, nu, mc, c0, n_out, lg, Q);
     }
     __syncthreads();
     const float qc = qtrack ? qtrack[tr] : qconst;
@@ -316,15 +334,22 @@ void eq1_basis_launch(cudaStream_t s, const float* Ep, int r, const float* W32, 
                       int n_steps, int n_out, double dt, double v_w, const void* lags, int nu, float* out) {
     if (r < 1 || r > 32) fail(WT_ERR_ARG, "eq1: basis rank out of range");
     if (nu < 1 || nu > nt) fail(WT_ERR_ARG, "eq1: bad count of time samples in use");
-    const size_t ldw = 4 * (size_t)((nu + 3) / 4);
-    const size_t sh = ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nt) * sizeof(float) + 15) & ~(size_t)15) +
-                      (size_t)n_out * sizeof(double);
+    // time samples per thread in the staged product: the fewest that keep the (samples / nb) x
+    // (steps / 4) items within one pass of the 256 threads
+    const int nb = std::min(4, std::max(1, (nu + 63) / 64));
+    const size_t ldw = (size_t)nb * ((nu + nb - 1) / nb);
+    const size_t base = ((((size_t)r * ldw + EQ1_MC * 32 + (size_t)EQ1_MC * nu) * sizeof(float) + 15) & ~(size_t)15) +
+                        (size_t)n_out * sizeof(double);
+    // the lag table goes into shared memory beside the rest when it is small (12 B per output)
+    const bool stage_lags = (size_t)n_out * sizeof(Eq1Lag) <= 16384;
+    const size_t sh = base + (stage_lags ? (size_t)n_out * sizeof(Eq1Lag) : 0);
     if (sh > 200 * 1024) fail(WT_ERR_UNSUPPORTED, "eq1: n_t or n_out too large for shared memory");
     allow_dyn_smem(eq1_basis_kernel, sh);
     if (n_tracks > 0)
         eq1_basis_kernel<<<n_tracks, 256, sh, s>>>(Ep, r, W32, Nx, Ny, Nz, nt, nu, (float)(Nx / Lx), (float)(Ny / Ly),
                                                    (float)(Nz / Lz), x, y, z, vx, vy, vz, q, qconst, n_steps, n_out,
-                                                   dt, 1.0 / v_w, static_cast<const Eq1Lag*>(lags), out);
+                                                   dt, 1.0 / v_w, nb, stage_lags, static_cast<const Eq1Lag*>(lags),
+                                                   out);
     WT_LAUNCH("eq1_basis");
 }
 
