@@ -33,10 +33,12 @@ listed in the module docstrings:
                charge, threshold and constant-fraction crossings) and their
                sensitivities, for the geometry scans of Sec. 5.
 
-Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
-except the brute-force finite-difference model (``bruteforce``), which is a
-loose consistency check between two different discretisations (agreement to
-~4-9 % on the single cell): parity unpinned for that one comparison.
+Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``.
+The brute-force finite-difference model (``bruteforce``) is pinned in its parts
+(the Laplacian's spectrum, parallel plates, the Schur complement against its
+definition); its agreement with the spectral fit is a loose consistency check
+between two different discretisations (~4-9 % on the single cell), parity
+unpinned for that one comparison.
 """
 from . import greens, geometry, fit, relax, extend, eq1, bruteforce  # noqa: F401
 from .pipeline import solve, Solution  # noqa: F401

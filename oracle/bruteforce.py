@@ -13,7 +13,10 @@ complement (sparse LU).  The resistive lines are the same as in
 
 Against the spectral fit this model differs in discretisation (voxel
 staircase vs band-limited point sources), so only loose agreement is
-expected: parity unpinned for this comparison.
+expected: parity unpinned for this comparison.  Its parts are pinned on their
+own (tests/test_oracle_bruteforce.py): the operator's spectrum against the
+closed form, a plane-filling column against parallel plates, and the Schur
+complement against the charge of the harmonic extension solved densely.
 """
 from __future__ import annotations
 
@@ -94,6 +97,11 @@ def node_capacitance(grid, columns):
     bset = np.nonzero(node < 0)[0]
     P = sp.csr_matrix((np.ones(cset.size), (np.arange(cset.size), node[cset])), shape=(cset.size, n_nodes))
     Ccc = C[cset][:, cset]
+    if bset.size == 0:                                 # conductors fill the grid: nothing to eliminate
+        X = np.zeros((0, n_nodes))
+        Cn = P.T @ (Ccc @ P).toarray()
+        Cn = 0.5 * (Cn + Cn.T)
+        return np.asarray(Cn), {"X": X, "bset": bset, "cset": cset, "node": node}
     Ccb = C[cset][:, bset]
     Cbb = C[bset][:, bset].tocsc()
     Cbc_P = (C[bset][:, cset] @ P).toarray()
