@@ -119,3 +119,35 @@ def test_noalloc_eq1_rejects_what_it_cannot_do_without_allocating(torch, sensor)
     code = B.load_library().wt_eq1_noalloc(sen.ctx, B._ptr(host_H), C.byref(tr_s), B._ptr(out),
                                            B._stream_handle(None))
     assert code == B.WT_ERR_ARG
+
+
+def test_noalloc_eq1_replays_from_a_captured_graph(torch, sensor):
+    """After a first call (which looks up the scratch address), wt_eq1_noalloc can be captured
+    into a CUDA graph: a replay gives wt_eq1's currents bit for bit, and a replay after the track
+    arrays were rewritten in place follows the new tracks."""
+    import paper_2605_13987_gb300 as P
+    w, sen, H = sensor
+    tr = W.configs.mip_tracks(w.grid, 12, 24, np.random.default_rng(21))
+    tr.n_out = 50
+    td = device_tracks(tr, torch)
+    out = torch.zeros((tr.n_tracks, tr.n_out), dtype=torch.float32, device="cuda")
+    P.wt_eq1_noalloc(sen.ctx, H, td, out)            # the first call resolves the scratch address
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=s):
+        P.wt_eq1_noalloc(sen.ctx, H, td, out)
+    torch.cuda.synchronize()
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    ref = sen.eq1(H, td)
+    assert torch.equal(out, ref)
+    tr2 = W.configs.mip_tracks(w.grid, 12, 24, np.random.default_rng(22))
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        td[k].copy_(torch.tensor(np.ascontiguousarray(getattr(tr2, k)), dtype=torch.float32, device="cuda"))
+    g.replay()
+    torch.cuda.synchronize()
+    ref2 = sen.eq1(H, td)
+    assert torch.equal(out, ref2) and not torch.equal(ref, ref2)
