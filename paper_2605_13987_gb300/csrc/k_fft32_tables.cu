@@ -17,7 +17,9 @@
 // the lateral transform.  The tables are built once per context with the
 // deposit and plane kernels (a unit z-transform per column); an extension then
 // needs this combination and the z pass only.  The combination runs over
-// slabs of y rows so that the slab's planes stay in L2 for the z pass.
+// slabs of y rows (the autotuner picks their height): a small slab's planes
+// stay in L2 for the z pass; larger ones go through DRAM but take fewer,
+// longer launches.
 #include "k_fft32_common.cuh"
 
 #include <type_traits>
