@@ -30,7 +30,8 @@ def null_basis(n):
 
 
 def fit(P, S, tikhonov=0.0, want_cond=False):
-    """Return dict with F (Ns x Ns), offsets (Ns), Cn, and diagnostics."""
+    """Return dict with F (sources x nodes), offsets (nodes), Cn (when sources and nodes coincide),
+    and diagnostics."""
     nc, ns = P.shape
     B = null_basis(ns)
     A = np.hstack([P @ B, np.ones((nc, 1))])
@@ -45,8 +46,10 @@ def fit(P, S, tikhonov=0.0, want_cond=False):
     QtR, R = sla.qr_multiply(A, rhs.T, mode="right", overwrite_a=True)
     X = sla.solve_triangular(R, QtR.T, lower=False)
     F = B @ X[:ns - 1]
-    out = {"F": F, "offset": X[ns - 1], "Cn": 0.5 * (F + F.T), "B": B}
-    out["asymmetry"] = np.linalg.norm(F - F.T) / np.linalg.norm(F)
+    out = {"F": F, "offset": X[ns - 1], "B": B}
+    if F.shape[0] == F.shape[1]:        # one source per node: F is the capacitance itself
+        out["Cn"] = 0.5 * (F + F.T)
+        out["asymmetry"] = np.linalg.norm(F - F.T) / np.linalg.norm(F)
     if want_cond:
         # condition number of A with unit-norm columns (the offset column and
         # the potential columns differ by ~1e15 in scale; QR is insensitive to

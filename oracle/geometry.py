@@ -96,6 +96,34 @@ def layout(grid, columns, n_az=4, n_h=2, az0=None) -> Layout:
                   np.array(colloc_off))
 
 
+def ring_sources(columns, lay: Layout, n_ring, frac=0.5, az0=0.0, n_az=4):
+    """Sources on a ring of n_ring lines inside each column (a reading of the point charges "at the
+    boundaries" of the active volume, Sec. 3, that resolves the azimuthal variation of the column
+    potential which one axial line cannot): at every node height of the column, n_ring point
+    sources at radius frac * r_c and azimuths az0 + 2 pi k / n_ring.  n_ring = 1 gives the axial
+    sources of ``layout`` (frac ignored).  The ring's azimuthal harmonics must be resolved by the
+    n_az collocation azimuths, so n_ring < n_az (n_ring = n_az leaves patterns that vanish at every
+    collocation point and makes the fit singular).  Returns (src [Ns', 3], node [Ns']): the
+    positions and, for each source, the node (column, height) whose potential it carries."""
+    if n_ring < 1:
+        raise ValueError("n_ring must be at least 1")
+    if n_ring > 1 and n_ring >= n_az:
+        raise ValueError("a ring needs fewer lines than collocation azimuths (n_ring < n_az)")
+    if n_ring > 1 and not (0.0 < frac < 1.0):
+        raise ValueError("the ring radius must lie inside the column (0 < frac < 1)")
+    src, node = [], []
+    for ci, c in enumerate(columns):
+        m = c.n_sources
+        zs = c.z0 + (np.arange(m) + 0.5) * (c.z1 - c.z0) / m
+        rr = frac * c.radius if n_ring > 1 else 0.0
+        for j in range(m):
+            for k in range(n_ring):
+                th = az0 + 2.0 * math.pi * k / n_ring
+                src.append([c.x + rr * math.cos(th), c.y + rr * math.sin(th), zs[j]])
+                node.append(lay.col_off[ci] + j)
+    return np.array(src), np.array(node)
+
+
 def interp_matrix(columns, lay: Layout):
     """S [Nc, Ns]: column potential at each collocation height from node potentials."""
     S = np.zeros((len(lay.colloc), lay.n_src))
