@@ -1569,10 +1569,13 @@ void do_loss_grad(wt_ctx* c, const wt_tracks* tr, double* loss, double* grad, co
             house_right(c, dP.p, nc);
             set_column(s, dP.p, nc, ns, 0, 0.0);
             scale_columns(s, dP.p, nc, ns, ns, c->fitD.p);                    // dA_s
-            tmp.alloc((size_t)nc * ns);
-            dgemm(s, false, false, nc, ns, ns, 1.0, dP.p, ns, c->fitY.p, ns, 0.0, tmp.p, ns);
+            // T = dA_s^T R - (A_s^T dA_s) Y: the collocation-long contraction A_s^T dA_s once, then
+            // the N_s-long product with Y (4 N_c N_s^2 + 2 N_s^3 flop instead of 6 N_c N_s^2 for
+            // A_s^T (dA_s Y))
+            tmp.alloc((size_t)ns * ns);
+            dgemm(s, true, false, ns, ns, nc, 1.0, c->fitA.p, ns, dP.p, ns, 0.0, tmp.p, ns);
             T.alloc((size_t)ns * ns);
-            dgemm(s, true, false, ns, ns, nc, -1.0, c->fitA.p, ns, tmp.p, ns, 0.0, T.p, ns);
+            dgemm(s, false, false, ns, ns, ns, -1.0, tmp.p, ns, c->fitY.p, ns, 0.0, T.p, ns);
             dgemm(s, true, false, ns, ns, nc, 1.0, dP.p, ns, Rs.p, ns, 1.0, T.p, ns);
             trsm_lower(s, c->fitL.p, ns, ns, T.p, ns, ns);
             trsm_lower_t(s, c->fitL.p, ns, ns, T.p, ns, ns);
