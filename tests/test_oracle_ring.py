@@ -90,3 +90,14 @@ def test_aliased_ring_is_refused(cell):
         geometry.ring_sources(w.columns, axial.lay, 4, n_az=4)
     with pytest.raises(ValueError):
         geometry.ring_sources(w.columns, axial.lay, 3, frac=1.2)
+
+
+def test_residual_keeps_falling_with_more_lines(cell):
+    """Five lines, with six collocation azimuths to resolve them, take the residual further down
+    than three (the second azimuthal harmonic of the column potential becomes representable)."""
+    w, _, ring3 = cell
+    w6 = W.Workload("m3", w.grid, w.columns, W.FitSpec(n_az=6), w.times)
+    ring5 = O.solve(w6, times=np.array([0.0, 1.0]), n_ring=5)
+    assert ring5.sources.shape[0] == 5 * ring3.lay.n_src
+    assert _residual(ring5) < 0.8 * _residual(ring3)
+    assert ring5.fit["asymmetry"] < 1e-2
